@@ -1,0 +1,127 @@
+"""Pins for the oracle's copy and digest, and for the seeded payload generator (CPU only)."""
+import numpy as np
+import pytest
+
+import payload
+from oracle import transfer as T
+
+# splitmix64 started at state 1234567: the first five outputs, as published with the
+# reference C implementation of splitmix64 (Vigna) and widely reproduced.
+SPLITMIX_1234567 = [6457827717110365317, 3203168211198807973, 9817491932198370423,
+                    4593380528125082431, 16408922859458223821]
+GAMMA = 0x9E3779B97F4A7C15
+M64 = (1 << 64) - 1
+
+
+def test_mix64_matches_published_splitmix64():
+    states = np.array([(1234567 + (i + 1) * GAMMA) & M64 for i in range(5)], dtype=np.uint64)
+    assert [int(v) for v in T.mix64(states)] == SPLITMIX_1234567
+
+
+def test_payload_generator_matches_published_splitmix64():
+    assert [payload.splitmix64_scalar(1234567, i) for i in range(5)] == SPLITMIX_1234567
+    assert [int(v) for v in payload.splitmix64_words(1234567, 0, 5)] == SPLITMIX_1234567
+    assert [int(v) for v in payload.splitmix64_words(1234567, 2, 3)] == SPLITMIX_1234567[2:]
+
+
+def test_digest_closed_forms():
+    assert T.hash64(b"") == 0                                   # mix64(0) = 0
+    m1 = int(T.mix64(np.array([1], dtype=np.uint64))[0])
+    assert T.hash64(b"\x01") == (2 * m1) & M64                  # mix64(1) + mix64(1 ^ 0)
+    m8 = int(T.mix64(np.array([8], dtype=np.uint64))[0])
+    assert T.hash64(bytes(8)) == m8                             # mix64(8) + mix64(0)
+    m16 = int(T.mix64(np.array([16], dtype=np.uint64))[0])
+    mg = int(T.mix64(np.array([GAMMA], dtype=np.uint64))[0])
+    assert T.hash64(bytes(16)) == (m16 + mg) & M64               # word 1 is 0 ^ GAMMA
+
+
+def test_digest_single_word_change():
+    rng = np.random.default_rng(3)
+    a = rng.integers(0, 256, 4096 + 5, dtype=np.uint8)
+    b = a.copy()
+    j = 300
+    b[8 * j + 3] ^= 0x40
+    wa = int(a[8 * j:8 * j + 8].view("<u8")[0])
+    wb = int(b[8 * j:8 * j + 8].view("<u8")[0])
+    ta = int(T.mix64(np.array([wa ^ ((j * GAMMA) & M64)], dtype=np.uint64))[0])
+    tb = int(T.mix64(np.array([wb ^ ((j * GAMMA) & M64)], dtype=np.uint64))[0])
+    assert (T.hash64(a) - T.hash64(b)) & M64 == (ta - tb) & M64
+
+
+def test_digest_is_position_sensitive_and_pads_with_zeros():
+    a = np.arange(64, dtype=np.uint8)
+    b = a.copy()
+    b[[0, 8]] = b[[8, 0]]
+    assert T.hash64(a) != T.hash64(b)
+    # 9 bytes: the tail word is the 9th byte zero-padded
+    nine = np.arange(1, 10, dtype=np.uint8)
+    w0 = int(nine[:8].view("<u8")[0])
+    m = lambda v: int(T.mix64(np.array([v & M64], dtype=np.uint64))[0])
+    assert T.hash64(nine) == (m(9) + m(w0) + m(9 ^ GAMMA)) & M64
+
+
+def test_digest_block_boundaries():
+    # the oracle digests in 4 Mi-word blocks; a buffer spanning two blocks equals the
+    # sum of its two halves' word terms.
+    n = (1 << 22) * 8 + 24
+    buf = payload.fill("u8", 99, n)
+    whole = T.hash64(buf)
+    lo = buf[: (1 << 22) * 8]
+    hi_terms = (T.hash64(buf) - T.hash64(lo)) & M64
+    m = lambda v: int(T.mix64(np.array([v & M64], dtype=np.uint64))[0])
+    words = buf[(1 << 22) * 8:].view("<u8")
+    expect = sum(m(int(w) ^ ((((1 << 22) + i) * GAMMA) & M64)) for i, w in enumerate(words))
+    assert hi_terms == (expect + m(n) - m((1 << 22) * 8)) & M64
+    assert whole != T.hash64(buf[:-1])
+
+
+def test_copy_is_identity():
+    buf = payload.fill("u32", 5, 12345)
+    out = T.copy(buf)
+    assert out.tobytes() == buf.tobytes() and out is not buf
+
+
+def test_batch_expected():
+    dev = np.arange(100, dtype=np.uint8)
+    host = np.arange(100, 200, dtype=np.uint8)
+    dst = np.zeros(64, dtype=np.uint8)
+    out = T.batch_expected(dst, {"dev": dev, "host": host}, [("dev", 10, 0, 16), ("host", 5, 32, 8)])
+    assert list(out[:16]) == list(range(10, 26))
+    assert list(out[32:40]) == list(range(105, 113))
+    assert not out[16:32].any() and not out[40:].any()
+    with pytest.raises(ValueError):
+        T.batch_expected(dst, {"dev": dev}, [("dev", 0, 0, 16), ("dev", 0, 8, 16)])
+
+
+def test_payload_encodings():
+    n = 1000
+    f = payload.fill("f32", 11, 4 * n).view("<f4")
+    assert f.min() >= -1.0 and f.max() < 1.0
+    x = payload.splitmix64_words(11, 0, n)
+    assert np.array_equal(f.astype(np.float64), (x >> np.uint64(40)).astype(np.float64) * 2.0 ** -23 - 1.0)
+    bf = payload.fill("bf16", 11, 2 * n).view("<u2")
+    assert np.array_equal(bf, (f.view("<u4") >> 16).astype(np.uint16))
+    u = payload.fill("u32", 11, 4 * n).view("<u4")
+    assert np.array_equal(u, (x & np.uint64(0xFFFFFFFF)).astype(np.uint32))
+    b = payload.fill("u8", 11, 8 * n).view("<u8")
+    assert np.array_equal(b, x)
+
+
+def test_payload_prefix_property():
+    for kind in ("u8", "u32", "f32", "bf16"):
+        full = payload.fill(kind, 21, 4099)
+        for n in (0, 1, 3, 7, 64, 4098):
+            assert np.array_equal(payload.fill(kind, 21, n), full[:n])
+
+
+def test_batch_and_serving_workloads_shape():
+    sizes, d2d, gaps = payload.batch_workload(4096)
+    assert len(sizes) == 4096 and min(sizes) >= 256 and max(sizes) <= 16 << 20
+    assert all(s % 2 == 0 for s in sizes) and all(g % 16 == 0 and 16 <= g <= 112 for g in gaps)
+    frac = sum(d2d) / len(d2d)
+    assert 0.66 < frac < 0.74
+    sched = payload.serving_schedule(1000.0, 2.0)
+    assert 1800 < len(sched) < 2200
+    assert all(16 <= nb <= 256 << 20 and nb % 16 == 0 for _, nb, _ in sched)
+    med = sorted(nb for _, nb, _ in sched)[len(sched) // 2]
+    assert (1 << 20) * 0.8 < med < (1 << 20) * 1.25
