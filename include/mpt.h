@@ -1,0 +1,236 @@
+/*
+ * mpt.h -- C ABI of the single-GPU multi-path transfer library.
+ *
+ * Problem statement (Sec. 4.3, Algorithm 1 "CreateGraph"): move N bytes from a source
+ * buffer to a destination buffer by splitting the message over a set of transfer paths
+ * (the horizontal split, one share per path), cutting each path's part into chunks (the
+ * vertical split) and running every path at the same time; the whole workflow is built
+ * once as a CUDA graph, cached, and replayed (Sec. 4.2 "CUDA Graph Engine" / "CUDA Graph
+ * Cache", Algorithm 1 "LaunchGraph").  On one GPU the paths are:
+ *
+ *   MPT_PATH_CE  copy-engine DMA, one memcpy per chunk (Algorithm 2 "PeerToPeerCopy");
+ *   MPT_PATH_SM  a copy kernel driven by the SMs (device-to-device only);
+ *   MPT_PATH_HS  a two-hop staged route, hop two of a chunk after its hop one
+ *                (Algorithm 2 "StageHostCopy"): device-to-device goes through pinned
+ *                host memory; host-to-device and device-to-host go through a device
+ *                stage, chained by device-side chunk-ready flags;
+ *   MPT_PATH_ZC  a zero-copy kernel that reads or writes mapped pinned host memory
+ *                directly over the host link (host-to-device and device-to-host only).
+ *
+ * Conventions for every call:
+ *   - Every function returns mpt_status; nothing aborts or exits.  On failure
+ *     mpt_last_error() returns a thread-local message describing the last error.
+ *   - "stream" arguments are cudaStream_t values passed as void* (NULL = the legacy
+ *     default stream).  Device pointers are CUDA device addresses; "host" buffers must be
+ *     page-locked (cudaHostAlloc / cudaHostRegister / mpt_host_alloc) so that copy engines
+ *     and kernels can reach them.
+ *   - A context (mpt_ctx_t) owns its streams, events, staging buffers, device status
+ *     word, graph cache and tuner cache.  One host thread per context.
+ *   - Asynchronous calls only enqueue work; results are valid after the stream the work
+ *     joined has been synchronised.  Device-side waits are bounded: a wait that gives up
+ *     records MPT_ETIMEDOUT in the context's status word (mpt_ctx_status) instead of
+ *     hanging the GPU.
+ */
+#ifndef MPT_H
+#define MPT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define MPT_API __attribute__((visibility("default")))
+#else
+#define MPT_API
+#endif
+
+#define MPT_SHARE_ONE 65536u          /* shares are parts of 65536 */
+#define MPT_MAX_PATHS 8u
+#define MPT_MAX_ALIGN 4096u
+#define MPT_MAX_CHUNKS (1u << 20)     /* chunks per plan */
+
+typedef enum {
+  MPT_OK = 0,
+  MPT_EINVAL = 1,     /* invalid argument or plan */
+  MPT_ENOMEM = 2,     /* allocation failed */
+  MPT_EAGAIN = 3,     /* admission refused (staging budget or slots), retry later */
+  MPT_ETIMEDOUT = 4,  /* a bounded device-side or host-side wait gave up */
+  MPT_ENOTSUP = 5,    /* not supported on this device */
+  MPT_ECUDA = 6       /* a CUDA runtime call failed; see mpt_last_error() */
+} mpt_status;
+
+typedef enum { MPT_D2D = 0, MPT_H2D = 1, MPT_D2H = 2 } mpt_dir;
+typedef enum { MPT_PATH_CE = 1, MPT_PATH_SM = 2, MPT_PATH_HS = 4, MPT_PATH_ZC = 8 } mpt_path_kind;
+typedef enum { MPT_LAYOUT_CONTIG = 0, MPT_LAYOUT_INTERLEAVE = 1 } mpt_layout;
+
+/* mpt_path_spec.flags for SM-kernel paths: which copy kernel variant to run. */
+#define MPT_SM_VEC128 0u   /* 128-bit vector loads/stores, grid-stride over tiles */
+#define MPT_SM_BULK 1u     /* cp.async.bulk global->shared->global ring per CTA */
+
+/* One path of a plan.
+ *   kind         one mpt_path_kind; allowed kinds per direction:
+ *                D2D {CE, SM, HS}, H2D {CE, ZC, HS}, D2H {CE, ZC, HS}.
+ *   share        this path's part of the message in 1/65536 units (> 0; all sum to 65536).
+ *   chunk_bytes  C_p, chunk size of the vertical split; a positive multiple of the
+ *                alignment, or 0 to let the context's tuner choose (needs a context).
+ *   ctas         grid size for kernel lanes (0 = library default); ignored by CE.
+ *   flags        kernel variant (MPT_SM_*), 0 otherwise. */
+typedef struct {
+  uint32_t kind;
+  uint32_t share;
+  uint64_t chunk_bytes;
+  uint32_t ctas;
+  uint32_t flags;
+} mpt_path_spec;
+
+/* One chunk of a plan: bytes [offset, offset+bytes) of the message go down path
+ * path_index as that path's chunk number chunk_index. */
+typedef struct {
+  uint64_t offset;
+  uint64_t bytes;
+  uint32_t path_index;
+  uint32_t chunk_index;
+} mpt_chunk;
+
+/* One transfer of a batch: copy `bytes` bytes from src to dst in direction dir. */
+typedef struct {
+  const void* src;
+  void* dst;
+  uint64_t bytes;
+  uint32_t dir;
+  uint32_t flags;
+} mpt_xfer;
+
+/* Graph lifecycle figures of a captured transfer (Sec. 5.5: creation, construction,
+ * instantiation; launch is timed by the caller). */
+typedef struct {
+  uint32_t nodes;          /* graph nodes, every kind */
+  uint32_t memcpy_nodes;
+  uint32_t kernel_nodes;
+  uint32_t memset_nodes;
+  double create_us;        /* cudaGraphCreate */
+  double construct_us;     /* adding nodes and edges */
+  double instantiate_us;   /* cudaGraphInstantiate */
+  uint64_t staging_bytes;  /* staging memory this graph owns */
+} mpt_graph_info;
+
+typedef struct mpt_ctx_s* mpt_ctx_t;
+typedef struct mpt_plan_s* mpt_plan_t;
+typedef struct mpt_graph_s* mpt_graph_t;
+typedef struct mpt_batch_s* mpt_batch_t;
+
+/* ---- library and context ------------------------------------------------------- */
+
+/* Version string; static storage. */
+MPT_API const char* mpt_version(void);
+
+/* Message of the last failed call on this thread; static thread-local storage. */
+MPT_API const char* mpt_last_error(void);
+
+/* Create a context on `device` (makes it current).  tune_file: path of a tuner cache to
+ * load (JSON written by mpt_tune_save), or NULL.  Sec. 4.2 "Base Module": probes the
+ * device and creates streams, events and the status word.  Errors: EINVAL (bad device),
+ * ECUDA, ENOMEM. */
+MPT_API mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out);
+
+/* Destroy a context and everything it owns (cached graphs included).  Waits for the
+ * device to go idle first.  Handles created from it become invalid. */
+MPT_API mpt_status mpt_ctx_destroy(mpt_ctx_t ctx);
+
+/* Read the context's device status word (blocking: synchronises the device), return it
+ * (MPT_OK or the first recorded MPT_ETIMEDOUT) and reset it to MPT_OK.  `site` (nullable)
+ * receives an implementation-defined code of the wait that gave up. */
+MPT_API mpt_status mpt_ctx_status(mpt_ctx_t ctx, uint32_t* site);
+
+/* ---- planning (Sec. 4.3 horizontal + vertical split; Algorithm 1) ----------------- */
+
+/* Build the chunk plan for an `nbytes` message in direction `dir` over `npaths` paths.
+ * ctx may be NULL when every path has an explicit chunk size.  paths == NULL asks the
+ * context's tuner for the whole path set (needs ctx).  align: chunk offsets are
+ * multiples of it (power of two <= 4096; 16 is the library's default).  layout:
+ * CONTIG gives each path one contiguous region in path order; INTERLEAVE deals chunks
+ * round robin (Sec. 4.3, the text after Algorithm 2).  Horizontal split: path p < P-1
+ * gets floor_A(floor(N*share_p/65536)) bytes, the last path the remainder; every chunk
+ * but a path's last has chunk_bytes bytes.  The plan is owned by the caller
+ * (mpt_plan_destroy).  Errors: EINVAL for a bad argument, a kind that cannot carry
+ * `dir`, shares not summing to 65536, a zero share, a chunk size that is not a positive
+ * multiple of `align`, or more than MPT_MAX_CHUNKS chunks. */
+MPT_API mpt_status mpt_plan(mpt_ctx_t ctx, uint64_t nbytes, uint32_t dir, const mpt_path_spec* paths,
+                    uint32_t npaths, uint32_t align, uint32_t layout, mpt_plan_t* out);
+
+/* Copy up to `cap` chunks, sorted by (path_index, chunk_index), into `out` (nullable when
+ * cap == 0) and store the total count in *n. */
+MPT_API mpt_status mpt_plan_chunks(mpt_plan_t plan, mpt_chunk* out, size_t cap, size_t* n);
+
+/* Copy the plan's resolved path specs (chunk sizes and CTA counts filled in) into `out`
+ * (capacity `cap`) and store the path count in *n. */
+MPT_API mpt_status mpt_plan_paths(mpt_plan_t plan, mpt_path_spec* out, uint32_t cap, uint32_t* n);
+
+MPT_API mpt_status mpt_plan_destroy(mpt_plan_t plan);
+
+/* ---- graph capture, cache and launch (Algorithm 1 CreateGraph / LaunchGraph) ------ */
+
+/* Return the executable graph that moves plan's message from src to dst, building,
+ * instantiating and caching it on a miss (key: src, dst, N, direction, plan hash;
+ * fixed-capacity LRU, capacity MPT_GRAPH_CACHE, default 64; Sec. 4.2 "CUDA Graph
+ * Cache").  src/dst must match the plan's direction (device or page-locked host memory)
+ * and must stay allocated while the graph can run: a graph is bound to its addresses.
+ * *out is a new reference owned by the caller (mpt_graph_release); eviction from the
+ * cache never invalidates a held reference.  Graphs with a staged path own their
+ * staging memory.  Errors: EINVAL (pointer kind does not fit the direction, chunk of a
+ * staged path above the stage size), ECUDA, ENOMEM. */
+MPT_API mpt_status mpt_capture(mpt_ctx_t ctx, mpt_plan_t plan, void* dst, const void* src, mpt_graph_t* out);
+
+/* Launch a captured graph on `stream`: it starts after the work already queued on the
+ * stream and later work on the stream waits for all of its chunks (Sec. 4.5 "Final
+ * Synchronization").  Asynchronous.  Launches of one graph run one after another. */
+MPT_API mpt_status mpt_launch(mpt_graph_t graph, void* stream);
+
+/* Lifecycle figures of a captured graph. */
+MPT_API mpt_status mpt_graph_get_info(mpt_graph_t graph, mpt_graph_info* out);
+
+/* Drop a graph reference obtained from mpt_capture. */
+MPT_API mpt_status mpt_graph_release(mpt_graph_t graph);
+
+/* Drop every cached graph whose source or destination range contains `ptr` (call before
+ * freeing a buffer that cached graphs refer to); *n (nullable) gets the count. */
+MPT_API mpt_status mpt_graph_evict(mpt_ctx_t ctx, const void* ptr, uint32_t* n);
+
+/* Issue the same multi-path workflow without a graph (Sec. 4.3's static runtime
+ * pipelining engine): fork from `stream` onto per-path lane streams, enqueue every chunk,
+ * join back onto `stream`.  Asynchronous.  Eager transfers that use the same staged path
+ * serialise on that path's lane (Sec. 4.5 "Contention Avoidance"). */
+MPT_API mpt_status mpt_launch_eager(mpt_ctx_t ctx, mpt_plan_t plan, void* dst, const void* src, void* stream);
+
+/* ---- single kernels (the SM and zero-copy paths on their own) -------------------- */
+
+/* Copy `nbytes` from src to dst with one launch of the SM copy kernel on `stream`.
+ * Both pointers must be device-accessible (device memory, or mapped page-locked host
+ * memory for the zero-copy direction).  variant: MPT_SM_VEC128 or MPT_SM_BULK (the bulk
+ * variant handles the 16-byte-aligned body with cp.async.bulk and the rest with plain
+ * loads; it falls back to VEC128 when src and dst differ modulo 16).  ctas: grid size,
+ * 0 = default.  ctx supplies the status word for bounded waits.  Errors: EINVAL. */
+MPT_API mpt_status mpt_sm_copy(mpt_ctx_t ctx, void* dst, const void* src, uint64_t nbytes, uint32_t variant,
+                       uint32_t ctas, void* stream);
+
+/* Digest of a device-accessible byte range, computed on the GPU on `stream`, waited for,
+ * and stored in *out: H = mix64(N) + sum_i mix64(w_i XOR i*0x9E3779B97F4A7C15) mod 2^64,
+ * w_i the little-endian 8-byte words of the range zero-padded, mix64 the splitmix64
+ * output finaliser.  Blocking. */
+MPT_API mpt_status mpt_hash_device(mpt_ctx_t ctx, const void* ptr, uint64_t nbytes, void* stream, uint64_t* out);
+
+/* ---- page-locked host memory ---------------------------------------------------- */
+
+/* Allocate `nbytes` of page-locked, device-mapped host memory (usable by copy engines and
+ * by the zero-copy kernel at the same address).  Free with mpt_host_free. */
+MPT_API mpt_status mpt_host_alloc(uint64_t nbytes, void** out);
+MPT_API mpt_status mpt_host_free(void* ptr);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPT_H */

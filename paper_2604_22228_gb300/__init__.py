@@ -1,0 +1,173 @@
+"""Single-GPU multi-path transfers with CUDA graphs, on GB300 (sm_103a).
+
+A message of N bytes is split over several transfer paths by share (horizontal split),
+each path's part is cut into chunks (vertical split), and the paths run concurrently
+inside one cached CUDA graph (Sec. 4.2-4.3 of the paper).  On one GPU the paths are the
+copy engines, an SM copy kernel, a two-hop staged route and a zero-copy kernel over
+mapped page-locked host memory.
+
+This module is a thin binding over the C ABI of ``include/mpt.h``: the functions carry
+the C names and only marshal arguments (pointers may be ints or anything with
+``data_ptr()``; streams may be ints, ``None`` or objects with ``cuda_stream``).  Every
+byte moves inside libmpt.so; a missing library raises instead of falling back.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+from . import _ffi
+from ._ffi import (MPT_D2D, MPT_D2H, MPT_H2D, MPT_LAYOUT_CONTIG, MPT_LAYOUT_INTERLEAVE, MPT_MAX_CHUNKS,  # noqa: F401
+                   MPT_MAX_PATHS, MPT_PATH_CE, MPT_PATH_HS, MPT_PATH_SM, MPT_PATH_ZC, MPT_SHARE_ONE, MPT_SM_BULK,
+                   MPT_SM_VEC128, STATUS_NAMES)
+from ._ffi import MPT_EAGAIN, MPT_ECUDA, MPT_EINVAL, MPT_ENOMEM, MPT_ENOTSUP, MPT_ETIMEDOUT, MPT_OK  # noqa: F401
+
+
+class MptError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+def lib():
+    return _ffi.load()
+
+
+def _check(st: int, where: str) -> None:
+    if st != MPT_OK:
+        raise MptError(st, where, lib().mpt_last_error().decode(errors="replace"))
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        return x.ctypes.data
+    raise TypeError(f"cannot take a pointer of {type(x).__name__}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def _specs(paths):
+    arr = (_ffi.mpt_path_spec * len(paths))()
+    for i, p in enumerate(paths):
+        if isinstance(p, dict):
+            p = (p["kind"], p["share"], p.get("chunk_bytes", 0), p.get("ctas", 0), p.get("flags", 0))
+        p = tuple(p) + (0,) * (5 - len(p))
+        arr[i] = _ffi.mpt_path_spec(*p)
+    return arr
+
+
+def mpt_version() -> str:
+    return lib().mpt_version().decode()
+
+
+def mpt_last_error() -> str:
+    return lib().mpt_last_error().decode(errors="replace")
+
+
+def mpt_ctx_create(device: int = 0, tune_file: str | None = None) -> int:
+    h = C.c_void_p()
+    _check(lib().mpt_ctx_create(device, tune_file.encode() if tune_file else None, C.byref(h)), "mpt_ctx_create")
+    return h.value
+
+
+def mpt_ctx_destroy(ctx: int) -> None:
+    _check(lib().mpt_ctx_destroy(ctx), "mpt_ctx_destroy")
+
+
+def mpt_ctx_status(ctx: int) -> tuple[int, int]:
+    """(status, site) of the context's device status word, which is then reset."""
+    site = C.c_uint32()
+    st = lib().mpt_ctx_status(ctx, C.byref(site))
+    return st, site.value
+
+
+def mpt_plan(ctx, nbytes: int, direction: int, paths, align: int = 16, layout: int = MPT_LAYOUT_CONTIG) -> int:
+    h = C.c_void_p()
+    if paths is None:
+        st = lib().mpt_plan(ctx, nbytes, direction, None, 0, align, layout, C.byref(h))
+    else:
+        arr = _specs(paths)
+        st = lib().mpt_plan(ctx, nbytes, direction, arr, len(paths), align, layout, C.byref(h))
+    _check(st, "mpt_plan")
+    return h.value
+
+
+def mpt_plan_chunks(plan: int) -> list[tuple[int, int, int, int]]:
+    n = C.c_size_t()
+    _check(lib().mpt_plan_chunks(plan, None, 0, C.byref(n)), "mpt_plan_chunks")
+    arr = (_ffi.mpt_chunk * max(1, n.value))()
+    _check(lib().mpt_plan_chunks(plan, arr, n.value, C.byref(n)), "mpt_plan_chunks")
+    return [(c.offset, c.bytes, c.path_index, c.chunk_index) for c in arr[: n.value]]
+
+
+def mpt_plan_paths(plan: int) -> list[dict]:
+    arr = (_ffi.mpt_path_spec * MPT_MAX_PATHS)()
+    n = C.c_uint32()
+    _check(lib().mpt_plan_paths(plan, arr, MPT_MAX_PATHS, C.byref(n)), "mpt_plan_paths")
+    return [dict(kind=s.kind, share=s.share, chunk_bytes=s.chunk_bytes, ctas=s.ctas, flags=s.flags)
+            for s in arr[: n.value]]
+
+
+def mpt_plan_destroy(plan: int) -> None:
+    _check(lib().mpt_plan_destroy(plan), "mpt_plan_destroy")
+
+
+def mpt_capture(ctx: int, plan: int, dst, src) -> int:
+    h = C.c_void_p()
+    _check(lib().mpt_capture(ctx, plan, _ptr(dst), _ptr(src), C.byref(h)), "mpt_capture")
+    return h.value
+
+
+def mpt_launch(graph: int, stream=None) -> None:
+    _check(lib().mpt_launch(graph, _stream(stream)), "mpt_launch")
+
+
+def mpt_graph_get_info(graph: int) -> dict:
+    info = _ffi.mpt_graph_info()
+    _check(lib().mpt_graph_get_info(graph, C.byref(info)), "mpt_graph_get_info")
+    return {name: getattr(info, name) for name, _ in _ffi.mpt_graph_info._fields_}
+
+
+def mpt_graph_release(graph: int) -> None:
+    _check(lib().mpt_graph_release(graph), "mpt_graph_release")
+
+
+def mpt_graph_evict(ctx: int, ptr) -> int:
+    n = C.c_uint32()
+    _check(lib().mpt_graph_evict(ctx, _ptr(ptr), C.byref(n)), "mpt_graph_evict")
+    return n.value
+
+
+def mpt_launch_eager(ctx: int, plan: int, dst, src, stream=None) -> None:
+    _check(lib().mpt_launch_eager(ctx, plan, _ptr(dst), _ptr(src), _stream(stream)), "mpt_launch_eager")
+
+
+def mpt_sm_copy(ctx: int, dst, src, nbytes: int, variant: int = MPT_SM_VEC128, ctas: int = 0, stream=None) -> None:
+    _check(lib().mpt_sm_copy(ctx, _ptr(dst), _ptr(src), nbytes, variant, ctas, _stream(stream)), "mpt_sm_copy")
+
+
+def mpt_hash_device(ctx: int, ptr, nbytes: int, stream=None) -> int:
+    out = C.c_uint64()
+    _check(lib().mpt_hash_device(ctx, _ptr(ptr), nbytes, _stream(stream), C.byref(out)), "mpt_hash_device")
+    return out.value
+
+
+def mpt_host_alloc(nbytes: int) -> int:
+    p = C.c_void_p()
+    _check(lib().mpt_host_alloc(nbytes, C.byref(p)), "mpt_host_alloc")
+    return p.value
+
+
+def mpt_host_free(ptr) -> None:
+    _check(lib().mpt_host_free(_ptr(ptr)), "mpt_host_free")

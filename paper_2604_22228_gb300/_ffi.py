@@ -1,0 +1,94 @@
+"""ctypes declarations of the C ABI in include/mpt.h.
+
+Argument marshalling only: every step of a transfer runs inside libmpt.so.  The library
+is built in-tree (``paper_2604_22228_gb300/libmpt.so``) by ``build.py``; loading fails
+loudly when it is missing -- there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmpt.so")
+
+# status codes
+MPT_OK, MPT_EINVAL, MPT_ENOMEM, MPT_EAGAIN, MPT_ETIMEDOUT, MPT_ENOTSUP, MPT_ECUDA = range(7)
+STATUS_NAMES = {0: "MPT_OK", 1: "MPT_EINVAL", 2: "MPT_ENOMEM", 3: "MPT_EAGAIN", 4: "MPT_ETIMEDOUT",
+                5: "MPT_ENOTSUP", 6: "MPT_ECUDA"}
+# directions, path kinds, layouts, kernel variants
+MPT_D2D, MPT_H2D, MPT_D2H = 0, 1, 2
+MPT_PATH_CE, MPT_PATH_SM, MPT_PATH_HS, MPT_PATH_ZC = 1, 2, 4, 8
+MPT_LAYOUT_CONTIG, MPT_LAYOUT_INTERLEAVE = 0, 1
+MPT_SM_VEC128, MPT_SM_BULK = 0, 1
+MPT_SHARE_ONE = 65536
+MPT_MAX_PATHS = 8
+MPT_MAX_CHUNKS = 1 << 20
+
+
+class mpt_path_spec(C.Structure):
+    _fields_ = [("kind", C.c_uint32), ("share", C.c_uint32), ("chunk_bytes", C.c_uint64),
+                ("ctas", C.c_uint32), ("flags", C.c_uint32)]
+
+
+class mpt_chunk(C.Structure):
+    _fields_ = [("offset", C.c_uint64), ("bytes", C.c_uint64), ("path_index", C.c_uint32),
+                ("chunk_index", C.c_uint32)]
+
+
+class mpt_xfer(C.Structure):
+    _fields_ = [("src", C.c_void_p), ("dst", C.c_void_p), ("bytes", C.c_uint64), ("dir", C.c_uint32),
+                ("flags", C.c_uint32)]
+
+
+class mpt_graph_info(C.Structure):
+    _fields_ = [("nodes", C.c_uint32), ("memcpy_nodes", C.c_uint32), ("kernel_nodes", C.c_uint32),
+                ("memset_nodes", C.c_uint32), ("create_us", C.c_double), ("construct_us", C.c_double),
+                ("instantiate_us", C.c_double), ("staging_bytes", C.c_uint64)]
+
+
+H = C.c_void_p  # opaque handles
+P = C.POINTER
+
+# name -> (restype, argtypes); the names and order follow include/mpt.h
+SIGNATURES = {
+    "mpt_version": (C.c_char_p, []),
+    "mpt_last_error": (C.c_char_p, []),
+    "mpt_ctx_create": (C.c_int, [C.c_int, C.c_char_p, P(H)]),
+    "mpt_ctx_destroy": (C.c_int, [H]),
+    "mpt_ctx_status": (C.c_int, [H, P(C.c_uint32)]),
+    "mpt_plan": (C.c_int, [H, C.c_uint64, C.c_uint32, P(mpt_path_spec), C.c_uint32, C.c_uint32, C.c_uint32,
+                          P(H)]),
+    "mpt_plan_chunks": (C.c_int, [H, P(mpt_chunk), C.c_size_t, P(C.c_size_t)]),
+    "mpt_plan_paths": (C.c_int, [H, P(mpt_path_spec), C.c_uint32, P(C.c_uint32)]),
+    "mpt_plan_destroy": (C.c_int, [H]),
+    "mpt_capture": (C.c_int, [H, H, C.c_void_p, C.c_void_p, P(H)]),
+    "mpt_launch": (C.c_int, [H, C.c_void_p]),
+    "mpt_graph_get_info": (C.c_int, [H, P(mpt_graph_info)]),
+    "mpt_graph_release": (C.c_int, [H]),
+    "mpt_graph_evict": (C.c_int, [H, C.c_void_p, P(C.c_uint32)]),
+    "mpt_launch_eager": (C.c_int, [H, H, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "mpt_sm_copy": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint32, C.c_uint32, C.c_void_p]),
+    "mpt_hash_device": (C.c_int, [H, C.c_void_p, C.c_uint64, C.c_void_p, P(C.c_uint64)]),
+    "mpt_host_alloc": (C.c_int, [C.c_uint64, P(C.c_void_p)]),
+    "mpt_host_free": (C.c_int, [C.c_void_p]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> C.CDLL:
+    """Load libmpt.so and declare every entry point; raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_2604_22228_gb300.build` "
+                          "(the library has no non-CUDA fallback)")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib

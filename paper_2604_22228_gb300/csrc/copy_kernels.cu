@@ -1,0 +1,397 @@
+// Data-moving kernels of the transfer paths, written for sm_103a.
+//
+//  k_sm_copy_vec   SM copy kernel, 128-bit loads/stores: each CTA walks 32 KiB tiles of
+//                  the ranges it is given, every thread keeping four 16-byte vectors in
+//                  flight.  The device-to-device path the SMs add next to the copy
+//                  engines (Sec. 4.3's horizontal split over paths).
+//  k_sm_copy_bulk  same contract, body moved by cp.async.bulk global->shared->global
+//                  (non-multicast) through a four-stage shared-memory ring driven by one
+//                  thread per CTA and tracked by mbarriers.
+//  k_zc_copy       zero-copy kernel: the vec128 loop with plain (coherent) loads, used on
+//                  mapped page-locked host memory for host<->device transfers.
+//  k_stage_consume second hop of the host-to-device staged path: waits on per-chunk
+//                  ready flags set after each copy-engine hop one, then moves the chunk
+//                  from the device stage to its destination (Algorithm 2 StageHostCopy's
+//                  "hop two after hop one" edge, carried by device flags).
+//  k_hash          digest of a byte range (test utility).
+//
+// Every device-side wait is bounded by the global timer and records MPT_ETIMEDOUT in
+// the context's status word instead of spinning forever.
+#include "kernels.cuh"
+
+#include <algorithm>
+
+namespace mpt {
+
+namespace {
+
+constexpr uint32_t kTimedOut = 4;  // MPT_ETIMEDOUT
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void record_timeout(uint32_t* status, uint32_t site) {
+  if (status) atomicCAS(status, 0u, (site << 8) | kTimedOut);
+}
+
+__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ uint4 ld_plain(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.v4.u32 {%0,%1,%2,%3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+
+__device__ __forceinline__ void st_plain(uint4* p, const uint4& v) {
+  asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
+               "r"(v.w)
+               : "memory");
+}
+
+__device__ __forceinline__ int find_range(const CopyArgs& a, uint32_t t) {
+  int r = 0;
+  while (r + 1 < (int)a.nranges && t >= a.tile_start[r + 1]) ++r;
+  return r;
+}
+
+// Head (bytes before the aligned body) and tail (bytes after it) of a coaligned range;
+// threads 0..15 copy the head, threads 32..47 the tail.
+__device__ __forceinline__ void copy_edges(const uint8_t* s, uint8_t* o, const RangeDesc& d,
+                                           uint64_t body_bytes) {
+  const uint32_t tid = threadIdx.x;
+  if (tid < d.head) o[tid] = s[tid];
+  const uint64_t tail_start = d.head + body_bytes;
+  const uint32_t tail = (uint32_t)(d.bytes - tail_start);
+  if (tid >= 32 && tid < 32 + tail) o[tail_start + (tid - 32)] = s[tail_start + (tid - 32)];
+}
+
+template <bool kHostLink>
+__device__ __forceinline__ void copy_tiles_vec(const CopyArgs& a) {
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    const int r = find_range(a, t);
+    const uint32_t lt = t - a.tile_start[r];
+    const RangeDesc d = a.r[r];
+    const uint8_t* s = a.src + d.src_off;
+    uint8_t* o = a.dst + d.dst_off;
+    if (d.coaligned) {
+      const uint64_t nvec = (d.bytes - d.head) >> 4;
+      if (lt == 0) copy_edges(s, o, d, nvec << 4);
+      const uint4* sv = reinterpret_cast<const uint4*>(s + d.head);
+      uint4* ov = reinterpret_cast<uint4*>(o + d.head);
+      const uint64_t v0 = (uint64_t)lt * kVecTileVecs + tid;
+      uint4 buf[kVecUnroll];
+#pragma unroll
+      for (int u = 0; u < kVecUnroll; ++u) {
+        const uint64_t i = v0 + (uint64_t)u * kVecThreads;
+        if (i < nvec) buf[u] = kHostLink ? ld_plain(sv + i) : ld_stream(sv + i);
+      }
+#pragma unroll
+      for (int u = 0; u < kVecUnroll; ++u) {
+        const uint64_t i = v0 + (uint64_t)u * kVecThreads;
+        if (i < nvec) st_plain(ov + i, buf[u]);
+      }
+    } else {
+      const uint64_t b0 = (uint64_t)lt * kByteTile;
+      const uint64_t b1 = b0 + kByteTile < d.bytes ? b0 + kByteTile : d.bytes;
+      for (uint64_t i = b0 + tid; i < b1; i += blockDim.x) o[i] = s[i];
+    }
+  }
+}
+
+// ---- cp.async.bulk + mbarrier helpers -----------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Wait for phase `parity` of the barrier to complete; false if the deadline passes.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t deadline) {
+  while (true) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (global_ns() > deadline) return false;
+  }
+}
+
+__device__ __forceinline__ void bulk_load(uint32_t dst_smem, const void* src, uint32_t bytes,
+                                          uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          dst_smem),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void bulk_store(void* dst, uint32_t src_smem, uint32_t bytes) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src_smem),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+// Global addresses and length of the bulk body piece of tile t.
+__device__ __forceinline__ uint32_t bulk_piece(const CopyArgs& a, uint32_t t, const uint8_t*& gs,
+                                               uint8_t*& gd) {
+  const int r = find_range(a, t);
+  const uint32_t lt = t - a.tile_start[r];
+  const RangeDesc& d = a.r[r];
+  const uint64_t body = ((d.bytes - d.head) >> 4) << 4;
+  const uint64_t off = (uint64_t)lt * kBulkStageBytes;
+  gs = a.src + d.src_off + d.head + off;
+  gd = a.dst + d.dst_off + d.head + off;
+  if (off >= body) return 0;
+  const uint64_t n = body - off;
+  return n < kBulkStageBytes ? (uint32_t)n : kBulkStageBytes;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec(CopyArgs a) { copy_tiles_vec<false>(a); }
+
+__global__ void __launch_bounds__(kVecThreads) k_zc_copy(CopyArgs a) { copy_tiles_vec<true>(a); }
+
+__global__ void __launch_bounds__(kBulkThreads, 1) k_sm_copy_bulk(CopyArgs a) {
+  extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ __align__(8) uint64_t bar[kBulkStages];
+  const uint32_t tid = threadIdx.x;
+
+  // Bytes outside the 16-byte body go with plain loads by the CTA owning tile 0.
+  for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
+    const int r = find_range(a, t);
+    if (t != a.tile_start[r]) continue;
+    const RangeDesc d = a.r[r];
+    copy_edges(a.src + d.src_off, a.dst + d.dst_off, d, ((d.bytes - d.head) >> 4) << 4);
+  }
+
+  if (tid == 0) {
+    for (int s = 0; s < kBulkStages; ++s) mbar_init(smem_addr(&bar[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid != 0) return;
+
+  const uint32_t n_my =
+      blockIdx.x < a.ntiles ? (a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  const uint32_t base = smem_addr(smem);
+  const uint64_t deadline = global_ns() + kDefaultTimeoutNs;
+
+  auto issue_load = [&](uint32_t i) {
+    const uint32_t s = i % kBulkStages;
+    const uint32_t b = smem_addr(&bar[s]);
+    const uint8_t* gs;
+    uint8_t* gd;
+    const uint32_t n = bulk_piece(a, blockIdx.x + i * gridDim.x, gs, gd);
+    if (n) {
+      mbar_arrive_expect_tx(b, n);
+      bulk_load(base + s * kBulkStageBytes, gs, n, b);
+    } else {
+      mbar_arrive(b);
+    }
+  };
+
+  const uint32_t prologue = n_my < (uint32_t)kBulkStages ? n_my : (uint32_t)kBulkStages;
+  for (uint32_t i = 0; i < prologue; ++i) issue_load(i);
+
+  uint32_t i = 0;
+  bool failed = false;
+  for (; i < n_my; ++i) {
+    const uint32_t s = i % kBulkStages;
+    if (!mbar_wait(smem_addr(&bar[s]), (i / kBulkStages) & 1u, deadline)) {
+      failed = true;
+      break;
+    }
+    const uint8_t* gs;
+    uint8_t* gd;
+    const uint32_t n = bulk_piece(a, blockIdx.x + i * gridDim.x, gs, gd);
+    if (n) bulk_store(gd, base + s * kBulkStageBytes, n);
+    bulk_commit();
+    // Refill the stage of tile i-1 once its store has finished reading shared memory.
+    if (i >= 1 && i - 1 + kBulkStages < n_my) {
+      bulk_wait_read<1>();
+      issue_load(i - 1 + kBulkStages);
+    }
+  }
+  bulk_wait_all();
+  if (failed) {
+    record_timeout(a.status, kSiteBulkLoad);
+    // Give loads still in flight a bounded chance to land before shared memory is released.
+    const uint64_t drain = global_ns() + kDefaultTimeoutNs;
+    const uint32_t hi = (i + kBulkStages < n_my) ? i + kBulkStages : n_my;
+    for (uint32_t j = i; j < hi; ++j) mbar_wait(smem_addr(&bar[j % kBulkStages]), (j / kBulkStages) & 1u, drain);
+  }
+}
+
+__global__ void __launch_bounds__(kVecThreads) k_stage_consume(StageArgs a) {
+  __shared__ int ok;
+  constexpr uint64_t kTile = kVecTileVecs * 16;
+  const uint32_t total = a.nchunks * a.tiles_per_chunk;
+  const uint32_t tid = threadIdx.x;
+  for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
+    const uint32_t k = t / a.tiles_per_chunk;
+    const uint32_t lt = t - k * a.tiles_per_chunk;
+    if (tid == 0) {
+      const uint64_t deadline = global_ns() + a.timeout_ns;
+      int seen = 0;
+      while (true) {
+        uint32_t v;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a.ready + k) : "memory");
+        if (v != 0) {
+          seen = 1;
+          break;
+        }
+        if (global_ns() > deadline) break;
+        __nanosleep(128);
+      }
+      ok = seen;
+      if (!seen) record_timeout(a.status, kSiteStageFlag);
+    }
+    __syncthreads();
+    if (!ok) return;
+    const StageChunk c = a.chunks[k];
+    const uint64_t off = (uint64_t)lt * kTile;
+    if (off < c.bytes) {
+      const uint64_t n = c.bytes - off < kTile ? c.bytes - off : kTile;
+      const uint8_t* s = a.stage + c.stage_off + off;
+      uint8_t* o = a.dst + c.dst_off + off;
+      if (((reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(o)) & 15) == 0) {
+        const uint64_t nv = n >> 4;
+        const uint4* sv = reinterpret_cast<const uint4*>(s);
+        uint4* ov = reinterpret_cast<uint4*>(o);
+        for (uint64_t v = tid; v < nv; v += blockDim.x) ov[v] = __ldcg(sv + v);
+        for (uint64_t b = (nv << 4) + tid; b < n; b += blockDim.x) o[b] = __ldcg(s + b);
+      } else {
+        for (uint64_t b = tid; b < n; b += blockDim.x) o[b] = __ldcg(s + b);
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      const uint32_t prev = atomicAdd(a.done + k, 1u);
+      if (prev == a.tiles_per_chunk - 1) {
+        a.done[k] = 0;
+        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(a.ready + k), "r"(0u) : "memory");
+      }
+    }
+  }
+}
+
+namespace {
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_hash(const uint8_t* p, uint64_t n, unsigned long long* out) {
+  constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+  const uint64_t nw = (n + 7) >> 3;
+  const bool aligned = (reinterpret_cast<uintptr_t>(p) & 7) == 0;
+  uint64_t acc = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < nw; w += stride) {
+    uint64_t v = 0;
+    if (aligned && (w + 1) * 8 <= n) {
+      v = __ldcs(reinterpret_cast<const unsigned long long*>(p) + w);
+    } else {
+      for (int b = 0; b < 8; ++b) {
+        const uint64_t i = w * 8 + b;
+        if (i < n) v |= (uint64_t)p[i] << (8 * b);
+      }
+    }
+    acc += mix64(v ^ (w * kGamma));
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  __shared__ uint64_t warp_sum[8];
+  if ((threadIdx.x & 31) == 0) warp_sum[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint64_t s = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += warp_sum[i];
+    if (blockIdx.x == 0) s += mix64(n);
+    atomicAdd(out, (unsigned long long)s);
+  }
+}
+
+// ---- host side -------------------------------------------------------------------------
+
+int make_copy_args(CopyArgs& a, const void* src, void* dst, const RangeDesc* ranges, int n,
+                   int variant, uint32_t* status) {
+  a.src = static_cast<const uint8_t*>(src);
+  a.dst = static_cast<uint8_t*>(dst);
+  a.status = status;
+  a.nranges = 0;
+  uint64_t tiles = 0;
+  a.tile_start[0] = 0;
+  for (int i = 0; i < n && i < kInlineRanges; ++i) {
+    RangeDesc d = ranges[i];
+    if (d.bytes == 0) continue;
+    const uintptr_t s = reinterpret_cast<uintptr_t>(src) + d.src_off;
+    const uintptr_t o = reinterpret_cast<uintptr_t>(dst) + d.dst_off;
+    d.coaligned = ((s ^ o) & 15) == 0 ? 1u : 0u;
+    d.head = d.coaligned ? (uint32_t)std::min<uint64_t>(d.bytes, (16 - (o & 15)) & 15) : 0u;
+    if (variant == 1 && !d.coaligned) return kArgsNeedVec;
+    uint64_t t;
+    const uint64_t body = ((d.bytes - d.head) >> 4) << 4;
+    if (!d.coaligned) {
+      t = (d.bytes + kByteTile - 1) / kByteTile;
+    } else if (variant == 1) {
+      t = (body + kBulkStageBytes - 1) / kBulkStageBytes;
+    } else {
+      t = ((body >> 4) + kVecTileVecs - 1) / kVecTileVecs;
+    }
+    if (t == 0) t = 1;  // a range too short for a body still needs its edge bytes copied
+    a.r[a.nranges] = d;
+    tiles += t;
+    a.tile_start[a.nranges + 1] = (uint32_t)tiles;
+    a.nranges++;
+  }
+  for (uint32_t i = a.nranges + 1; i <= (uint32_t)kInlineRanges; ++i) a.tile_start[i] = (uint32_t)tiles;
+  a.ntiles = (uint32_t)tiles;
+  return tiles < (1ull << 31) ? kArgsOk : kArgsTooLarge;
+}
+
+}  // namespace mpt

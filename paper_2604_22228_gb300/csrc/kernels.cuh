@@ -1,0 +1,87 @@
+// Internal interface between the runtime (graph builder, eager engine) and the CUDA
+// kernels of the transfer paths.  Not part of the public ABI (include/mpt.h).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mpt {
+
+// ---- byte-range copies (SM copy kernel, zero-copy kernel) ------------------------
+
+constexpr int kInlineRanges = 16;     // ranges carried by value in one launch
+constexpr int kVecThreads = 512;      // vec128 kernel block size
+constexpr int kVecUnroll = 4;         // 16-byte vectors in flight per thread per tile
+constexpr uint64_t kVecTileVecs = (uint64_t)kVecThreads * kVecUnroll;  // 32 KiB tiles
+constexpr uint64_t kByteTile = 16384; // tile of the bytewise fallback
+constexpr int kBulkThreads = 128;     // bulk kernel block size (thread 0 drives the ring)
+constexpr int kBulkStages = 4;        // shared-memory ring depth
+constexpr uint32_t kBulkStageBytes = 48 * 1024;  // one cp.async.bulk per stage
+
+// One contiguous range to copy: src + src_off -> dst + dst_off, `bytes` long.
+// head: bytes before the 16-byte aligned body when src and dst agree modulo 16
+// (coaligned), else unused; the kernel copies such ranges bytewise.
+struct RangeDesc {
+  uint64_t src_off;
+  uint64_t dst_off;
+  uint64_t bytes;
+  uint32_t head;
+  uint32_t coaligned;
+};
+
+struct CopyArgs {
+  const uint8_t* src;
+  uint8_t* dst;
+  uint32_t nranges;
+  uint32_t ntiles;                       // sum of tiles over ranges
+  uint32_t tile_start[kInlineRanges + 1];
+  RangeDesc r[kInlineRanges];
+  uint32_t* status;                      // device status word (bounded waits)
+};
+
+// Fill `a` for up to kInlineRanges ranges with the tiling of `variant` (0 vec128,
+// 1 bulk, 2 zero-copy).  Returns kArgsOk, kArgsNeedVec when a bulk launch must fall
+// back to vec128 (source and destination differ modulo 16), or kArgsTooLarge.
+constexpr int kArgsOk = 0, kArgsNeedVec = 1, kArgsTooLarge = 2;
+int make_copy_args(CopyArgs& a, const void* src, void* dst, const RangeDesc* ranges, int n,
+                   int variant, uint32_t* status);
+
+__global__ void k_sm_copy_vec(CopyArgs a);
+__global__ void k_sm_copy_bulk(CopyArgs a);
+__global__ void k_zc_copy(CopyArgs a);
+
+// ---- flag-chained stage consumer (host-to-device staged path) ----------------------
+// The copy engine fills stage chunk k and a memset node then sets ready[k] = 1.  The
+// consumer kernel waits (bounded) for ready[k], copies the chunk from the stage to its
+// destination, and the CTA finishing the chunk's last tile clears ready[k] and done[k],
+// so a replay of the graph finds every flag at 0 again.
+struct StageChunk {
+  uint64_t dst_off;    // destination offset of the chunk
+  uint64_t stage_off;  // its offset in the stage buffer
+  uint64_t bytes;
+};
+
+struct StageArgs {
+  const uint8_t* stage;
+  uint8_t* dst;
+  const StageChunk* chunks;  // device table, nchunks entries
+  uint32_t* ready;           // nchunks flags
+  uint32_t* done;            // nchunks tile counters
+  uint32_t nchunks;
+  uint32_t tiles_per_chunk;  // ceil(max chunk bytes / tile)
+  uint32_t* status;
+  uint64_t timeout_ns;
+};
+
+__global__ void k_stage_consume(StageArgs a);
+
+// ---- digest (test utility) -------------------------------------------------------
+__global__ void k_hash(const uint8_t* p, uint64_t n, unsigned long long* out);
+
+// Status codes written by kernels: (site << 8) | MPT_ETIMEDOUT.
+constexpr uint32_t kSiteBulkLoad = 1;
+constexpr uint32_t kSiteStageFlag = 2;
+constexpr uint32_t kSiteBatch = 3;
+
+constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;  // 2 s
+
+}  // namespace mpt

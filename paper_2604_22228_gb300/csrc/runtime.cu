@@ -1,0 +1,778 @@
+// Runtime of the multi-path transfer library: contexts, the CUDA graph engine and its
+// LRU cache (Sec. 4.2), graph construction per path kind (Algorithms 1 and 2), the eager
+// runtime pipelining engine (Sec. 4.3), and the C ABI entry points of mpt.h that need
+// the GPU.
+#include <algorithm>
+#include <chrono>
+#include <cstdlib>
+#include <cstring>
+#include <list>
+#include <unordered_map>
+#include <unordered_set>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace mpt {
+const char* last_error_cstr();
+}
+
+#define CUDA_TRY(expr)                                                                           \
+  do {                                                                                           \
+    cudaError_t e_ = (expr);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return mpt::fail(MPT_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+namespace mpt {
+namespace {
+
+double now_us() {
+  using namespace std::chrono;
+  return duration<double, std::micro>(steady_clock::now().time_since_epoch()).count();
+}
+
+uint64_t env_u64(const char* name, uint64_t dflt) {
+  const char* v = std::getenv(name);
+  if (!v || !*v) return dflt;
+  char* end = nullptr;
+  unsigned long long x = std::strtoull(v, &end, 0);
+  return (end && *end == 0) ? (uint64_t)x : dflt;
+}
+
+struct GraphKey {
+  uint64_t src, dst, nbytes, dir, plan_hash;
+  bool operator==(const GraphKey& o) const {
+    return src == o.src && dst == o.dst && nbytes == o.nbytes && dir == o.dir && plan_hash == o.plan_hash;
+  }
+};
+struct GraphKeyHash {
+  size_t operator()(const GraphKey& k) const { return (size_t)fnv1a(&k, sizeof k); }
+};
+
+enum MemKind { kMemDevice, kMemHost, kMemOther };
+
+MemKind classify(const void* p, int device) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return kMemOther;
+  }
+  if ((a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == device)
+    return kMemDevice;
+  if (a.type == cudaMemoryTypeHost) return kMemHost;
+  return kMemOther;
+}
+
+// Per-path lane of the eager engine: hop-one and hop-two streams, per-slot events of the
+// two-slot staging ring, and the lane's staging buffers (grown on demand).
+struct EagerLane {
+  cudaStream_t s[2] = {nullptr, nullptr};
+  cudaEvent_t hop1[2] = {nullptr, nullptr};
+  cudaEvent_t hop2[2] = {nullptr, nullptr};
+  cudaEvent_t done = nullptr;
+  void* host_stage = nullptr;
+  uint64_t host_stage_bytes = 0;
+  void* dev_stage = nullptr;
+  uint64_t dev_stage_bytes = 0;
+};
+
+constexpr uint32_t kDefaultConsumerCtas = 32;
+
+}  // namespace
+}  // namespace mpt
+
+struct mpt_graph_s {
+  int refs = 0;
+  mpt_ctx_t ctx = nullptr;
+  mpt::GraphKey key{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  mpt_graph_info info{};
+  std::vector<void*> host_allocs, dev_allocs;
+  uint64_t src_lo = 0, src_hi = 0, dst_lo = 0, dst_hi = 0;
+  bool cached = false;
+  std::list<mpt_graph_s*>::iterator lru_it;
+};
+
+struct mpt_ctx_s {
+  int device = 0;
+  int sms = 0;
+  int engines = 0;
+  uint32_t* d_status = nullptr;       // device status word
+  unsigned long long* d_hash = nullptr;
+  mpt::EagerLane lane[MPT_MAX_PATHS];
+  cudaEvent_t fork = nullptr;
+  std::unordered_map<mpt::GraphKey, mpt_graph_s*, mpt::GraphKeyHash> cache;
+  std::list<mpt_graph_s*> lru;        // front = most recently used
+  std::unordered_set<mpt_graph_s*> live;  // every graph not yet released
+  size_t cache_cap = 64;
+  uint64_t stage_max = 8ull << 20;
+};
+
+namespace mpt {
+namespace {
+
+void graph_destroy_exec(mpt_graph_s* g) {
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->graph) cudaGraphDestroy(g->graph);
+  g->exec = nullptr;
+  g->graph = nullptr;
+  for (void* p : g->dev_allocs) cudaFree(p);
+  for (void* p : g->host_allocs) cudaFreeHost(p);
+  g->dev_allocs.clear();
+  g->host_allocs.clear();
+}
+
+void graph_unref(mpt_graph_s* g) {
+  if (--g->refs > 0) return;
+  if (g->ctx) g->ctx->live.erase(g);
+  graph_destroy_exec(g);
+  delete g;
+}
+
+void cache_drop(mpt_ctx_t c, mpt_graph_s* g) {
+  c->cache.erase(g->key);
+  c->lru.erase(g->lru_it);
+  g->cached = false;
+  graph_unref(g);
+}
+
+uint32_t default_ctas(mpt_ctx_t c, uint32_t kind, uint32_t variant) {
+  if (kind == MPT_PATH_ZC) return (uint32_t)c->sms;
+  return variant == MPT_SM_BULK ? (uint32_t)c->sms : 2u * (uint32_t)c->sms;
+}
+
+// Chunks of one path merged into maximal contiguous ranges (CONTIG plans give one).
+std::vector<RangeDesc> path_ranges(const mpt_plan_s* plan, uint32_t p) {
+  std::vector<RangeDesc> out;
+  for (uint32_t i = plan->first_chunk[p]; i < plan->first_chunk[p + 1]; ++i) {
+    const mpt_chunk& c = plan->chunks[i];
+    if (!out.empty() && out.back().src_off + out.back().bytes == c.offset) {
+      out.back().bytes += c.bytes;
+    } else {
+      out.push_back(RangeDesc{c.offset, c.offset, c.bytes, 0, 0});
+    }
+  }
+  return out;
+}
+
+void* kernel_fn(int variant) {
+  if (variant == 1) return reinterpret_cast<void*>(&k_sm_copy_bulk);
+  if (variant == 2) return reinterpret_cast<void*>(&k_zc_copy);
+  return reinterpret_cast<void*>(&k_sm_copy_vec);
+}
+
+// Build CopyArgs for up to kInlineRanges ranges; the bulk variant falls back to vec128
+// when a range's source and destination differ modulo 16.
+mpt_status prepare_copy(CopyArgs& a, int& variant, const void* src, void* dst, const RangeDesc* r, int n,
+                        uint32_t* status) {
+  int rc = make_copy_args(a, src, dst, r, n, variant, status);
+  if (rc == kArgsNeedVec) {
+    variant = 0;
+    rc = make_copy_args(a, src, dst, r, n, variant, status);
+  }
+  if (rc != kArgsOk) return fail(MPT_EINVAL, "copy of more than 2^31 tiles");
+  return MPT_OK;
+}
+
+dim3 grid_for(const CopyArgs& a, uint32_t ctas) {
+  return dim3(std::max<uint32_t>(1u, std::min<uint32_t>(ctas, a.ntiles)));
+}
+
+uint32_t block_for(int variant) { return variant == 1 ? (uint32_t)kBulkThreads : (uint32_t)kVecThreads; }
+size_t smem_for(int variant) { return variant == 1 ? (size_t)kBulkStages * kBulkStageBytes : 0; }
+
+mpt_status add_copy_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, cudaGraphNode_t* node,
+                         int variant, const CopyArgs& a, uint32_t ctas, mpt_graph_info& info) {
+  CopyArgs args = a;
+  void* params[] = {&args};
+  cudaKernelNodeParams kp{};
+  kp.func = kernel_fn(variant);
+  kp.gridDim = grid_for(a, ctas);
+  kp.blockDim = dim3(block_for(variant));
+  kp.sharedMemBytes = (unsigned)smem_for(variant);
+  kp.kernelParams = params;
+  CUDA_TRY(cudaGraphAddKernelNode(node, g, deps, ndeps, &kp));
+  info.kernel_nodes++;
+  return MPT_OK;
+}
+
+mpt_status launch_copy(cudaStream_t s, int variant, const CopyArgs& a, uint32_t ctas) {
+  void* kfn = kernel_fn(variant);
+  CopyArgs args = a;
+  void* params[] = {&args};
+  CUDA_TRY(cudaLaunchKernel(kfn, grid_for(a, ctas), dim3(block_for(variant)), params, smem_for(variant), s));
+  return MPT_OK;
+}
+
+// Kernel lane of a plan: every range of path p, 16 per launch / node.
+template <typename Emit>
+mpt_status for_each_copy(mpt_ctx_t c, const mpt_plan_s* plan, uint32_t p, const void* src, void* dst,
+                         Emit emit) {
+  const mpt_path_spec& spec = plan->paths[p];
+  std::vector<RangeDesc> ranges = path_ranges(plan, p);
+  int base_variant = spec.kind == MPT_PATH_ZC ? 2 : (spec.flags & MPT_SM_BULK ? 1 : 0);
+  for (size_t i = 0; i < ranges.size(); i += kInlineRanges) {
+    int n = (int)std::min<size_t>(kInlineRanges, ranges.size() - i);
+    int variant = base_variant;
+    CopyArgs a;
+    mpt_status st = prepare_copy(a, variant, src, dst, ranges.data() + i, n, c->d_status);
+    if (st != MPT_OK) return st;
+    if (a.ntiles == 0) continue;
+    uint32_t ctas = spec.ctas ? spec.ctas : default_ctas(c, spec.kind, (uint32_t)variant);
+    st = emit(variant, a, ctas);
+    if (st != MPT_OK) return st;
+  }
+  return MPT_OK;
+}
+
+// ---- graph construction (Algorithm 1 CreateGraph, Algorithm 2 node helpers) ---------------
+
+mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src, mpt_graph_s* g) {
+  mpt_graph_info& info = g->info;
+  const double t0 = now_us();
+  CUDA_TRY(cudaGraphCreate(&g->graph, 0));
+  const double t1 = now_us();
+  uint8_t* d8 = static_cast<uint8_t*>(dst);
+  const uint8_t* s8 = static_cast<const uint8_t*>(src);
+
+  for (uint32_t p = 0; p < plan->npaths; ++p) {
+    const uint32_t lo = plan->first_chunk[p], hi = plan->first_chunk[p + 1];
+    if (lo == hi) continue;
+    const mpt_path_spec& spec = plan->paths[p];
+    switch (spec.kind) {
+      case MPT_PATH_CE: {  // Algorithm 2 PeerToPeerCopy: one memcpy node per chunk
+        for (uint32_t i = lo; i < hi; ++i) {
+          const mpt_chunk& ch = plan->chunks[i];
+          cudaGraphNode_t n;
+          CUDA_TRY(cudaGraphAddMemcpyNode1D(&n, g->graph, nullptr, 0, d8 + ch.offset, s8 + ch.offset, ch.bytes,
+                                            cudaMemcpyDefault));
+          info.memcpy_nodes++;
+        }
+        break;
+      }
+      case MPT_PATH_SM:
+      case MPT_PATH_ZC: {
+        mpt_status st = for_each_copy(c, plan, p, src, dst, [&](int variant, const CopyArgs& a, uint32_t ctas) {
+          cudaGraphNode_t n;
+          return add_copy_node(g->graph, nullptr, 0, &n, variant, a, ctas, info);
+        });
+        if (st != MPT_OK) return st;
+        break;
+      }
+      case MPT_PATH_HS: {
+        const uint64_t cb = spec.chunk_bytes;
+        if (cb > c->stage_max)
+          return fail(MPT_EINVAL, "mpt_capture: staged chunk %llu exceeds the stage size %llu (MPT_STAGE_BYTES)",
+                      (unsigned long long)cb, (unsigned long long)c->stage_max);
+        if (plan->dir == MPT_D2D) {
+          // Algorithm 2 StageHostCopy: device -> pinned host slot -> device, two slots;
+          // hop two of chunk k after its hop one, hop one of chunk k+2 after hop two of k.
+          void* stage = nullptr;
+          CUDA_TRY(cudaHostAlloc(&stage, 2 * cb, cudaHostAllocPortable));
+          g->host_allocs.push_back(stage);
+          info.staging_bytes += 2 * cb;
+          uint8_t* st8 = static_cast<uint8_t*>(stage);
+          cudaGraphNode_t prev_hop2[2] = {nullptr, nullptr};
+          for (uint32_t i = lo; i < hi; ++i) {
+            const mpt_chunk& ch = plan->chunks[i];
+            const uint32_t slot = (i - lo) & 1u;
+            cudaGraphNode_t h1, h2;
+            CUDA_TRY(cudaGraphAddMemcpyNode1D(&h1, g->graph, prev_hop2[slot] ? &prev_hop2[slot] : nullptr,
+                                              prev_hop2[slot] ? 1 : 0, st8 + slot * cb, s8 + ch.offset, ch.bytes,
+                                              cudaMemcpyDeviceToHost));
+            CUDA_TRY(cudaGraphAddMemcpyNode1D(&h2, g->graph, &h1, 1, d8 + ch.offset, st8 + slot * cb, ch.bytes,
+                                              cudaMemcpyHostToDevice));
+            info.memcpy_nodes += 2;
+            prev_hop2[slot] = h2;
+          }
+        } else if (plan->dir == MPT_H2D) {
+          // Copy engine fills a device stage chunk by chunk; after each chunk a memset node
+          // raises its ready flag; one consumer kernel moves chunks out as flags rise.
+          const uint32_t nch = hi - lo;
+          std::vector<StageChunk> table(nch);
+          uint64_t stage_bytes = 0;
+          for (uint32_t k = 0; k < nch; ++k) {
+            const mpt_chunk& ch = plan->chunks[lo + k];
+            table[k] = StageChunk{ch.offset, stage_bytes, ch.bytes};
+            stage_bytes += (ch.bytes + 255) & ~255ull;
+          }
+          void* dstage = nullptr;
+          void* ctrl = nullptr;
+          const size_t flags_bytes = (size_t)nch * 2 * sizeof(uint32_t);
+          const size_t table_off = (flags_bytes + 255) & ~(size_t)255;
+          CUDA_TRY(cudaMalloc(&dstage, std::max<uint64_t>(stage_bytes, 256)));
+          g->dev_allocs.push_back(dstage);
+          CUDA_TRY(cudaMalloc(&ctrl, table_off + nch * sizeof(StageChunk)));
+          g->dev_allocs.push_back(ctrl);
+          CUDA_TRY(cudaMemset(ctrl, 0, flags_bytes));
+          CUDA_TRY(cudaMemcpy(static_cast<uint8_t*>(ctrl) + table_off, table.data(), nch * sizeof(StageChunk),
+                              cudaMemcpyHostToDevice));
+          info.staging_bytes += stage_bytes;
+          uint32_t* ready = static_cast<uint32_t*>(ctrl);
+          uint8_t* ds8 = static_cast<uint8_t*>(dstage);
+          for (uint32_t k = 0; k < nch; ++k) {
+            const mpt_chunk& ch = plan->chunks[lo + k];
+            cudaGraphNode_t h1, m;
+            CUDA_TRY(cudaGraphAddMemcpyNode1D(&h1, g->graph, nullptr, 0, ds8 + table[k].stage_off, s8 + ch.offset,
+                                              ch.bytes, cudaMemcpyHostToDevice));
+            cudaMemsetParams mp{};
+            mp.dst = ready + k;
+            mp.value = 1;
+            mp.elementSize = 4;
+            mp.width = 1;
+            mp.height = 1;
+            mp.pitch = 0;
+            CUDA_TRY(cudaGraphAddMemsetNode(&m, g->graph, &h1, 1, &mp));
+            info.memcpy_nodes++;
+            info.memset_nodes++;
+          }
+          StageArgs sa{};
+          sa.stage = ds8;
+          sa.dst = d8;
+          sa.chunks = reinterpret_cast<const StageChunk*>(static_cast<uint8_t*>(ctrl) + table_off);
+          sa.ready = ready;
+          sa.done = ready + nch;
+          sa.nchunks = nch;
+          const uint64_t tile = kVecTileVecs * 16;
+          sa.tiles_per_chunk = (uint32_t)((cb + tile - 1) / tile);
+          sa.status = c->d_status;
+          sa.timeout_ns = kDefaultTimeoutNs;
+          void* params[] = {&sa};
+          cudaKernelNodeParams kp{};
+          kp.func = reinterpret_cast<void*>(&k_stage_consume);
+          const uint32_t ctas = spec.ctas ? spec.ctas : kDefaultConsumerCtas;
+          kp.gridDim = dim3(std::min<uint32_t>(ctas, nch * sa.tiles_per_chunk));
+          kp.blockDim = dim3(kVecThreads);
+          kp.kernelParams = params;
+          cudaGraphNode_t kn;
+          CUDA_TRY(cudaGraphAddKernelNode(&kn, g->graph, nullptr, 0, &kp));
+          info.kernel_nodes++;
+        } else {
+          // Device-to-host through a two-slot device stage: SM copy into the slot, then a
+          // copy-engine hop to the host; a slot is refilled after its previous hop two.
+          void* dstage = nullptr;
+          CUDA_TRY(cudaMalloc(&dstage, 2 * cb));
+          g->dev_allocs.push_back(dstage);
+          info.staging_bytes += 2 * cb;
+          uint8_t* ds8 = static_cast<uint8_t*>(dstage);
+          cudaGraphNode_t prev_hop2[2] = {nullptr, nullptr};
+          for (uint32_t i = lo; i < hi; ++i) {
+            const mpt_chunk& ch = plan->chunks[i];
+            const uint32_t slot = (i - lo) & 1u;
+            RangeDesc r{ch.offset, slot * cb, ch.bytes, 0, 0};
+            int variant = 0;
+            CopyArgs a;
+            mpt_status st = prepare_copy(a, variant, src, ds8, &r, 1, c->d_status);
+            if (st != MPT_OK) return st;
+            cudaGraphNode_t h1, h2;
+            st = add_copy_node(g->graph, prev_hop2[slot] ? &prev_hop2[slot] : nullptr, prev_hop2[slot] ? 1 : 0, &h1,
+                               variant, a, spec.ctas ? spec.ctas : default_ctas(c, MPT_PATH_SM, 0), info);
+            if (st != MPT_OK) return st;
+            CUDA_TRY(cudaGraphAddMemcpyNode1D(&h2, g->graph, &h1, 1, d8 + ch.offset, ds8 + slot * cb, ch.bytes,
+                                              cudaMemcpyDeviceToHost));
+            info.memcpy_nodes++;
+            prev_hop2[slot] = h2;
+          }
+        }
+        break;
+      }
+      default:
+        return fail(MPT_EINVAL, "mpt_capture: unknown path kind %u", spec.kind);
+    }
+  }
+  const double t2 = now_us();
+  size_t nodes = 0;
+  CUDA_TRY(cudaGraphGetNodes(g->graph, nullptr, &nodes));
+  info.nodes = (uint32_t)nodes;
+  if (nodes > 0) CUDA_TRY(cudaGraphInstantiate(&g->exec, g->graph, 0));
+  const double t3 = now_us();
+  info.create_us = t1 - t0;
+  info.construct_us = t2 - t1;
+  info.instantiate_us = t3 - t2;
+  return MPT_OK;
+}
+
+mpt_status check_pointers(mpt_ctx_t c, uint32_t dir, const void* dst, const void* src) {
+  const MemKind ks = classify(src, c->device), kd = classify(dst, c->device);
+  const MemKind want_s = dir == MPT_H2D ? kMemHost : kMemDevice;
+  const MemKind want_d = dir == MPT_D2H ? kMemHost : kMemDevice;
+  if (ks != want_s)
+    return fail(MPT_EINVAL, "source %p is not %s memory", src,
+                want_s == kMemHost ? "page-locked host" : "device (this context's GPU)");
+  if (kd != want_d)
+    return fail(MPT_EINVAL, "destination %p is not %s memory", dst,
+                want_d == kMemHost ? "page-locked host" : "device (this context's GPU)");
+  return MPT_OK;
+}
+
+// ---- eager engine (Sec. 4.3 static runtime pipelining; Sec. 4.5 contention avoidance) ------
+
+mpt_status grow_host(EagerLane& L, uint64_t bytes) {
+  if (L.host_stage_bytes >= bytes) return MPT_OK;
+  if (L.host_stage) CUDA_TRY(cudaFreeHost(L.host_stage));
+  L.host_stage = nullptr;
+  L.host_stage_bytes = 0;
+  CUDA_TRY(cudaHostAlloc(&L.host_stage, bytes, cudaHostAllocPortable));
+  L.host_stage_bytes = bytes;
+  return MPT_OK;
+}
+
+mpt_status grow_dev(EagerLane& L, uint64_t bytes) {
+  if (L.dev_stage_bytes >= bytes) return MPT_OK;
+  if (L.dev_stage) CUDA_TRY(cudaFree(L.dev_stage));
+  L.dev_stage = nullptr;
+  L.dev_stage_bytes = 0;
+  CUDA_TRY(cudaMalloc(&L.dev_stage, bytes));
+  L.dev_stage_bytes = bytes;
+  return MPT_OK;
+}
+
+mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src, cudaStream_t user) {
+  if (plan->nbytes == 0) return MPT_OK;
+  CUDA_TRY(cudaEventRecord(c->fork, user));
+  uint8_t* d8 = static_cast<uint8_t*>(dst);
+  const uint8_t* s8 = static_cast<const uint8_t*>(src);
+  for (uint32_t p = 0; p < plan->npaths; ++p) {
+    const uint32_t lo = plan->first_chunk[p], hi = plan->first_chunk[p + 1];
+    if (lo == hi) continue;
+    EagerLane& L = c->lane[p];
+    const mpt_path_spec& spec = plan->paths[p];
+    CUDA_TRY(cudaStreamWaitEvent(L.s[0], c->fork, 0));
+    cudaStream_t last = L.s[0];
+    switch (spec.kind) {
+      case MPT_PATH_CE:
+        for (uint32_t i = lo; i < hi; ++i) {
+          const mpt_chunk& ch = plan->chunks[i];
+          CUDA_TRY(cudaMemcpyAsync(d8 + ch.offset, s8 + ch.offset, ch.bytes, cudaMemcpyDefault, L.s[0]));
+        }
+        break;
+      case MPT_PATH_SM:
+      case MPT_PATH_ZC: {
+        mpt_status st = for_each_copy(c, plan, p, src, dst, [&](int variant, const CopyArgs& a, uint32_t ctas) {
+          return launch_copy(L.s[0], variant, a, ctas);
+        });
+        if (st != MPT_OK) return st;
+        break;
+      }
+      case MPT_PATH_HS: {
+        const uint64_t cb = spec.chunk_bytes;
+        if (cb > c->stage_max)
+          return fail(MPT_EINVAL, "mpt_launch_eager: staged chunk %llu exceeds the stage size %llu",
+                      (unsigned long long)cb, (unsigned long long)c->stage_max);
+        CUDA_TRY(cudaStreamWaitEvent(L.s[1], c->fork, 0));
+        uint8_t* stage;
+        if (plan->dir == MPT_D2D) {
+          mpt_status st = grow_host(L, 2 * cb);
+          if (st != MPT_OK) return st;
+          stage = static_cast<uint8_t*>(L.host_stage);
+        } else {
+          mpt_status st = grow_dev(L, 2 * cb);
+          if (st != MPT_OK) return st;
+          stage = static_cast<uint8_t*>(L.dev_stage);
+        }
+        for (uint32_t i = lo; i < hi; ++i) {
+          const mpt_chunk& ch = plan->chunks[i];
+          const uint32_t slot = (i - lo) & 1u;
+          uint8_t* sl = stage + slot * cb;
+          // hop one may refill this slot only after the slot's previous hop two
+          CUDA_TRY(cudaStreamWaitEvent(L.s[0], L.hop2[slot], 0));
+          if (plan->dir == MPT_D2H) {
+            RangeDesc r{ch.offset, 0, ch.bytes, 0, 0};
+            int variant = 0;
+            CopyArgs a;
+            mpt_status st = prepare_copy(a, variant, src, sl, &r, 1, c->d_status);
+            if (st != MPT_OK) return st;
+            st = launch_copy(L.s[0], variant, a, spec.ctas ? spec.ctas : default_ctas(c, MPT_PATH_SM, 0));
+            if (st != MPT_OK) return st;
+          } else {
+            CUDA_TRY(cudaMemcpyAsync(sl, s8 + ch.offset, ch.bytes, cudaMemcpyDefault, L.s[0]));
+          }
+          CUDA_TRY(cudaEventRecord(L.hop1[slot], L.s[0]));
+          CUDA_TRY(cudaStreamWaitEvent(L.s[1], L.hop1[slot], 0));
+          if (plan->dir == MPT_H2D) {
+            RangeDesc r{0, ch.offset, ch.bytes, 0, 0};
+            int variant = 0;
+            CopyArgs a;
+            mpt_status st = prepare_copy(a, variant, sl, dst, &r, 1, c->d_status);
+            if (st != MPT_OK) return st;
+            st = launch_copy(L.s[1], variant, a, spec.ctas ? spec.ctas : default_ctas(c, MPT_PATH_SM, 0));
+            if (st != MPT_OK) return st;
+          } else {
+            CUDA_TRY(cudaMemcpyAsync(d8 + ch.offset, sl, ch.bytes, cudaMemcpyDefault, L.s[1]));
+          }
+          CUDA_TRY(cudaEventRecord(L.hop2[slot], L.s[1]));
+        }
+        last = L.s[1];
+        break;
+      }
+      default:
+        return fail(MPT_EINVAL, "unknown path kind %u", spec.kind);
+    }
+    CUDA_TRY(cudaEventRecord(L.done, last));
+    CUDA_TRY(cudaStreamWaitEvent(user, L.done, 0));
+  }
+  return MPT_OK;
+}
+
+}  // namespace
+}  // namespace mpt
+
+using namespace mpt;
+
+extern "C" {
+
+const char* mpt_version(void) { return "mpt 0.1 (sm_103a)"; }
+
+const char* mpt_last_error(void) { return last_error_cstr(); }
+
+mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out) {
+  if (!out) return fail(MPT_EINVAL, "mpt_ctx_create: out is NULL");
+  *out = nullptr;
+  int n = 0;
+  CUDA_TRY(cudaGetDeviceCount(&n));
+  if (device < 0 || device >= n) return fail(MPT_EINVAL, "mpt_ctx_create: device %d of %d", device, n);
+  CUDA_TRY(cudaSetDevice(device));
+  mpt_ctx_s* c = new mpt_ctx_s;
+  c->device = device;
+  auto bail = [&](mpt_status st) {
+    mpt_ctx_destroy(c);
+    return st;
+  };
+  if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->engines, cudaDevAttrAsyncEngineCount, device) != cudaSuccess)
+    return bail(fail(MPT_ECUDA, "mpt_ctx_create: device attributes unavailable"));
+  void* words = nullptr;
+  if (cudaMalloc(&words, 256) != cudaSuccess) return bail(fail(MPT_ENOMEM, "mpt_ctx_create: status word"));
+  c->d_status = static_cast<uint32_t*>(words);
+  c->d_hash = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(words) + 128);
+  if (cudaMemset(words, 0, 256) != cudaSuccess) return bail(fail(MPT_ECUDA, "mpt_ctx_create: memset"));
+  for (uint32_t p = 0; p < MPT_MAX_PATHS; ++p) {
+    EagerLane& L = c->lane[p];
+    for (int i = 0; i < 2; ++i) {
+      if (cudaStreamCreateWithFlags(&L.s[i], cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&L.hop1[i], cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&L.hop2[i], cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(MPT_ECUDA, "mpt_ctx_create: streams/events"));
+    }
+    if (cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess)
+      return bail(fail(MPT_ECUDA, "mpt_ctx_create: events"));
+  }
+  if (cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess)
+    return bail(fail(MPT_ECUDA, "mpt_ctx_create: events"));
+  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_sm_copy_bulk),
+                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)(kBulkStages * kBulkStageBytes)) != cudaSuccess)
+    return bail(fail(MPT_ECUDA, "mpt_ctx_create: bulk kernel shared memory"));
+  c->cache_cap = (size_t)std::max<uint64_t>(1, env_u64("MPT_GRAPH_CACHE", 64));
+  c->stage_max = std::max<uint64_t>(4096, env_u64("MPT_STAGE_BYTES", 8ull << 20));
+  (void)tune_file;
+  *out = c;
+  return MPT_OK;
+}
+
+mpt_status mpt_ctx_destroy(mpt_ctx_t c) {
+  if (!c) return MPT_OK;
+  cudaSetDevice(c->device);
+  cudaDeviceSynchronize();
+  // Drop the cache's references; graphs the caller still holds lose their executable.
+  while (!c->lru.empty()) cache_drop(c, c->lru.front());
+  for (mpt_graph_s* g : c->live) {
+    graph_destroy_exec(g);
+    g->ctx = nullptr;
+  }
+  c->live.clear();
+  for (uint32_t p = 0; p < MPT_MAX_PATHS; ++p) {
+    EagerLane& L = c->lane[p];
+    for (int i = 0; i < 2; ++i) {
+      if (L.s[i]) cudaStreamDestroy(L.s[i]);
+      if (L.hop1[i]) cudaEventDestroy(L.hop1[i]);
+      if (L.hop2[i]) cudaEventDestroy(L.hop2[i]);
+    }
+    if (L.done) cudaEventDestroy(L.done);
+    if (L.host_stage) cudaFreeHost(L.host_stage);
+    if (L.dev_stage) cudaFree(L.dev_stage);
+  }
+  if (c->fork) cudaEventDestroy(c->fork);
+  if (c->d_status) cudaFree(c->d_status);
+  delete c;
+  return MPT_OK;
+}
+
+mpt_status mpt_ctx_status(mpt_ctx_t c, uint32_t* site) {
+  if (!c) return fail(MPT_EINVAL, "mpt_ctx_status: NULL context");
+  CUDA_TRY(cudaSetDevice(c->device));
+  CUDA_TRY(cudaDeviceSynchronize());
+  uint32_t w = 0;
+  CUDA_TRY(cudaMemcpy(&w, c->d_status, sizeof w, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemset(c->d_status, 0, sizeof w));
+  if (site) *site = w >> 8;
+  const uint32_t code = w & 0xffu;
+  if (code == 0) return MPT_OK;
+  return fail((mpt_status)code, "device wait gave up (site %u)", w >> 8);
+}
+
+mpt_status mpt_capture(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void* src, mpt_graph_t* out) {
+  if (!c || !plan || !out) return fail(MPT_EINVAL, "mpt_capture: NULL argument");
+  *out = nullptr;
+  CUDA_TRY(cudaSetDevice(c->device));
+  if (plan->nbytes > 0) {
+    mpt_status st = check_pointers(c, plan->dir, dst, src);
+    if (st != MPT_OK) return st;
+  }
+  GraphKey key{(uint64_t)(uintptr_t)src, (uint64_t)(uintptr_t)dst, plan->nbytes, plan->dir, plan->hash};
+  auto it = c->cache.find(key);
+  if (it != c->cache.end()) {
+    mpt_graph_s* g = it->second;
+    c->lru.splice(c->lru.begin(), c->lru, g->lru_it);
+    g->refs++;
+    *out = g;
+    return MPT_OK;
+  }
+  mpt_graph_s* g = new mpt_graph_s;
+  g->ctx = c;
+  g->key = key;
+  g->src_lo = key.src;
+  g->src_hi = key.src + plan->nbytes;
+  g->dst_lo = key.dst;
+  g->dst_hi = key.dst + plan->nbytes;
+  mpt_status st = build_graph(c, plan, dst, src, g);
+  if (st != MPT_OK) {
+    graph_destroy_exec(g);
+    delete g;
+    return st;
+  }
+  while (c->cache.size() >= c->cache_cap && !c->lru.empty()) cache_drop(c, c->lru.back());
+  g->refs = 2;  // the cache's and the caller's
+  g->cached = true;
+  c->lru.push_front(g);
+  g->lru_it = c->lru.begin();
+  c->cache.emplace(key, g);
+  c->live.insert(g);
+  *out = g;
+  return MPT_OK;
+}
+
+mpt_status mpt_launch(mpt_graph_t g, void* stream) {
+  if (!g) return fail(MPT_EINVAL, "mpt_launch: NULL graph");
+  if (!g->ctx) return fail(MPT_EINVAL, "mpt_launch: the graph's context was destroyed");
+  if (!g->exec) return MPT_OK;  // empty message: nothing to move
+  CUDA_TRY(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
+  return MPT_OK;
+}
+
+mpt_status mpt_graph_get_info(mpt_graph_t g, mpt_graph_info* out) {
+  if (!g || !out) return fail(MPT_EINVAL, "mpt_graph_get_info: NULL argument");
+  *out = g->info;
+  return MPT_OK;
+}
+
+mpt_status mpt_graph_release(mpt_graph_t g) {
+  if (!g) return MPT_OK;
+  graph_unref(g);
+  return MPT_OK;
+}
+
+mpt_status mpt_graph_evict(mpt_ctx_t c, const void* ptr, uint32_t* n) {
+  if (!c) return fail(MPT_EINVAL, "mpt_graph_evict: NULL context");
+  const uint64_t a = (uint64_t)(uintptr_t)ptr;
+  uint32_t dropped = 0;
+  for (auto it = c->lru.begin(); it != c->lru.end();) {
+    mpt_graph_s* g = *it++;
+    const bool hit = (a >= g->src_lo && a < g->src_hi) || (a >= g->dst_lo && a < g->dst_hi) ||
+                     (a == g->src_lo) || (a == g->dst_lo);
+    if (hit) {
+      cache_drop(c, g);
+      dropped++;
+    }
+  }
+  if (n) *n = dropped;
+  return MPT_OK;
+}
+
+mpt_status mpt_launch_eager(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void* src, void* stream) {
+  if (!c || !plan) return fail(MPT_EINVAL, "mpt_launch_eager: NULL argument");
+  CUDA_TRY(cudaSetDevice(c->device));
+  if (plan->nbytes > 0) {
+    mpt_status st = check_pointers(c, plan->dir, dst, src);
+    if (st != MPT_OK) return st;
+  }
+  return eager(c, plan, dst, src, static_cast<cudaStream_t>(stream));
+}
+
+mpt_status mpt_sm_copy(mpt_ctx_t c, void* dst, const void* src, uint64_t nbytes, uint32_t variant, uint32_t ctas,
+                       void* stream) {
+  if (!c) return fail(MPT_EINVAL, "mpt_sm_copy: NULL context");
+  if (variant > MPT_SM_BULK) return fail(MPT_EINVAL, "mpt_sm_copy: unknown variant %u", variant);
+  if (nbytes == 0) return MPT_OK;
+  if (!dst || !src) return fail(MPT_EINVAL, "mpt_sm_copy: NULL pointer");
+  CUDA_TRY(cudaSetDevice(c->device));
+  const MemKind ks = classify(src, c->device), kd = classify(dst, c->device);
+  if (ks == kMemOther || kd == kMemOther)
+    return fail(MPT_EINVAL, "mpt_sm_copy: pointers must be device or page-locked host memory");
+  const bool host = ks == kMemHost || kd == kMemHost;
+  RangeDesc r{0, 0, nbytes, 0, 0};
+  int v = host ? 2 : (int)variant;
+  CopyArgs a;
+  mpt_status st = prepare_copy(a, v, src, dst, &r, 1, c->d_status);
+  if (st != MPT_OK) return st;
+  const uint32_t g = ctas ? ctas : default_ctas(c, host ? MPT_PATH_ZC : MPT_PATH_SM, (uint32_t)v);
+  return launch_copy(static_cast<cudaStream_t>(stream), v, a, g);
+}
+
+mpt_status mpt_hash_device(mpt_ctx_t c, const void* ptr, uint64_t nbytes, void* stream, uint64_t* out) {
+  if (!c || !out) return fail(MPT_EINVAL, "mpt_hash_device: NULL argument");
+  if (nbytes > 0 && !ptr) return fail(MPT_EINVAL, "mpt_hash_device: NULL pointer");
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaMemsetAsync(c->d_hash, 0, sizeof(unsigned long long), s));
+  const uint64_t words = (nbytes + 7) / 8;
+  const uint32_t blocks = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(4ull * c->sms, (words + 255) / 256));
+  k_hash<<<blocks, 256, 0, s>>>(static_cast<const uint8_t*>(ptr), nbytes, c->d_hash);
+  CUDA_TRY(cudaGetLastError());
+  unsigned long long h = 0;
+  CUDA_TRY(cudaMemcpyAsync(&h, c->d_hash, sizeof h, cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  *out = h;
+  return MPT_OK;
+}
+
+mpt_status mpt_host_alloc(uint64_t nbytes, void** out) {
+  if (!out) return fail(MPT_EINVAL, "mpt_host_alloc: out is NULL");
+  *out = nullptr;
+  if (cudaHostAlloc(out, std::max<uint64_t>(nbytes, 1), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MPT_ENOMEM, "mpt_host_alloc: %llu bytes", (unsigned long long)nbytes);
+  }
+  return MPT_OK;
+}
+
+mpt_status mpt_host_free(void* p) {
+  if (p) CUDA_TRY(cudaFreeHost(p));
+  return MPT_OK;
+}
+
+}  // extern "C"
+
+namespace mpt {
+
+// Default path set and chunk sizes until a tuned choice exists for this size bucket:
+// device-to-device on the SM copy kernel, host transfers on the copy engine, 4 MiB chunks.
+mpt_status tuner_fill(mpt_ctx_t ctx, uint64_t nbytes, uint32_t dir, uint32_t align, mpt_path_spec* specs,
+                      uint32_t* npaths, bool whole_set) {
+  (void)ctx;
+  (void)nbytes;
+  if (dir > MPT_D2H) return fail(MPT_EINVAL, "mpt_plan: unknown direction %u", dir);
+  const uint64_t chunk = ((4ull << 20) + align - 1) / align * align;
+  if (whole_set) {
+    specs[0] = mpt_path_spec{dir == MPT_D2D ? (uint32_t)MPT_PATH_SM : (uint32_t)MPT_PATH_CE, MPT_SHARE_ONE, chunk, 0, 0};
+    *npaths = 1;
+    return MPT_OK;
+  }
+  for (uint32_t p = 0; p < *npaths; ++p)
+    if (specs[p].chunk_bytes == 0) specs[p].chunk_bytes = chunk;
+  return MPT_OK;
+}
+
+}  // namespace mpt

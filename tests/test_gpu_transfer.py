@@ -1,0 +1,211 @@
+"""GPU parity: every transfer path, graph and eager, against the oracle (bit-exact bytes,
+identical plans, identical digests).  Calls go through the C ABI via the binding."""
+import numpy as np
+import pytest
+
+import paper_2604_22228_gb300 as mpt
+import payload
+from oracle import planner as P
+from oracle import transfer as T
+
+from gpu_util import Buf, seeded
+
+pytestmark = pytest.mark.gpu
+MiB = 1 << 20
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    torch.cuda.init()
+    from paper_2604_22228_gb300 import build
+    build.build()
+    c = mpt.mpt_ctx_create(0)
+    yield c
+    st, site = mpt.mpt_ctx_status(c)
+    mpt.mpt_ctx_destroy(c)
+    assert st == mpt.MPT_OK, f"device status {st} at site {site}"
+
+
+def run_transfer(ctx, n, direction, specs, kind="u8", seed=1, src_off=0, dst_off=0, layout=P.CONTIG, align=16,
+                 mode="graph", replays=2):
+    src_where = "host" if direction == P.H2D else "dev"
+    dst_where = "host" if direction == P.D2H else "dev"
+    src = Buf(n, src_where, src_off)
+    dst = Buf(n, dst_where, dst_off)
+    data = seeded(kind, seed, n)
+    src.fill(data)
+    plan = mpt.mpt_plan(ctx, n, direction, specs, align, layout)
+    try:
+        got_plan = [P.Chunk(*c) for c in mpt.mpt_plan_chunks(plan)]
+        resolved = [(p["kind"], p["share"], p["chunk_bytes"]) for p in mpt.mpt_plan_paths(plan)]
+        assert got_plan == P.plan(n, direction, resolved, align, layout)
+        import torch
+        s = torch.cuda.current_stream()
+        info = None
+        for _ in range(replays):
+            if mode == "graph":
+                g = mpt.mpt_capture(ctx, plan, dst.ptr, src.ptr)
+                info = mpt.mpt_graph_get_info(g)
+                mpt.mpt_launch(g, s)
+                mpt.mpt_graph_release(g)
+            else:
+                mpt.mpt_launch_eager(ctx, plan, dst.ptr, src.ptr, s)
+        torch.cuda.synchronize()
+    finally:
+        mpt.mpt_plan_destroy(plan)
+    expect = T.copy(data)
+    out = dst.numpy()
+    assert np.array_equal(out, expect), f"first mismatch at {int(np.argmax(out != expect))}"
+    assert dst.guards_intact(), "bytes outside the destination were written"
+    st, site = mpt.mpt_ctx_status(ctx)
+    assert st == mpt.MPT_OK, f"device status {st} site {site}"
+    return info, dst
+
+
+SIZES = [1, 15, 16, 17, 255, 4096, 65536 + 3, MiB + 5, 3 * 48 * 1024 + 7, 5 * MiB + 11]
+OFFSETS = [(0, 0), (1, 1), (3, 3), (8, 8), (15, 15), (0, 1), (5, 9), (16, 0)]
+
+
+@pytest.mark.parametrize("variant", [mpt.MPT_SM_VEC128, mpt.MPT_SM_BULK])
+def test_sm_copy_kernel_sizes_and_alignment(ctx, variant):
+    import torch
+    for n in SIZES:
+        for so, do in OFFSETS:
+            src, dst = Buf(n, "dev", so), Buf(n, "dev", do)
+            data = seeded("u8", n * 31 + so, n)
+            src.fill(data)
+            mpt.mpt_sm_copy(ctx, dst.ptr, src.ptr, n, variant, 0, torch.cuda.current_stream())
+            out = dst.numpy()
+            assert np.array_equal(out, data), (variant, n, so, do, int(np.argmax(out != data)))
+            assert dst.guards_intact(), (variant, n, so, do)
+    assert mpt.mpt_ctx_status(ctx)[0] == mpt.MPT_OK
+
+
+@pytest.mark.parametrize("ctas", [1, 3, 152, 1000])
+def test_sm_copy_kernel_grid_sizes(ctx, ctas):
+    import torch
+    n = 7 * MiB + 333
+    for variant in (mpt.MPT_SM_VEC128, mpt.MPT_SM_BULK):
+        src, dst = Buf(n, "dev"), Buf(n, "dev")
+        data = seeded("f32", 9, n)
+        src.fill(data)
+        mpt.mpt_sm_copy(ctx, dst.ptr, src.ptr, n, variant, ctas, torch.cuda.current_stream())
+        assert np.array_equal(dst.numpy(), data) and dst.guards_intact()
+
+
+def test_copy64_graph_two_paths(ctx):
+    # 64 MiB u8 payload, copy engine + SM kernel at 50/50, 4 MiB chunks, one graph.
+    specs = [(P.CE, 32768, 4 * MiB), (P.SM, 32768, 4 * MiB)]
+    info, dst = run_transfer(ctx, 64 * MiB, P.D2D, specs, "u8", payload.SEED_COPY64)
+    assert info["memcpy_nodes"] == 8 and info["kernel_nodes"] == 1 and info["nodes"] == 9
+    assert mpt.mpt_hash_device(ctx, dst.ptr, dst.n) == T.hash64(seeded("u8", payload.SEED_COPY64, 64 * MiB))
+
+
+@pytest.mark.parametrize("mode", ["graph", "eager"])
+@pytest.mark.parametrize("pathset", ["ce", "sm", "sm_bulk", "ce+sm", "hs", "ce+sm+hs"])
+def test_d2d_paths(ctx, mode, pathset):
+    sets = {
+        "ce": [(P.CE, 65536, MiB)],
+        "sm": [(P.SM, 65536, MiB)],
+        "sm_bulk": [(P.SM, 65536, MiB, 0, mpt.MPT_SM_BULK)],
+        "ce+sm": [(P.CE, 20000, MiB), (P.SM, 45536, 256 * 1024)],
+        "hs": [(P.HS, 65536, MiB)],
+        "ce+sm+hs": [(P.CE, 30000, MiB), (P.SM, 30000, MiB, 0, mpt.MPT_SM_BULK), (P.HS, 5536, 512 * 1024)],
+    }
+    for n in (8, 4096, 3 * MiB + 48, 9 * MiB + 5):
+        run_transfer(ctx, n, P.D2D, sets[pathset], "f32", payload.SEED_D2D_SWEEP + n, mode=mode)
+
+
+@pytest.mark.parametrize("mode", ["graph", "eager"])
+@pytest.mark.parametrize("direction", [P.H2D, P.D2H])
+@pytest.mark.parametrize("pathset", ["ce", "zc", "hs", "all"])
+def test_host_paths(ctx, mode, direction, pathset):
+    sets = {
+        "ce": [(P.CE, 65536, MiB)],
+        "zc": [(P.ZC, 65536, MiB)],
+        "hs": [(P.HS, 65536, MiB)],
+        "all": [(P.CE, 30000, MiB), (P.ZC, 20000, 2 * MiB), (P.HS, 15536, 512 * 1024)],
+    }
+    for n in (4096, 5 * MiB + 4, 11 * MiB + 7):
+        run_transfer(ctx, n, direction, sets[pathset], "u32", payload.SEED_HOST_SWEEP + n, mode=mode)
+
+
+@pytest.mark.parametrize("mode", ["graph", "eager"])
+def test_interleave_layout(ctx, mode):
+    specs = [(P.CE, 21845, 64 * 1024), (P.SM, 21845, 128 * 1024), (P.HS, 21846, 64 * 1024)]
+    for n in (100, 1 << 20, 5 * MiB + 13):
+        run_transfer(ctx, n, P.D2D, specs, "bf16", 77 + n, layout=P.INTERLEAVE, mode=mode)
+    specs = [(P.CE, 30000, 64 * 1024), (P.ZC, 35536, 32 * 1024)]
+    run_transfer(ctx, 3 * MiB + 9, P.H2D, specs, "u32", 5, layout=P.INTERLEAVE, mode=mode)
+
+
+def test_unaligned_buffers_multipath(ctx):
+    specs = [(P.CE, 32768, MiB), (P.SM, 32768, MiB, 0, mpt.MPT_SM_BULK)]
+    for so, do in [(1, 1), (3, 7), (8, 0)]:
+        run_transfer(ctx, 4 * MiB + 3, P.D2D, specs, "u8", so * 10 + do, src_off=so, dst_off=do)
+    run_transfer(ctx, 2 * MiB + 3, P.H2D, [(P.CE, 32768, MiB), (P.ZC, 32768, MiB)], "u8", 3, src_off=5, dst_off=9)
+
+
+def test_empty_and_tiny_messages(ctx):
+    for n in (0, 1, 7):
+        run_transfer(ctx, n, P.D2D, [(P.CE, 32768, 16), (P.SM, 32768, 16)], "u8", n)
+    plan = mpt.mpt_plan(ctx, 0, P.D2D, [(P.SM, 65536, 16)])
+    g = mpt.mpt_capture(ctx, plan, 0, 0)
+    assert mpt.mpt_graph_get_info(g)["nodes"] == 0
+    mpt.mpt_launch(g, None)
+    mpt.mpt_graph_release(g)
+    mpt.mpt_plan_destroy(plan)
+
+
+def test_hash_matches_oracle(ctx):
+    for n in (0, 1, 7, 8, 9, 4096, MiB + 3):
+        for off in (0, 1, 8):
+            b = Buf(n, "dev", off)
+            data = seeded("u8", 1000 + n + off, n)
+            b.fill(data)
+            assert mpt.mpt_hash_device(ctx, b.ptr, n) == T.hash64(data), (n, off)
+
+
+def test_graph_cache_hits_and_eviction(ctx):
+    import torch
+    n = MiB
+    src, dst = Buf(n, "dev"), Buf(n, "dev")
+    plan = mpt.mpt_plan(ctx, n, P.D2D, [(P.CE, 32768, 256 * 1024), (P.SM, 32768, 256 * 1024)])
+    g1 = mpt.mpt_capture(ctx, plan, dst.ptr, src.ptr)
+    g2 = mpt.mpt_capture(ctx, plan, dst.ptr, src.ptr)
+    assert g1 == g2
+    g3 = mpt.mpt_capture(ctx, plan, dst.ptr + 16, src.ptr)  # different address: new graph
+    assert g3 != g1
+    assert mpt.mpt_graph_evict(ctx, dst.ptr + 100) == 2
+    # held references survive eviction
+    src.fill(seeded("u8", 4, n))
+    mpt.mpt_launch(g1, torch.cuda.current_stream())
+    assert np.array_equal(dst.numpy(), seeded("u8", 4, n))
+    for g in (g1, g2, g3):
+        mpt.mpt_graph_release(g)
+    mpt.mpt_plan_destroy(plan)
+
+
+def test_pointer_kind_checked(ctx):
+    n = 4096
+    host, dev = Buf(n, "host"), Buf(n, "dev")
+    plan = mpt.mpt_plan(ctx, n, P.D2D, [(P.SM, 65536, 4096)])
+    with pytest.raises(mpt.MptError) as e:
+        mpt.mpt_capture(ctx, plan, dev.ptr, host.ptr)
+    assert e.value.status == mpt.MPT_EINVAL
+    mpt.mpt_plan_destroy(plan)
+    plan = mpt.mpt_plan(ctx, n, P.H2D, [(P.CE, 65536, 4096)])
+    with pytest.raises(mpt.MptError):
+        mpt.mpt_capture(ctx, plan, dev.ptr, dev.ptr)
+    mpt.mpt_plan_destroy(plan)
+
+
+def test_staged_chunk_above_stage_size_rejected(ctx):
+    n = 32 * MiB
+    src, dst = Buf(n, "dev"), Buf(n, "dev")
+    plan = mpt.mpt_plan(ctx, n, P.D2D, [(P.HS, 65536, 16 * MiB)])
+    with pytest.raises(mpt.MptError) as e:
+        mpt.mpt_capture(ctx, plan, dst.ptr, src.ptr)
+    assert e.value.status == mpt.MPT_EINVAL
+    mpt.mpt_plan_destroy(plan)
