@@ -65,6 +65,9 @@ typedef enum {
 typedef enum { MPT_D2D = 0, MPT_H2D = 1, MPT_D2H = 2 } mpt_dir;
 typedef enum { MPT_PATH_CE = 1, MPT_PATH_SM = 2, MPT_PATH_HS = 4, MPT_PATH_ZC = 8 } mpt_path_kind;
 typedef enum { MPT_LAYOUT_CONTIG = 0, MPT_LAYOUT_INTERLEAVE = 1 } mpt_layout;
+/* OR into mpt_plan's layout to ask the tuner for its eager-mode (non-graph) choice. */
+#define MPT_PLAN_EAGER 0x100u
+typedef enum { MPT_MODE_GRAPH = 0, MPT_MODE_EAGER = 1 } mpt_mode;
 
 /* mpt_path_spec.flags for SM-kernel paths: which copy kernel variant to run. */
 #define MPT_SM_VEC128 0u   /* 128-bit vector loads/stores, grid-stride over tiles */
@@ -117,6 +120,26 @@ typedef struct {
   uint64_t staging_bytes;  /* staging memory this graph owns */
 } mpt_graph_info;
 
+/* Cost model of one path kind: per-chunk issue latency and bandwidth (the staged path's
+ * two hops have separate bandwidths; other kinds ignore beta2_Bps). */
+typedef struct {
+  uint64_t alpha_ps;
+  uint64_t beta_Bps;
+  uint64_t beta2_Bps;
+} mpt_path_model;
+
+/* Cost model of a plan (stated by this library; the paper tunes offline by exhaustive
+ * search over link bandwidths and latencies, Sec. 4.4, without printing a model):
+ * launch latency, HBM bandwidth, host-link bandwidth per direction, and one
+ * mpt_path_model per path kind.  Bandwidths in bytes/s, times in picoseconds. */
+typedef struct {
+  uint64_t launch_ps;
+  uint64_t hbm_Bps;
+  uint64_t link_h2d_Bps;
+  uint64_t link_d2h_Bps;
+  mpt_path_model ce, sm, hs, zc;
+} mpt_model;
+
 typedef struct mpt_ctx_s* mpt_ctx_t;
 typedef struct mpt_plan_s* mpt_plan_t;
 typedef struct mpt_graph_s* mpt_graph_t;
@@ -149,7 +172,13 @@ MPT_API mpt_status mpt_ctx_status(mpt_ctx_t ctx, uint32_t* site);
 
 /* Build the chunk plan for an `nbytes` message in direction `dir` over `npaths` paths.
  * ctx may be NULL when every path has an explicit chunk size.  paths == NULL asks the
- * context's tuner for the whole path set (needs ctx).  align: chunk offsets are
+ * tuner for the whole path set (Sec. 4.4): the environment (MPT_PATHS=ce,sm,hs,zc,
+ * MPT_SHARES=w0,w1.., MPT_CHUNK_BYTES=C or MPT_CHUNKS=k per path, MPT_CTAS,
+ * MPT_SM_VARIANT=vec|bulk) when MPT_PATHS is set, else the context's tuned entry for
+ * this (direction, mode, log2 size) bucket, else the cost model's best split; chunk_bytes
+ * 0 on a listed path asks the same sources for that path's chunk size.  Without
+ * MPT_PATHS these need a context.  layout | MPT_PLAN_EAGER selects the eager-mode
+ * choices.  align: chunk offsets are
  * multiples of it (power of two <= 4096; 16 is the library's default).  layout:
  * CONTIG gives each path one contiguous region in path order; INTERLEAVE deals chunks
  * round robin (Sec. 4.3, the text after Algorithm 2).  Horizontal split: path p < P-1
@@ -221,6 +250,55 @@ MPT_API mpt_status mpt_sm_copy(mpt_ctx_t ctx, void* dst, const void* src, uint64
  * w_i the little-endian 8-byte words of the range zero-padded, mix64 the splitmix64
  * output finaliser.  Blocking. */
 MPT_API mpt_status mpt_hash_device(mpt_ctx_t ctx, const void* ptr, uint64_t nbytes, void* stream, uint64_t* out);
+
+/* ---- cost model and split search (tuner building blocks; host only, no GPU) -------- */
+
+/* Modelled time in picoseconds of `npaths` paths of kinds `kinds` carrying bytes[p] each
+ * in chunks of `chunk` bytes, direction `dir`:
+ *   T_p  = alpha_p * ceil(b_p/C) + ceil(b_p * 1e12 / beta_p)
+ *   T_HS = alpha * (ceil(b/C) + 1) + ceil(b*1e12/min(beta,beta2)) + ceil(min(C,b)*1e12/max(beta,beta2))
+ *   T    = launch + max(max_p T_p, T_HBM, T_link_h2d, T_link_d2h)
+ * where T_HBM and T_link count how often each payload byte crosses HBM (2 device-to-
+ * device; 1 direct host transfer; 3 host transfer through a device stage) and the link
+ * (once per crossing, per direction).  Integer arithmetic, ceilings as written.
+ * Errors: EINVAL (zero bandwidth, kind not allowed for `dir`, chunk 0). */
+MPT_API mpt_status mpt_model_time(const mpt_model* m, uint32_t dir, const uint32_t* kinds, const uint64_t* bytes,
+                                  uint32_t npaths, uint64_t chunk, uint64_t* out_ps);
+
+/* Best split of an `nbytes` message over 1..4 paths under the model: paths 0..P-2 take
+ * multiples of `step` bytes (step = align for nbytes <= 4096 -- an exhaustive search --
+ * else floor_align(nbytes/64), i.e. 1/64 shares), the last path the remainder; chunk
+ * sizes align*2^k <= max(nbytes, align) shared by all paths.  Ties: lowest time, fewest
+ * non-empty paths, lexicographically largest split, largest chunk.  out_bytes receives
+ * npaths byte counts. */
+MPT_API mpt_status mpt_model_optimize(const mpt_model* m, uint64_t nbytes, uint32_t dir, const uint32_t* kinds,
+                                      uint32_t npaths, uint32_t align, uint64_t* out_bytes, uint64_t* out_chunk,
+                                      uint64_t* out_ps);
+
+/* ---- autotuner (Sec. 4.4: tuned paths/chunks, separately for graph and eager mode) ---- */
+
+/* Measure candidate path sets for an `nbytes` message in direction `dir` and execution
+ * mode `mode` (MPT_MODE_GRAPH or MPT_MODE_EAGER) on this context's GPU -- single copy
+ * engine paths with 1..8 chunks, the SM kernel (vec128/bulk, several CTA counts), the
+ * zero-copy kernel, copy engine + kernel splits at several shares and chunk counts, the
+ * staged path -- each the median of `reps` timed runs (0 = default) with the L2 flushed
+ * before every run, and store the fastest for the message's log2 size bucket.  Blocking;
+ * allocates scratch buffers of `nbytes` (kept by the context).  out (capacity 4, nullable),
+ * out_n and out_us (nullable) receive the winner.  Errors: EINVAL, ECUDA, ENOMEM. */
+MPT_API mpt_status mpt_tune(mpt_ctx_t ctx, uint32_t dir, uint64_t nbytes, uint32_t mode, uint32_t reps,
+                            mpt_path_spec* out, uint32_t* out_n, double* out_us);
+
+/* Write every tuned entry as JSON lines {"dir","mode","bucket","layout","us","paths":
+ * [[kind, share, chunk_bytes, ctas, flags], ...]}. */
+MPT_API mpt_status mpt_tune_save(mpt_ctx_t ctx, const char* path);
+
+/* Load entries written by mpt_tune_save (also done by mpt_ctx_create for its tune_file
+ * argument or $MPT_TUNE_FILE).  Errors: EINVAL for an unreadable file or invalid entry. */
+MPT_API mpt_status mpt_tune_load(mpt_ctx_t ctx, const char* path);
+
+/* The tuned entry for the bucket of `nbytes` (EAGAIN when there is none). */
+MPT_API mpt_status mpt_tune_get(mpt_ctx_t ctx, uint32_t dir, uint64_t nbytes, uint32_t mode, mpt_path_spec* out,
+                                uint32_t* out_n, double* out_us);
 
 /* ---- page-locked host memory ---------------------------------------------------- */
 

@@ -163,6 +163,35 @@ def mpt_hash_device(ctx: int, ptr, nbytes: int, stream=None) -> int:
     return out.value
 
 
+def _model(m):
+    if isinstance(m, _ffi.mpt_model):
+        return m
+    out = _ffi.mpt_model(m["launch_ps"], m["hbm_Bps"], m["link_h2d_Bps"], m["link_d2h_Bps"])
+    for name in ("ce", "sm", "hs", "zc"):
+        setattr(out, name, _ffi.mpt_path_model(*m[name]))
+    return out
+
+
+def mpt_model_time(model, direction: int, kinds, nbytes_per_path, chunk: int) -> int:
+    n = len(kinds)
+    k = (C.c_uint32 * n)(*kinds)
+    b = (C.c_uint64 * n)(*nbytes_per_path)
+    out = C.c_uint64()
+    _check(lib().mpt_model_time(C.byref(_model(model)), direction, k, b, n, chunk, C.byref(out)), "mpt_model_time")
+    return out.value
+
+
+def mpt_model_optimize(model, nbytes: int, direction: int, kinds, align: int = 16):
+    """(bytes per path, chunk, modelled ps) of the best split under the model."""
+    n = len(kinds)
+    k = (C.c_uint32 * n)(*kinds)
+    b = (C.c_uint64 * n)()
+    chunk, ps = C.c_uint64(), C.c_uint64()
+    _check(lib().mpt_model_optimize(C.byref(_model(model)), nbytes, direction, k, n, align, b, C.byref(chunk),
+                                    C.byref(ps)), "mpt_model_optimize")
+    return tuple(b), chunk.value, ps.value
+
+
 def mpt_host_alloc(nbytes: int) -> int:
     p = C.c_void_p()
     _check(lib().mpt_host_alloc(nbytes, C.byref(p)), "mpt_host_alloc")

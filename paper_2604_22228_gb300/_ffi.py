@@ -47,6 +47,16 @@ class mpt_graph_info(C.Structure):
                 ("instantiate_us", C.c_double), ("staging_bytes", C.c_uint64)]
 
 
+class mpt_path_model(C.Structure):
+    _fields_ = [("alpha_ps", C.c_uint64), ("beta_Bps", C.c_uint64), ("beta2_Bps", C.c_uint64)]
+
+
+class mpt_model(C.Structure):
+    _fields_ = [("launch_ps", C.c_uint64), ("hbm_Bps", C.c_uint64), ("link_h2d_Bps", C.c_uint64),
+                ("link_d2h_Bps", C.c_uint64), ("ce", mpt_path_model), ("sm", mpt_path_model),
+                ("hs", mpt_path_model), ("zc", mpt_path_model)]
+
+
 H = C.c_void_p  # opaque handles
 P = C.POINTER
 
@@ -70,6 +80,10 @@ SIGNATURES = {
     "mpt_launch_eager": (C.c_int, [H, H, C.c_void_p, C.c_void_p, C.c_void_p]),
     "mpt_sm_copy": (C.c_int, [H, C.c_void_p, C.c_void_p, C.c_uint64, C.c_uint32, C.c_uint32, C.c_void_p]),
     "mpt_hash_device": (C.c_int, [H, C.c_void_p, C.c_uint64, C.c_void_p, P(C.c_uint64)]),
+    "mpt_model_time": (C.c_int, [P(mpt_model), C.c_uint32, P(C.c_uint32), P(C.c_uint64), C.c_uint32, C.c_uint64,
+                                 P(C.c_uint64)]),
+    "mpt_model_optimize": (C.c_int, [P(mpt_model), C.c_uint64, C.c_uint32, P(C.c_uint32), C.c_uint32, C.c_uint32,
+                                     P(C.c_uint64), P(C.c_uint64), P(C.c_uint64)]),
     "mpt_host_alloc": (C.c_int, [C.c_uint64, P(C.c_void_p)]),
     "mpt_host_free": (C.c_int, [C.c_void_p]),
 }

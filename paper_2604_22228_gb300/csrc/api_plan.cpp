@@ -7,8 +7,8 @@
 namespace mpt {
 // Implemented by the runtime: fill chunk sizes (and, when whole_set, the path set and
 // shares) from the context's tuner for this message size and direction.
-mpt_status tuner_fill(mpt_ctx_t ctx, uint64_t nbytes, uint32_t dir, uint32_t align, mpt_path_spec* specs,
-                      uint32_t* npaths, bool whole_set);
+mpt_status tuner_fill(mpt_ctx_t ctx, uint64_t nbytes, uint32_t dir, uint32_t mode, uint32_t align,
+                      mpt_path_spec* specs, uint32_t* npaths, bool whole_set);
 }  // namespace mpt
 
 using namespace mpt;
@@ -21,11 +21,12 @@ mpt_status mpt_plan(mpt_ctx_t ctx, uint64_t nbytes, uint32_t dir, const mpt_path
   *out = nullptr;
   mpt_path_spec specs[MPT_MAX_PATHS];
   std::memset(specs, 0, sizeof specs);
+  const uint32_t mode = (layout & MPT_PLAN_EAGER) ? 1u : 0u;
+  layout &= ~MPT_PLAN_EAGER;
   if (paths == nullptr) {
-    if (!ctx) return fail(MPT_EINVAL, "mpt_plan: a tuned path set needs a context");
     if (align == 0 || (align & (align - 1)) != 0 || align > MPT_MAX_ALIGN)
       return fail(MPT_EINVAL, "mpt_plan: alignment %u is not a power of two <= %u", align, MPT_MAX_ALIGN);
-    mpt_status st = tuner_fill(ctx, nbytes, dir, align, specs, &npaths, true);
+    mpt_status st = tuner_fill(ctx, nbytes, dir, mode, align, specs, &npaths, true);
     if (st != MPT_OK) return st;
   } else {
     if (npaths == 0 || npaths > MPT_MAX_PATHS)
@@ -34,10 +35,9 @@ mpt_status mpt_plan(mpt_ctx_t ctx, uint64_t nbytes, uint32_t dir, const mpt_path
     bool need_tuner = false;
     for (uint32_t p = 0; p < npaths; ++p) need_tuner |= specs[p].chunk_bytes == 0;
     if (need_tuner) {
-      if (!ctx) return fail(MPT_EINVAL, "mpt_plan: chunk_bytes 0 asks the tuner, which needs a context");
       if (align == 0 || (align & (align - 1)) != 0 || align > MPT_MAX_ALIGN)
         return fail(MPT_EINVAL, "mpt_plan: alignment %u is not a power of two <= %u", align, MPT_MAX_ALIGN);
-      mpt_status st = tuner_fill(ctx, nbytes, dir, align, specs, &npaths, false);
+      mpt_status st = tuner_fill(ctx, nbytes, dir, mode, align, specs, &npaths, false);
       if (st != MPT_OK) return st;
     }
   }

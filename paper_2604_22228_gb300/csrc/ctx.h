@@ -1,0 +1,87 @@
+// Internal context and graph objects (runtime.cu, tuner.cu).
+#pragma once
+#include <list>
+#include <map>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+#include "internal.h"
+#include "kernels.cuh"
+
+namespace mpt {
+
+struct GraphKey {
+  uint64_t src, dst, nbytes, dir, plan_hash;
+  bool operator==(const GraphKey& o) const {
+    return src == o.src && dst == o.dst && nbytes == o.nbytes && dir == o.dir && plan_hash == o.plan_hash;
+  }
+};
+struct GraphKeyHash {
+  size_t operator()(const GraphKey& k) const { return (size_t)fnv1a(&k, sizeof k); }
+};
+
+// Per-path lane of the eager engine: hop-one and hop-two streams, per-slot events of the
+// two-slot staging ring, and the lane's staging buffers (grown on demand).
+struct EagerLane {
+  cudaStream_t s[2] = {nullptr, nullptr};
+  cudaEvent_t hop1[2] = {nullptr, nullptr};
+  cudaEvent_t hop2[2] = {nullptr, nullptr};
+  cudaEvent_t done = nullptr;
+  void* host_stage = nullptr;
+  uint64_t host_stage_bytes = 0;
+  void* dev_stage = nullptr;
+  uint64_t dev_stage_bytes = 0;
+};
+
+// One tuned choice: the path set for a (direction, mode, log2 size bucket).
+struct TuneEntry {
+  uint32_t npaths = 0;
+  uint32_t layout = 0;
+  mpt_path_spec paths[4] = {};
+  double us = 0;
+};
+
+inline uint32_t tune_key(uint32_t dir, uint32_t mode, uint32_t bucket) { return (dir << 16) | (mode << 8) | bucket; }
+
+uint32_t size_bucket(uint64_t nbytes);
+mpt_model default_model(uint32_t dir, uint32_t mode);
+
+}  // namespace mpt
+
+struct mpt_graph_s {
+  int refs = 0;
+  mpt_ctx_t ctx = nullptr;
+  mpt::GraphKey key{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  mpt_graph_info info{};
+  std::vector<void*> host_allocs, dev_allocs;
+  uint64_t src_lo = 0, src_hi = 0, dst_lo = 0, dst_hi = 0;
+  bool cached = false;
+  std::list<mpt_graph_s*>::iterator lru_it;
+};
+
+struct mpt_ctx_s {
+  int device = 0;
+  int sms = 0;
+  int engines = 0;
+  uint32_t* d_status = nullptr;       // device status word
+  unsigned long long* d_hash = nullptr;
+  mpt::EagerLane lane[MPT_MAX_PATHS];
+  cudaEvent_t fork = nullptr;
+  std::unordered_map<mpt::GraphKey, mpt_graph_s*, mpt::GraphKeyHash> cache;
+  std::list<mpt_graph_s*> lru;        // front = most recently used
+  std::unordered_set<mpt_graph_s*> live;  // every graph not yet released
+  size_t cache_cap = 64;
+  uint64_t stage_max = 8ull << 20;
+  std::map<uint32_t, mpt::TuneEntry> tuned;  // tune_key -> choice
+  // tuner scratch (grown on demand)
+  void* tune_a = nullptr;
+  void* tune_b = nullptr;
+  uint64_t tune_dev_bytes = 0;
+  void* tune_h = nullptr;
+  uint64_t tune_host_bytes = 0;
+  void* flush = nullptr;              // L2 flush buffer
+  uint64_t flush_bytes = 0;
+};

@@ -21,6 +21,11 @@ mpt_status build_chunks(uint64_t nbytes, uint32_t dir, const mpt_path_spec* path
                         uint32_t align, uint32_t layout, std::vector<mpt_chunk>& out,
                         uint64_t* path_bytes);
 
+uint64_t model_time(const mpt_model& m, uint32_t dir, const uint32_t* kinds, const uint64_t* bytes, uint32_t n,
+                    uint64_t chunk);
+mpt_status model_optimize(const mpt_model& m, uint64_t nbytes, uint32_t dir, const uint32_t* kinds, uint32_t n,
+                          uint32_t align, uint64_t* best_bytes, uint64_t* best_chunk, uint64_t* best_ps);
+
 uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull);
 
 }  // namespace mpt

@@ -10,8 +10,7 @@
 #include <unordered_map>
 #include <unordered_set>
 
-#include "internal.h"
-#include "kernels.cuh"
+#include "ctx.h"
 
 namespace mpt {
 const char* last_error_cstr();
@@ -40,16 +39,6 @@ uint64_t env_u64(const char* name, uint64_t dflt) {
   return (end && *end == 0) ? (uint64_t)x : dflt;
 }
 
-struct GraphKey {
-  uint64_t src, dst, nbytes, dir, plan_hash;
-  bool operator==(const GraphKey& o) const {
-    return src == o.src && dst == o.dst && nbytes == o.nbytes && dir == o.dir && plan_hash == o.plan_hash;
-  }
-};
-struct GraphKeyHash {
-  size_t operator()(const GraphKey& k) const { return (size_t)fnv1a(&k, sizeof k); }
-};
-
 enum MemKind { kMemDevice, kMemHost, kMemOther };
 
 MemKind classify(const void* p, int device) {
@@ -64,51 +53,10 @@ MemKind classify(const void* p, int device) {
   return kMemOther;
 }
 
-// Per-path lane of the eager engine: hop-one and hop-two streams, per-slot events of the
-// two-slot staging ring, and the lane's staging buffers (grown on demand).
-struct EagerLane {
-  cudaStream_t s[2] = {nullptr, nullptr};
-  cudaEvent_t hop1[2] = {nullptr, nullptr};
-  cudaEvent_t hop2[2] = {nullptr, nullptr};
-  cudaEvent_t done = nullptr;
-  void* host_stage = nullptr;
-  uint64_t host_stage_bytes = 0;
-  void* dev_stage = nullptr;
-  uint64_t dev_stage_bytes = 0;
-};
-
 constexpr uint32_t kDefaultConsumerCtas = 32;
 
 }  // namespace
 }  // namespace mpt
-
-struct mpt_graph_s {
-  int refs = 0;
-  mpt_ctx_t ctx = nullptr;
-  mpt::GraphKey key{};
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
-  mpt_graph_info info{};
-  std::vector<void*> host_allocs, dev_allocs;
-  uint64_t src_lo = 0, src_hi = 0, dst_lo = 0, dst_hi = 0;
-  bool cached = false;
-  std::list<mpt_graph_s*>::iterator lru_it;
-};
-
-struct mpt_ctx_s {
-  int device = 0;
-  int sms = 0;
-  int engines = 0;
-  uint32_t* d_status = nullptr;       // device status word
-  unsigned long long* d_hash = nullptr;
-  mpt::EagerLane lane[MPT_MAX_PATHS];
-  cudaEvent_t fork = nullptr;
-  std::unordered_map<mpt::GraphKey, mpt_graph_s*, mpt::GraphKeyHash> cache;
-  std::list<mpt_graph_s*> lru;        // front = most recently used
-  std::unordered_set<mpt_graph_s*> live;  // every graph not yet released
-  size_t cache_cap = 64;
-  uint64_t stage_max = 8ull << 20;
-};
 
 namespace mpt {
 namespace {
@@ -517,6 +465,20 @@ mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src
 }
 
 }  // namespace
+
+mpt_status build_private_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src, mpt_graph_s* g) {
+  g->ctx = c;
+  mpt_status st = build_graph(c, plan, dst, src, g);
+  if (st != MPT_OK) graph_destroy_exec(g);
+  return st;
+}
+
+void free_private_graph(mpt_graph_s* g) { graph_destroy_exec(g); }
+
+mpt_status run_eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src, cudaStream_t s) {
+  return eager(c, plan, dst, src, s);
+}
+
 }  // namespace mpt
 
 using namespace mpt;
@@ -567,7 +529,11 @@ mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out) {
     return bail(fail(MPT_ECUDA, "mpt_ctx_create: bulk kernel shared memory"));
   c->cache_cap = (size_t)std::max<uint64_t>(1, env_u64("MPT_GRAPH_CACHE", 64));
   c->stage_max = std::max<uint64_t>(4096, env_u64("MPT_STAGE_BYTES", 8ull << 20));
-  (void)tune_file;
+  const char* tf = tune_file && *tune_file ? tune_file : std::getenv("MPT_TUNE_FILE");
+  if (tf && *tf) {
+    mpt_status st = mpt_tune_load(c, tf);
+    if (st != MPT_OK) return bail(st);
+  }
   *out = c;
   return MPT_OK;
 }
@@ -596,6 +562,10 @@ mpt_status mpt_ctx_destroy(mpt_ctx_t c) {
   }
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->d_status) cudaFree(c->d_status);
+  if (c->tune_a) cudaFree(c->tune_a);
+  if (c->tune_b) cudaFree(c->tune_b);
+  if (c->tune_h) cudaFreeHost(c->tune_h);
+  if (c->flush) cudaFree(c->flush);
   delete c;
   return MPT_OK;
 }
@@ -755,24 +725,3 @@ mpt_status mpt_host_free(void* p) {
 
 }  // extern "C"
 
-namespace mpt {
-
-// Default path set and chunk sizes until a tuned choice exists for this size bucket:
-// device-to-device on the SM copy kernel, host transfers on the copy engine, 4 MiB chunks.
-mpt_status tuner_fill(mpt_ctx_t ctx, uint64_t nbytes, uint32_t dir, uint32_t align, mpt_path_spec* specs,
-                      uint32_t* npaths, bool whole_set) {
-  (void)ctx;
-  (void)nbytes;
-  if (dir > MPT_D2H) return fail(MPT_EINVAL, "mpt_plan: unknown direction %u", dir);
-  const uint64_t chunk = ((4ull << 20) + align - 1) / align * align;
-  if (whole_set) {
-    specs[0] = mpt_path_spec{dir == MPT_D2D ? (uint32_t)MPT_PATH_SM : (uint32_t)MPT_PATH_CE, MPT_SHARE_ONE, chunk, 0, 0};
-    *npaths = 1;
-    return MPT_OK;
-  }
-  for (uint32_t p = 0; p < *npaths; ++p)
-    if (specs[p].chunk_bytes == 0) specs[p].chunk_bytes = chunk;
-  return MPT_OK;
-}
-
-}  // namespace mpt

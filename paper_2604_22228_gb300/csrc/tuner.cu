@@ -1,0 +1,465 @@
+// Autotuner: chooses the path set, shares, chunk size and CTA count for a message, cached
+// per (direction, execution mode, log2 size bucket).  Sec. 4.4: paths and chunks can be
+// set through environment variables, otherwise tuned values found by an offline search
+// are the defaults, kept separately for graph and non-graph execution.
+//
+//  * environment (highest priority): MPT_PATHS=ce,sm,hs,zc (path kinds in order),
+//    MPT_SHARES=w0,w1,... (parts of 65536; default equal), MPT_CHUNK_BYTES=C or
+//    MPT_CHUNKS=k (chunks per path), MPT_CTAS=n, MPT_SM_VARIANT=vec|bulk;
+//  * a measured entry for the bucket (mpt_tune, or loaded from a tune file);
+//  * otherwise the cost model's best split (mpt_model_optimize) with parameters measured
+//    on GB300 (default_model).
+#include <algorithm>
+#include <cerrno>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+
+#include "ctx.h"
+
+#define CUDA_TRY(expr)                                                                           \
+  do {                                                                                           \
+    cudaError_t e_ = (expr);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return mpt::fail(MPT_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+namespace mpt {
+
+// Implemented in runtime.cu: build a private (uncached) graph / run eagerly.
+mpt_status build_private_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src, mpt_graph_s* g);
+void free_private_graph(mpt_graph_s* g);
+mpt_status run_eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src, cudaStream_t s);
+
+uint32_t size_bucket(uint64_t n) { return n == 0 ? 0u : 63u - (uint32_t)__builtin_clzll(n); }
+
+// Cost-model parameters from measurements on a GB300 (152 SMs, 3 copy engines): SM copy
+// and copy-engine device copies near 3.3 TB/s of payload (6.6-6.8 TB/s of HBM traffic);
+// host link about 211 GB/s host-to-device and 193 GB/s device-to-host for copy engines
+// and the zero-copy kernel alike; a few microseconds of issue cost per memcpy.
+mpt_model default_model(uint32_t dir, uint32_t mode) {
+  mpt_model m{};
+  const uint64_t us = 1000000;  // ps per microsecond
+  m.launch_ps = mode == 0 ? 3 * us : 2 * us;
+  m.hbm_Bps = 6757900000000ull;
+  m.link_h2d_Bps = 211000000000ull;
+  m.link_d2h_Bps = 193000000000ull;
+  const uint64_t link = dir == MPT_D2H ? m.link_d2h_Bps : m.link_h2d_Bps;
+  if (dir == MPT_D2D) {
+    m.ce = mpt_path_model{(mode == 0 ? 2 : 4) * us, 3380000000000ull, 0};
+    m.sm = mpt_path_model{mode == 0 ? us / 2 : us, 3400000000000ull, 0};
+    m.hs = mpt_path_model{(mode == 0 ? 3 : 5) * us, m.link_d2h_Bps, m.link_h2d_Bps};
+    m.zc = mpt_path_model{us, link, 0};
+  } else {
+    m.ce = mpt_path_model{(mode == 0 ? 2 : 4) * us, link, 0};
+    m.zc = mpt_path_model{mode == 0 ? us / 2 : us, link, 0};
+    m.hs = mpt_path_model{(mode == 0 ? 3 : 5) * us, link, 3400000000000ull};
+    m.sm = mpt_path_model{us, 3400000000000ull, 0};
+  }
+  return m;
+}
+
+namespace {
+
+uint64_t round_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+uint32_t parse_kind(const std::string& s) {
+  if (s == "ce") return MPT_PATH_CE;
+  if (s == "sm") return MPT_PATH_SM;
+  if (s == "hs") return MPT_PATH_HS;
+  if (s == "zc") return MPT_PATH_ZC;
+  return 0;
+}
+
+std::vector<std::string> split_list(const char* v) {
+  std::vector<std::string> out;
+  std::string cur;
+  for (const char* p = v; *p; ++p) {
+    if (*p == ',') {
+      out.push_back(cur);
+      cur.clear();
+    } else if (*p != ' ') {
+      cur += (char)std::tolower((unsigned char)*p);
+    }
+  }
+  out.push_back(cur);
+  return out;
+}
+
+bool env_u64(const char* name, uint64_t& out) {
+  const char* v = std::getenv(name);
+  if (!v || !*v) return false;
+  char* end = nullptr;
+  errno = 0;
+  unsigned long long x = std::strtoull(v, &end, 0);
+  if (errno || !end || *end) return false;
+  out = x;
+  return true;
+}
+
+// Shares for byte counts: w_p = floor(65536 * b_p / N) for p < P-1, remainder last;
+// paths that would get no share are dropped.
+uint32_t specs_from_bytes(uint64_t n, const uint32_t* kinds, const uint64_t* bytes, uint32_t np, uint64_t chunk,
+                          mpt_path_spec* out) {
+  uint32_t k = 0;
+  uint64_t given = 0;
+  uint64_t nonempty = 0;
+  for (uint32_t p = 0; p < np; ++p) nonempty += bytes[p] > 0;
+  if (n == 0 || nonempty <= 1) {
+    uint32_t p = 0;
+    while (p + 1 < np && bytes[p] == 0) ++p;
+    out[0] = mpt_path_spec{kinds[p], MPT_SHARE_ONE, chunk, 0, 0};
+    return 1;
+  }
+  for (uint32_t p = 0; p < np; ++p) {
+    if (bytes[p] == 0) continue;
+    uint64_t w = (uint64_t)(((unsigned __int128)bytes[p] * MPT_SHARE_ONE) / n);
+    if (w == 0) w = 1;
+    out[k++] = mpt_path_spec{kinds[p], (uint32_t)w, chunk, 0, 0};
+    given += w;
+  }
+  // the last listed path absorbs rounding so shares sum to 65536
+  int64_t fix = (int64_t)MPT_SHARE_ONE - (int64_t)given;
+  out[k - 1].share = (uint32_t)((int64_t)out[k - 1].share + fix);
+  if ((int32_t)out[k - 1].share <= 0) {
+    out[k - 1].share = 1;
+    uint64_t s = 0;
+    for (uint32_t p = 0; p + 1 < k; ++p) s += out[p].share;
+    out[0].share -= (uint32_t)(s + 1 - MPT_SHARE_ONE);
+  }
+  return k;
+}
+
+TuneEntry model_choice(uint64_t n, uint32_t dir, uint32_t mode, uint32_t align) {
+  const mpt_model m = default_model(dir, mode);
+  static const uint32_t d2d_sets[3][2] = {{MPT_PATH_SM, 0}, {MPT_PATH_CE, 0}, {MPT_PATH_CE, MPT_PATH_SM}};
+  static const uint32_t host_sets[3][2] = {{MPT_PATH_CE, 0}, {MPT_PATH_ZC, 0}, {MPT_PATH_CE, MPT_PATH_ZC}};
+  const uint32_t(*sets)[2] = dir == MPT_D2D ? d2d_sets : host_sets;
+  TuneEntry best;
+  uint64_t best_t = ~0ull;
+  for (int s = 0; s < 3; ++s) {
+    const uint32_t np = sets[s][1] ? 2 : 1;
+    uint64_t bytes[2], chunk, t;
+    if (model_optimize(m, n, dir, sets[s], np, align, bytes, &chunk, &t) != MPT_OK) continue;
+    if (t < best_t) {
+      best_t = t;
+      best.npaths = specs_from_bytes(n, sets[s], bytes, np, chunk, best.paths);
+      best.us = (double)t / 1e6;
+    }
+  }
+  return best;
+}
+
+// MPT_PATHS and friends; false when MPT_PATHS is unset.
+bool env_choice(uint64_t n, uint32_t dir, uint32_t align, TuneEntry& e, mpt_status& st) {
+  const char* pv = std::getenv("MPT_PATHS");
+  st = MPT_OK;
+  if (!pv || !*pv) return false;
+  std::vector<std::string> names = split_list(pv);
+  if (names.empty() || names.size() > 4) {
+    st = fail(MPT_EINVAL, "MPT_PATHS: 1..4 paths");
+    return true;
+  }
+  e = TuneEntry{};
+  e.npaths = (uint32_t)names.size();
+  std::vector<uint32_t> shares(e.npaths, 0);
+  const char* sv = std::getenv("MPT_SHARES");
+  if (sv && *sv) {
+    std::vector<std::string> ws = split_list(sv);
+    if (ws.size() != names.size()) {
+      st = fail(MPT_EINVAL, "MPT_SHARES: %zu values for %zu paths", ws.size(), names.size());
+      return true;
+    }
+    for (size_t i = 0; i < ws.size(); ++i) shares[i] = (uint32_t)std::strtoul(ws[i].c_str(), nullptr, 0);
+  } else {
+    for (uint32_t p = 0; p < e.npaths; ++p) shares[p] = MPT_SHARE_ONE / e.npaths;
+    shares[e.npaths - 1] += MPT_SHARE_ONE % e.npaths;
+  }
+  uint64_t chunk = 0, nchunks = 0, ctas = 0;
+  env_u64("MPT_CHUNK_BYTES", chunk);
+  env_u64("MPT_CHUNKS", nchunks);
+  env_u64("MPT_CTAS", ctas);
+  const char* var = std::getenv("MPT_SM_VARIANT");
+  const uint32_t flags = (var && std::strcmp(var, "bulk") == 0) ? MPT_SM_BULK : MPT_SM_VEC128;
+  for (uint32_t p = 0; p < e.npaths; ++p) {
+    const uint32_t kind = parse_kind(names[p]);
+    if (!kind) {
+      st = fail(MPT_EINVAL, "MPT_PATHS: unknown path '%s' (ce, sm, hs, zc)", names[p].c_str());
+      return true;
+    }
+    uint64_t c = chunk;
+    if (!c) {
+      const uint64_t bp = (uint64_t)(((unsigned __int128)n * shares[p]) >> 16);
+      c = nchunks ? (bp + nchunks - 1) / nchunks : (4ull << 20);
+    }
+    c = std::max<uint64_t>(align, round_up(c, align));
+    e.paths[p] = mpt_path_spec{kind, shares[p], c, (uint32_t)ctas, kind == MPT_PATH_SM ? flags : 0u};
+  }
+  return true;
+}
+
+mpt_status ensure_dev(void*& p, uint64_t& have, uint64_t need) {
+  if (have >= need) return MPT_OK;
+  if (p) cudaFree(p);
+  p = nullptr;
+  have = 0;
+  CUDA_TRY(cudaMalloc(&p, need));
+  have = need;
+  return MPT_OK;
+}
+
+}  // namespace
+
+mpt_status tuner_fill(mpt_ctx_t ctx, uint64_t nbytes, uint32_t dir, uint32_t mode, uint32_t align,
+                      mpt_path_spec* specs, uint32_t* npaths, bool whole_set) {
+  if (dir > MPT_D2H) return fail(MPT_EINVAL, "mpt_plan: unknown direction %u", dir);
+  TuneEntry e;
+  mpt_status st;
+  bool from_env = env_choice(nbytes, dir, align, e, st);
+  if (st != MPT_OK) return st;
+  if (!from_env) {
+    if (!ctx) return fail(MPT_EINVAL, "mpt_plan: the tuner needs a context (or MPT_PATHS)");
+    auto it = ctx->tuned.find(tune_key(dir, mode, size_bucket(nbytes)));
+    e = it != ctx->tuned.end() ? it->second : model_choice(nbytes, dir, mode, align);
+  }
+  for (uint32_t p = 0; p < e.npaths; ++p) e.paths[p].chunk_bytes = std::max<uint64_t>(align, round_up(e.paths[p].chunk_bytes, align));
+  if (whole_set) {
+    std::memcpy(specs, e.paths, e.npaths * sizeof(mpt_path_spec));
+    *npaths = e.npaths;
+    return MPT_OK;
+  }
+  for (uint32_t p = 0; p < *npaths; ++p) {
+    if (specs[p].chunk_bytes) continue;
+    uint64_t c = 0;
+    for (uint32_t q = 0; q < e.npaths && !c; ++q)
+      if (e.paths[q].kind == specs[p].kind) c = e.paths[q].chunk_bytes;
+    if (!c) c = e.npaths ? e.paths[0].chunk_bytes : (4ull << 20);
+    specs[p].chunk_bytes = std::max<uint64_t>(align, round_up(c, align));
+  }
+  return MPT_OK;
+}
+
+namespace {
+
+struct Candidate {
+  uint32_t n;
+  mpt_path_spec p[4];
+};
+
+std::vector<Candidate> candidates(mpt_ctx_t c, uint32_t dir, uint64_t n, uint32_t mode) {
+  std::vector<Candidate> out;
+  const uint32_t sms = (uint32_t)c->sms;
+  auto chunk_for = [](uint64_t bytes, uint64_t parts) {
+    return std::max<uint64_t>(16, round_up((bytes + parts - 1) / std::max<uint64_t>(parts, 1), 16));
+  };
+  auto one = [&](uint32_t kind, uint64_t chunk, uint32_t ctas, uint32_t flags) {
+    Candidate k{};
+    k.n = 1;
+    k.p[0] = mpt_path_spec{kind, MPT_SHARE_ONE, chunk, ctas, flags};
+    out.push_back(k);
+  };
+  auto two = [&](uint32_t k0, uint32_t w0, uint64_t c0, uint32_t k1, uint64_t c1, uint32_t ctas1, uint32_t f1) {
+    Candidate k{};
+    k.n = 2;
+    k.p[0] = mpt_path_spec{k0, w0, c0, 0, 0};
+    k.p[1] = mpt_path_spec{k1, MPT_SHARE_ONE - w0, c1, ctas1, f1};
+    out.push_back(k);
+  };
+  const uint64_t whole = chunk_for(n, 1);
+  if (dir == MPT_D2D) {
+    for (uint32_t ctas : {sms, 2 * sms, 4 * sms, 8 * sms}) one(MPT_PATH_SM, whole, ctas, MPT_SM_VEC128);
+    if (n >= (1u << 20))
+      for (uint32_t ctas : {sms, 2 * sms}) one(MPT_PATH_SM, whole, ctas, MPT_SM_BULK);
+    for (uint64_t parts : {1, 2, 3, 4, 8}) {
+      if (parts > 1 && n < parts * (64u << 10)) continue;
+      one(MPT_PATH_CE, chunk_for(n, parts), 0, 0);
+    }
+    if (n >= (256u << 10)) {
+      for (uint32_t w : {4096u, 8192u, 16384u, 24576u, 32768u, 40960u, 49152u})
+        for (uint64_t parts : {1, 2, 4}) {
+          const uint64_t bce = (n * w) >> 16;
+          two(MPT_PATH_CE, w, chunk_for(bce, parts), MPT_PATH_SM, chunk_for(n - bce, 1), 2 * sms, MPT_SM_VEC128);
+        }
+    }
+  } else {
+    for (uint64_t parts : {1, 2, 4, 8}) {
+      if (parts > 1 && n < parts * (64u << 10)) continue;
+      one(MPT_PATH_CE, chunk_for(n, parts), 0, 0);
+    }
+    for (uint32_t ctas : {sms / 2, sms, 2 * sms}) one(MPT_PATH_ZC, whole, ctas, 0);
+    if (n >= (256u << 10)) {
+      for (uint32_t w : {16384u, 32768u, 49152u, 57344u})
+        for (uint64_t parts : {1, 4}) {
+          const uint64_t bce = (n * w) >> 16;
+          two(MPT_PATH_CE, w, chunk_for(bce, parts), MPT_PATH_ZC, chunk_for(n - bce, 1), sms, 0);
+        }
+    }
+    if (n >= (1u << 20))
+      for (uint64_t cb : {1ull << 20, 4ull << 20, 8ull << 20})
+        if (cb <= c->stage_max && cb <= n) one(MPT_PATH_HS, cb, 0, 0);
+  }
+  (void)mode;
+  return out;
+}
+
+}  // namespace
+
+}  // namespace mpt
+
+using namespace mpt;
+
+extern "C" {
+
+mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, uint32_t reps, mpt_path_spec* out,
+                    uint32_t* out_n, double* out_us) {
+  if (!c) return fail(MPT_EINVAL, "mpt_tune: NULL context");
+  if (dir > MPT_D2H || mode > 1) return fail(MPT_EINVAL, "mpt_tune: bad direction or mode");
+  if (nbytes == 0) return fail(MPT_EINVAL, "mpt_tune: empty message");
+  if (reps == 0) reps = nbytes >= (64ull << 20) ? 3 : 5;
+  CUDA_TRY(cudaSetDevice(c->device));
+  // buffers: device a/b, page-locked host h, and a 256 MiB L2 flush buffer
+  mpt_status st = ensure_dev(c->tune_a, c->tune_dev_bytes, nbytes);
+  if (st != MPT_OK) return st;
+  if (c->tune_b) cudaFree(c->tune_b);
+  c->tune_b = nullptr;
+  CUDA_TRY(cudaMalloc(&c->tune_b, c->tune_dev_bytes));
+  if (dir != MPT_D2D && c->tune_host_bytes < nbytes) {
+    if (c->tune_h) cudaFreeHost(c->tune_h);
+    c->tune_h = nullptr;
+    c->tune_host_bytes = 0;
+    CUDA_TRY(cudaHostAlloc(&c->tune_h, nbytes, cudaHostAllocMapped | cudaHostAllocPortable));
+    c->tune_host_bytes = nbytes;
+  }
+  st = ensure_dev(c->flush, c->flush_bytes, 256ull << 20);
+  if (st != MPT_OK) return st;
+  void* src = dir == MPT_H2D ? c->tune_h : c->tune_a;
+  void* dst = dir == MPT_D2H ? c->tune_h : c->tune_b;
+  cudaStream_t s = c->lane[MPT_MAX_PATHS - 1].s[0];
+  cudaEvent_t e0, e1;
+  CUDA_TRY(cudaEventCreate(&e0));
+  CUDA_TRY(cudaEventCreate(&e1));
+  TuneEntry best;
+  double best_us = 1e30;
+  for (const Candidate& k : candidates(c, dir, nbytes, mode)) {
+    mpt_plan_t plan = nullptr;
+    if (mpt_plan(nullptr, nbytes, dir, k.p, k.n, 16, MPT_LAYOUT_CONTIG, &plan) != MPT_OK) continue;
+    mpt_graph_s g;
+    bool ok = true;
+    if (mode == 0) ok = build_private_graph(c, plan, dst, src, &g) == MPT_OK;
+    std::vector<float> ts;
+    for (uint32_t r = 0; ok && r < reps + 1; ++r) {
+      cudaMemsetAsync(c->flush, r & 0xff, c->flush_bytes, s);
+      cudaEventRecord(e0, s);
+      if (mode == 0) ok = g.exec == nullptr || cudaGraphLaunch(g.exec, s) == cudaSuccess;
+      else ok = run_eager(c, plan, dst, src, s) == MPT_OK;
+      cudaEventRecord(e1, s);
+      if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (r > 0) ts.push_back(ms);  // the first launch warms up
+    }
+    if (mode == 0) free_private_graph(&g);
+    mpt_plan_destroy(plan);
+    if (!ok || ts.empty()) {
+      cudaGetLastError();
+      continue;
+    }
+    std::sort(ts.begin(), ts.end());
+    const double us = 1e3 * ts[ts.size() / 2];
+    if (us < best_us) {
+      best_us = us;
+      best = TuneEntry{};
+      best.npaths = k.n;
+      std::memcpy(best.paths, k.p, sizeof k.p);
+      best.us = us;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (best.npaths == 0) return fail(MPT_ECUDA, "mpt_tune: no candidate ran");
+  mpt_status dev = mpt_ctx_status(c, nullptr);
+  if (dev != MPT_OK) return dev;
+  c->tuned[tune_key(dir, mode, size_bucket(nbytes))] = best;
+  if (out) std::memcpy(out, best.paths, best.npaths * sizeof(mpt_path_spec));
+  if (out_n) *out_n = best.npaths;
+  if (out_us) *out_us = best.us;
+  return MPT_OK;
+}
+
+mpt_status mpt_tune_save(mpt_ctx_t c, const char* path) {
+  if (!c || !path) return fail(MPT_EINVAL, "mpt_tune_save: NULL argument");
+  FILE* f = std::fopen(path, "w");
+  if (!f) return fail(MPT_EINVAL, "mpt_tune_save: cannot open %s", path);
+  for (const auto& kv : c->tuned) {
+    const TuneEntry& e = kv.second;
+    std::fprintf(f, "{\"dir\": %u, \"mode\": %u, \"bucket\": %u, \"layout\": %u, \"us\": %.3f, \"paths\": [",
+                 kv.first >> 16, (kv.first >> 8) & 0xffu, kv.first & 0xffu, e.layout, e.us);
+    for (uint32_t p = 0; p < e.npaths; ++p)
+      std::fprintf(f, "%s[%u, %u, %llu, %u, %u]", p ? ", " : "", e.paths[p].kind, e.paths[p].share,
+                   (unsigned long long)e.paths[p].chunk_bytes, e.paths[p].ctas, e.paths[p].flags);
+    std::fprintf(f, "]}\n");
+  }
+  std::fclose(f);
+  return MPT_OK;
+}
+
+// Reads the JSON-lines file mpt_tune_save writes (numbers in its fixed key order).
+mpt_status mpt_tune_load(mpt_ctx_t c, const char* path) {
+  if (!c || !path) return fail(MPT_EINVAL, "mpt_tune_load: NULL argument");
+  FILE* f = std::fopen(path, "r");
+  if (!f) return fail(MPT_EINVAL, "mpt_tune_load: cannot open %s", path);
+  char line[1024];
+  uint32_t lineno = 0;
+  while (std::fgets(line, sizeof line, f)) {
+    ++lineno;
+    double v[5 + 5 * 4];
+    int n = 0;
+    for (char* p = line; *p && n < (int)(sizeof v / sizeof v[0]);) {
+      if ((*p >= '0' && *p <= '9') || (*p == '-' && p[1] >= '0' && p[1] <= '9')) {
+        char* end;
+        v[n++] = std::strtod(p, &end);
+        p = end;
+      } else {
+        ++p;
+      }
+    }
+    if (n == 0) continue;
+    if (n < 10 || (n - 5) % 5 != 0 || v[0] > 2 || v[1] > 1 || v[2] > 63) {
+      std::fclose(f);
+      return fail(MPT_EINVAL, "mpt_tune_load: %s line %u is not a tuner entry", path, lineno);
+    }
+    TuneEntry e;
+    e.layout = (uint32_t)v[3];
+    e.us = v[4];
+    e.npaths = (uint32_t)((n - 5) / 5);
+    for (uint32_t p = 0; p < e.npaths; ++p) {
+      const double* q = v + 5 + 5 * p;
+      e.paths[p] = mpt_path_spec{(uint32_t)q[0], (uint32_t)q[1], (uint64_t)q[2], (uint32_t)q[3], (uint32_t)q[4]};
+    }
+    mpt_plan_t probe = nullptr;
+    if (mpt_plan(nullptr, 1ull << (uint32_t)v[2], (uint32_t)v[0], e.paths, e.npaths, 16, MPT_LAYOUT_CONTIG, &probe) !=
+        MPT_OK) {
+      std::fclose(f);
+      return fail(MPT_EINVAL, "mpt_tune_load: %s line %u holds an invalid path set", path, lineno);
+    }
+    mpt_plan_destroy(probe);
+    c->tuned[tune_key((uint32_t)v[0], (uint32_t)v[1], (uint32_t)v[2])] = e;
+  }
+  std::fclose(f);
+  return MPT_OK;
+}
+
+mpt_status mpt_tune_get(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, mpt_path_spec* out,
+                        uint32_t* out_n, double* out_us) {
+  if (!c || !out || !out_n) return fail(MPT_EINVAL, "mpt_tune_get: NULL argument");
+  auto it = c->tuned.find(tune_key(dir, mode, size_bucket(nbytes)));
+  if (it == c->tuned.end()) return fail(MPT_EAGAIN, "mpt_tune_get: no tuned entry for this bucket");
+  std::memcpy(out, it->second.paths, it->second.npaths * sizeof(mpt_path_spec));
+  *out_n = it->second.npaths;
+  if (out_us) *out_us = it->second.us;
+  return MPT_OK;
+}
+
+}  // extern "C"

@@ -168,7 +168,10 @@ def test_hash_matches_oracle(ctx):
 
 
 def test_graph_cache_hits_and_eviction(ctx):
+    # a context of its own: the shared one caches graphs of earlier tests whose freed
+    # addresses the allocator may hand out again
     import torch
+    ctx = mpt.mpt_ctx_create(0)
     n = MiB
     src, dst = Buf(n, "dev"), Buf(n, "dev")
     plan = mpt.mpt_plan(ctx, n, P.D2D, [(P.CE, 32768, 256 * 1024), (P.SM, 32768, 256 * 1024)])
@@ -185,6 +188,34 @@ def test_graph_cache_hits_and_eviction(ctx):
     for g in (g1, g2, g3):
         mpt.mpt_graph_release(g)
     mpt.mpt_plan_destroy(plan)
+    assert mpt.mpt_ctx_status(ctx)[0] == mpt.MPT_OK
+    mpt.mpt_ctx_destroy(ctx)
+
+
+def test_graph_cache_lru_capacity(monkeypatch):
+    import torch
+    monkeypatch.setenv("MPT_GRAPH_CACHE", "3")
+    ctx = mpt.mpt_ctx_create(0)
+    n = 64 * 1024
+    src, dst = Buf(n, "dev"), Buf(8 * n, "dev")
+    data = seeded("u8", 17, n)
+    src.fill(data)
+    plan = mpt.mpt_plan(ctx, n, P.D2D, [(P.SM, 65536, n)])
+    graphs = [mpt.mpt_capture(ctx, plan, dst.ptr + i * n, src.ptr) for i in range(5)]
+    assert len(set(graphs)) == 5
+    # only the three most recent stay cached; capturing the first again builds a new graph
+    assert mpt.mpt_capture(ctx, plan, dst.ptr + 4 * n, src.ptr) == graphs[4]
+    again = mpt.mpt_capture(ctx, plan, dst.ptr, src.ptr)
+    assert again != graphs[0]
+    for g in graphs:  # evicted graphs still run while referenced
+        mpt.mpt_launch(g, torch.cuda.current_stream())
+    out = dst.numpy()
+    for i in range(5):
+        assert np.array_equal(out[i * n:(i + 1) * n], data)
+    for g in graphs + [again, graphs[4]]:
+        mpt.mpt_graph_release(g)
+    mpt.mpt_plan_destroy(plan)
+    mpt.mpt_ctx_destroy(ctx)
 
 
 def test_pointer_kind_checked(ctx):
