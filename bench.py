@@ -147,16 +147,22 @@ def aggregate(world: int, bytes_per_rank: float, seconds: float) -> tuple[float,
 
 # ---- CPU oracle arm ------------------------------------------------------------------------
 
+_CPU_SRC = {}
+
+
 def cpu_oracle_sample(plans, budget_s=10.0, max_bytes=256 * MiB):
     """Time the oracle (planner + memcpy) over the sweep's sizes up to max_bytes, repeated
-    until budget_s has passed.  Returns (GB/s, seconds, bytes, description)."""
+    until budget_s has passed (at least one pass).  Returns (GB/s, seconds, bytes,
+    description)."""
     import numpy as np
 
     import payload
     from oracle import planner as OP
     from oracle import transfer as OT
     sizes = [n for n in SIZES if n <= max_bytes]
-    src = payload.fill("f32", SEED, max(sizes))
+    if max_bytes not in _CPU_SRC:
+        _CPU_SRC[max_bytes] = payload.fill("f32", SEED, max(sizes))
+    src = _CPU_SRC[max_bytes]
     moved, t0, reps = 0, time.perf_counter(), 0
     while True:
         for n in sizes:
@@ -251,6 +257,19 @@ def run_ours(args):
             graphs.append(mpt.mpt_capture(ctx, p, base_d + o, base_s + o))
         return plans, graphs
 
+    tune_s = 0.0
+    if args.tune == "online":
+        t_tune = time.perf_counter()
+        for n in SIZES:
+            for mode in (mpt.MPT_MODE_GRAPH, mpt.MPT_MODE_EAGER):
+                mpt.mpt_tune(ctx, mpt.MPT_D2D, n, mode)
+        if not args.no_e2e:
+            mpt.mpt_tune(ctx, mpt.MPT_H2D, total, mpt.MPT_MODE_GRAPH)
+            mpt.mpt_tune(ctx, mpt.MPT_D2H, total, mpt.MPT_MODE_GRAPH)
+        tune_s = time.perf_counter() - t_tune
+        if args.tune_out:
+            mpt.mpt_tune_save(ctx, args.tune_out)
+
     tuned_plans, tuned_graphs = capture_all("tuned")
     kernels_per_step = sum(mpt.mpt_graph_get_info(g)["kernel_nodes"] for g in tuned_graphs)
     total_bytes = sum(SIZES)
@@ -262,25 +281,34 @@ def run_ours(args):
             mpt.mpt_launch(g, stream)
     stream.synchronize()
 
-    # ---- timed region: K sweeps, events between messages for the per-size breakdown ----
+    # ---- timed region: K sweeps back to back, CUDA events around the whole region ----
     nsz = len(SIZES)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nsz + 1)] for _ in range(args.steps)]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     dist_barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        for k in range(args.steps):
-            ev[k][0].record(stream)
-            for i, g in enumerate(tuned_graphs):
-                mpt.mpt_launch(g, stream)
-                ev[k][i + 1].record(stream)
+    t_start.record(stream)
+    for k in range(args.steps):
+        for g in tuned_graphs:
+            mpt.mpt_launch(g, stream)
+    t_end.record(stream)
     stream.synchronize()
     dist_barrier(world)
     torch.cuda.synchronize()
     host_elapsed = time.perf_counter() - t0
-    dev_elapsed = sum(ev[k][0].elapsed_time(ev[k][nsz]) for k in range(args.steps)) / 1e3
+    dev_elapsed = t_start.elapsed_time(t_end) / 1e3
     value, slowest = aggregate(world, total_bytes * args.steps, dev_elapsed)
-    per_size_tuned = [statistics.median(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(args.steps))
+
+    # ---- per-size breakdown: the same sweeps with an event after every message ----
+    bk = max(3, min(args.steps, 20))
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nsz + 1)] for _ in range(bk)]
+    for k in range(bk):
+        ev[k][0].record(stream)
+        for i, g in enumerate(tuned_graphs):
+            mpt.mpt_launch(g, stream)
+            ev[k][i + 1].record(stream)
+    stream.synchronize()
+    per_size_tuned = [statistics.median(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(bk))
                       for i in range(nsz)]
 
     # ---- per-size baselines (not part of value) ----
@@ -317,16 +345,20 @@ def run_ours(args):
 
     reps = args.baseline_reps
     base = {}
-    for kind in ("ce", "sm", "split"):
-        plans, graphs = capture_all(kind)
-        base[kind] = time_graphs(graphs, reps)
-        for g in graphs:
-            mpt.mpt_graph_release(g)
-        if kind == "split":
-            base["split_eager"] = time_eager(plans, reps)
-        for p in plans:
+    if not args.no_baselines:
+        for kind in ("ce", "sm", "split"):
+            plans, graphs = capture_all(kind)
+            base[kind] = time_graphs(graphs, reps)
+            for g in graphs:
+                mpt.mpt_graph_release(g)
+            if kind == "split":
+                base["split_eager"] = time_eager(plans, reps)
+            for p in plans:
+                mpt.mpt_plan_destroy(p)
+        eager_plans = [mpt.mpt_plan(ctx, n, mpt.MPT_D2D, None, 16, mpt.MPT_PLAN_EAGER) for n in SIZES]
+        base["tuned_eager"] = time_eager(eager_plans, reps)
+        for p in eager_plans:
             mpt.mpt_plan_destroy(p)
-    base["tuned_eager"] = time_eager(tuned_plans, reps)
 
     # ---- dominant kernel alone: SM copy kernel on the 1 GiB message, CUDA events ----
     kin = args.kernel_launches
@@ -399,16 +431,20 @@ def run_ours(args):
 
     sweep = []
     for i, n in enumerate(SIZES):
-        gb = lambda ms: round(n / (ms / 1e3) / 1e9, 3) if ms > 0 else None
-        best_single = min(base["ce"][i], base["sm"][i])
-        sweep.append({
-            "bytes": n, "tuned_graph_gbs": gb(per_size_tuned[i]), "ce_graph_gbs": gb(base["ce"][i]),
-            "sm_graph_gbs": gb(base["sm"][i]), "split50_graph_gbs": gb(base["split"][i]),
-            "split50_eager_gbs": gb(base["split_eager"][i]), "tuned_eager_gbs": gb(base["tuned_eager"][i]),
-            "best_single_gbs": gb(best_single),
-            "tuned_vs_best_single": round(best_single / per_size_tuned[i], 3) if per_size_tuned[i] > 0 else None,
-            "plan": [(p["kind"], p["share"], p["chunk_bytes"]) for p in mpt.mpt_plan_paths(tuned_plans[i])],
-        })
+        gb = lambda ms: round(n / (ms / 1e3) / 1e9, 3) if ms and ms > 0 else None
+        row = {"bytes": n, "tuned_graph_gbs": gb(per_size_tuned[i]),
+               "plan": [(p["kind"], p["share"], p["chunk_bytes"], p["ctas"], p["flags"])
+                        for p in mpt.mpt_plan_paths(tuned_plans[i])]}
+        if base:
+            best_single = min(base["ce"][i], base["sm"][i])
+            row.update({
+                "ce_graph_gbs": gb(base["ce"][i]), "sm_graph_gbs": gb(base["sm"][i]),
+                "split50_graph_gbs": gb(base["split"][i]), "split50_eager_gbs": gb(base["split_eager"][i]),
+                "tuned_eager_gbs": gb(base["tuned_eager"][i]), "best_single_gbs": gb(best_single),
+                "tuned_vs_best_single": round(best_single / per_size_tuned[i], 3) if per_size_tuned[i] > 0 else None,
+                "tuned_graph_vs_tuned_eager": round(base["tuned_eager"][i] / per_size_tuned[i], 3)
+                if per_size_tuned[i] > 0 else None})
+        sweep.append(row)
 
     traffic = None
     prof = os.path.join(ROOT, "profiles", "roofline_traffic.json")
@@ -445,11 +481,48 @@ def run_ours(args):
                          "launch": "1 GiB message, 2 GiB algorithmic HBM bytes", "launch_ms": round(k_ms, 4),
                          "peak_source": f"{peak_kind} hbm_gbs (burst)"},
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": kernels_per_step * args.steps,
-            "clocks": clk, "parity_ok": ok, "host_elapsed_s": round(host_elapsed, 4),
+            "clocks": clk, "parity_ok": ok, "host_elapsed_s": round(host_elapsed, 4), "tune_s": round(tune_s, 2),
             "sweep": sweep, "wall_s": round(time.perf_counter() - t_wall0, 2),
         }
         print(json.dumps(line), flush=True)
     return 0 if ok else 1
+
+
+def run_kernel_only(args):
+    """One kernel alone on one message (for profiling): K launches timed with CUDA events."""
+    import torch
+
+    import paper_2604_22228_gb300 as mpt
+    from paper_2604_22228_gb300 import build
+    build.build()
+    n = args.kernel_bytes
+    ctx = mpt.mpt_ctx_create(0)
+    host = args.kernel_only == "zc"
+    if host:
+        a = torch.empty(n, dtype=torch.uint8).pin_memory()
+    else:
+        a = torch.empty(n, dtype=torch.uint8, device="cuda")
+    b = torch.empty(n, dtype=torch.uint8, device="cuda")
+    a.fill_(7)
+    variant = mpt.MPT_SM_BULK if args.kernel_only == "bulk" else mpt.MPT_SM_VEC128
+    s = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        mpt.mpt_sm_copy(ctx, b.data_ptr(), a.data_ptr(), n, variant, args.kernel_ctas, s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        mpt.mpt_sm_copy(ctx, b.data_ptr(), a.data_ptr(), n, variant, args.kernel_ctas, s)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ok = bool(torch.equal(a[:1 << 20].to(b.device), b[:1 << 20]))
+    st, _ = mpt.mpt_ctx_status(ctx)
+    mpt.mpt_ctx_destroy(ctx)
+    moved = n if host else 2 * n
+    print(json.dumps({"kernel": args.kernel_only, "bytes": n, "ctas": args.kernel_ctas, "launches": args.steps,
+                      "ms_per_launch": round(ms, 5), "gbs": round(moved / (ms / 1e3) / 1e9, 1),
+                      "ok": ok and st == 0}), flush=True)
+    return 0 if ok and st == 0 else 1
 
 
 def main(argv=None):
@@ -464,11 +537,21 @@ def main(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-baselines", action="store_true")
+    ap.add_argument("--tune", choices=["online", "model"], default="online",
+                    help="online: measure every size bucket with mpt_tune before capturing; model: cost model only")
+    ap.add_argument("--tune-out", default=None, help="write the tuned table (JSON lines) here")
+    ap.add_argument("--kernel-only", choices=["vec", "bulk", "zc"], default=None,
+                    help="time one copy kernel alone on --kernel-bytes (profiling)")
+    ap.add_argument("--kernel-bytes", type=int, default=256 * MiB)
+    ap.add_argument("--kernel-ctas", type=int, default=0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
     if args.impl == "reference":
         return run_reference(args)
+    if args.kernel_only:
+        return run_kernel_only(args)
     return run_ours(args)
 
 

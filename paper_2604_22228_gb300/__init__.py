@@ -18,7 +18,7 @@ import ctypes as C
 from . import _ffi
 from ._ffi import (MPT_D2D, MPT_D2H, MPT_H2D, MPT_LAYOUT_CONTIG, MPT_LAYOUT_INTERLEAVE, MPT_MAX_CHUNKS,  # noqa: F401
                    MPT_MAX_PATHS, MPT_PATH_CE, MPT_PATH_HS, MPT_PATH_SM, MPT_PATH_ZC, MPT_SHARE_ONE, MPT_SM_BULK,
-                   MPT_SM_VEC128, STATUS_NAMES)
+                   MPT_SM_VEC128, MPT_PLAN_EAGER, MPT_MODE_GRAPH, MPT_MODE_EAGER, STATUS_NAMES)
 from ._ffi import MPT_EAGAIN, MPT_ECUDA, MPT_EINVAL, MPT_ENOMEM, MPT_ENOTSUP, MPT_ETIMEDOUT, MPT_OK  # noqa: F401
 
 
@@ -190,6 +190,34 @@ def mpt_model_optimize(model, nbytes: int, direction: int, kinds, align: int = 1
     _check(lib().mpt_model_optimize(C.byref(_model(model)), nbytes, direction, k, n, align, b, C.byref(chunk),
                                     C.byref(ps)), "mpt_model_optimize")
     return tuple(b), chunk.value, ps.value
+
+
+def _paths_out(arr, n):
+    return [dict(kind=s.kind, share=s.share, chunk_bytes=s.chunk_bytes, ctas=s.ctas, flags=s.flags)
+            for s in arr[:n]]
+
+
+def mpt_tune(ctx: int, direction: int, nbytes: int, mode: int = MPT_MODE_GRAPH, reps: int = 0):
+    """Measure and store the best path set for this bucket; returns (paths, microseconds)."""
+    arr = (_ffi.mpt_path_spec * 4)()
+    n, us = C.c_uint32(), C.c_double()
+    _check(lib().mpt_tune(ctx, direction, nbytes, mode, reps, arr, C.byref(n), C.byref(us)), "mpt_tune")
+    return _paths_out(arr, n.value), us.value
+
+
+def mpt_tune_save(ctx: int, path: str) -> None:
+    _check(lib().mpt_tune_save(ctx, path.encode()), "mpt_tune_save")
+
+
+def mpt_tune_load(ctx: int, path: str) -> None:
+    _check(lib().mpt_tune_load(ctx, path.encode()), "mpt_tune_load")
+
+
+def mpt_tune_get(ctx: int, direction: int, nbytes: int, mode: int = MPT_MODE_GRAPH):
+    arr = (_ffi.mpt_path_spec * 4)()
+    n, us = C.c_uint32(), C.c_double()
+    _check(lib().mpt_tune_get(ctx, direction, nbytes, mode, arr, C.byref(n), C.byref(us)), "mpt_tune_get")
+    return _paths_out(arr, n.value), us.value
 
 
 def mpt_host_alloc(nbytes: int) -> int:

@@ -21,6 +21,8 @@ MPT_D2D, MPT_H2D, MPT_D2H = 0, 1, 2
 MPT_PATH_CE, MPT_PATH_SM, MPT_PATH_HS, MPT_PATH_ZC = 1, 2, 4, 8
 MPT_LAYOUT_CONTIG, MPT_LAYOUT_INTERLEAVE = 0, 1
 MPT_SM_VEC128, MPT_SM_BULK = 0, 1
+MPT_PLAN_EAGER = 0x100
+MPT_MODE_GRAPH, MPT_MODE_EAGER = 0, 1
 MPT_SHARE_ONE = 65536
 MPT_MAX_PATHS = 8
 MPT_MAX_CHUNKS = 1 << 20
@@ -84,6 +86,12 @@ SIGNATURES = {
                                  P(C.c_uint64)]),
     "mpt_model_optimize": (C.c_int, [P(mpt_model), C.c_uint64, C.c_uint32, P(C.c_uint32), C.c_uint32, C.c_uint32,
                                      P(C.c_uint64), P(C.c_uint64), P(C.c_uint64)]),
+    "mpt_tune": (C.c_int, [H, C.c_uint32, C.c_uint64, C.c_uint32, C.c_uint32, P(mpt_path_spec), P(C.c_uint32),
+                           P(C.c_double)]),
+    "mpt_tune_save": (C.c_int, [H, C.c_char_p]),
+    "mpt_tune_load": (C.c_int, [H, C.c_char_p]),
+    "mpt_tune_get": (C.c_int, [H, C.c_uint32, C.c_uint64, C.c_uint32, P(mpt_path_spec), P(C.c_uint32),
+                               P(C.c_double)]),
     "mpt_host_alloc": (C.c_int, [C.c_uint64, P(C.c_void_p)]),
     "mpt_host_free": (C.c_int, [C.c_void_p]),
 }
