@@ -300,6 +300,56 @@ MPT_API mpt_status mpt_tune_load(mpt_ctx_t ctx, const char* path);
 MPT_API mpt_status mpt_tune_get(mpt_ctx_t ctx, uint32_t dir, uint64_t nbytes, uint32_t mode, mpt_path_spec* out,
                                 uint32_t* out_n, double* out_us);
 
+/* ---- batched transfers (persistent descriptor-table kernel, replayed graph) ----------- */
+
+/* Size the context's batch ring: `slots` batches in flight at once (default 4), up to
+ * `max_xfers` transfers per batch (default 4096), `ctas` CTAs of the batch kernel
+ * (default 2 x SMs) and `tile_bytes` per work item (default 64 KiB; >= 4096, multiple of
+ * 16).  0 keeps a default.  Waits for the device; fails with EAGAIN while a batch is held.
+ * The ring is built on first use with defaults when this is never called. */
+MPT_API mpt_status mpt_batch_configure(mpt_ctx_t ctx, uint32_t slots, uint32_t max_xfers, uint32_t ctas,
+                                       uint32_t tile_bytes);
+
+/* Register an arena (this GPU's memory or page-locked host memory) so that batch
+ * descriptors inside it are classified without per-pointer runtime queries.  The caller
+ * keeps ownership; the arena must stay allocated while registered. */
+MPT_API mpt_status mpt_batch_register(mpt_ctx_t ctx, const void* base, uint64_t bytes);
+
+/* Move n transfers in one launch of the persistent batch kernel, as one replay of a slot's
+ * graph on `stream` (windowed transfers, Sec. 5.3: many messages in flight, one launch).
+ * Each xfer: D2D (device -> device), H2D (page-locked host -> device, read over the host
+ * link by the kernel) or D2H (device -> page-locked host).  Destinations must not overlap
+ * (Sec. 4.5: each transfer owns its region).  The descriptor table is copied into the
+ * slot, so `xfers` may be reused on return.  *out is owned by the caller until
+ * mpt_batch_release, which frees the slot.  Errors: EINVAL (bad descriptor, overlapping
+ * destinations, n outside 1..max_xfers), EAGAIN (every slot held), ECUDA. */
+MPT_API mpt_status mpt_batch_submit(mpt_ctx_t ctx, const mpt_xfer* xfers, size_t n, void* stream, mpt_batch_t* out);
+
+/* Non-blocking: number of the batch's transfers that have completed (their destination
+ * bytes are written and visible), read from page-locked per-transfer flags the kernel
+ * raises as each transfer's last tile finishes; flags (nullable, n bytes) gets 1/0 per
+ * transfer. */
+MPT_API mpt_status mpt_batch_poll(mpt_batch_t batch, size_t* done, uint8_t* flags);
+
+/* Wait up to timeout_ns for the whole batch (bounded host wait).  ETIMEDOUT when it is
+ * still running -- the batch keeps running and may be waited for again. */
+MPT_API mpt_status mpt_batch_wait(mpt_batch_t batch, uint64_t timeout_ns);
+
+/* Completion time of every transfer in nanoseconds after the batch kernel started (device
+ * global timer); waits for the batch.  out_ns has n entries. */
+MPT_API mpt_status mpt_batch_times(mpt_batch_t batch, uint64_t* out_ns);
+
+/* Release the handle and its slot. */
+MPT_API mpt_status mpt_batch_release(mpt_batch_t batch);
+
+/* ---- failure detection self-test ---------------------------------------------------- */
+
+/* Launch the staged path's consumer kernel on one chunk whose ready flag nothing raises,
+ * with a device-side wait limit of timeout_ns (<= 10 s), and return the context status it
+ * leaves: MPT_ETIMEDOUT with *site (nullable) = the wait's site code, and the GPU usable.
+ * Demonstrates that bounded device waits report instead of hanging. */
+MPT_API mpt_status mpt_selftest_flag_timeout(mpt_ctx_t ctx, uint64_t timeout_ns, uint32_t* site);
+
 /* ---- page-locked host memory ---------------------------------------------------- */
 
 /* Allocate `nbytes` of page-locked, device-mapped host memory (usable by copy engines and

@@ -220,6 +220,60 @@ def mpt_tune_get(ctx: int, direction: int, nbytes: int, mode: int = MPT_MODE_GRA
     return _paths_out(arr, n.value), us.value
 
 
+def mpt_batch_configure(ctx: int, slots: int = 0, max_xfers: int = 0, ctas: int = 0, tile_bytes: int = 0) -> None:
+    _check(lib().mpt_batch_configure(ctx, slots, max_xfers, ctas, tile_bytes), "mpt_batch_configure")
+
+
+def mpt_batch_register(ctx: int, base, nbytes: int) -> None:
+    _check(lib().mpt_batch_register(ctx, _ptr(base), nbytes), "mpt_batch_register")
+
+
+def make_xfers(xfers):
+    """ctypes array of mpt_xfer from (src, dst, nbytes, direction) tuples."""
+    arr = (_ffi.mpt_xfer * max(1, len(xfers)))()
+    for i, (s, d, n, direction) in enumerate(xfers):
+        arr[i] = _ffi.mpt_xfer(_ptr(s), _ptr(d), n, direction, 0)
+    return arr
+
+
+def mpt_batch_submit(ctx: int, xfers, stream=None) -> int:
+    """xfers: a ctypes mpt_xfer array from make_xfers, or a list of (src, dst, nbytes, dir)."""
+    n = len(xfers)
+    arr = xfers if isinstance(xfers, C.Array) else make_xfers(xfers)
+    h = C.c_void_p()
+    _check(lib().mpt_batch_submit(ctx, arr, n, _stream(stream), C.byref(h)), "mpt_batch_submit")
+    return h.value
+
+
+def mpt_batch_poll(batch: int, n: int | None = None):
+    """(completed count, per-transfer flags or None)."""
+    done = C.c_size_t()
+    flags = (C.c_uint8 * n)() if n else None
+    _check(lib().mpt_batch_poll(batch, C.byref(done), flags), "mpt_batch_poll")
+    return done.value, (list(flags) if flags is not None else None)
+
+
+def mpt_batch_wait(batch: int, timeout_ns: int = 10 ** 10) -> None:
+    _check(lib().mpt_batch_wait(batch, timeout_ns), "mpt_batch_wait")
+
+
+def mpt_batch_times(batch: int, n: int) -> list[int]:
+    out = (C.c_uint64 * n)()
+    _check(lib().mpt_batch_times(batch, out), "mpt_batch_times")
+    return list(out)
+
+
+def mpt_batch_release(batch: int) -> None:
+    _check(lib().mpt_batch_release(batch), "mpt_batch_release")
+
+
+def mpt_selftest_flag_timeout(ctx: int, timeout_ns: int):
+    """(status, site) left by a bounded device wait on a flag nothing raises."""
+    site = C.c_uint32()
+    st = lib().mpt_selftest_flag_timeout(ctx, timeout_ns, C.byref(site))
+    return st, site.value
+
+
 def mpt_host_alloc(nbytes: int) -> int:
     p = C.c_void_p()
     _check(lib().mpt_host_alloc(nbytes, C.byref(p)), "mpt_host_alloc")

@@ -92,6 +92,14 @@ SIGNATURES = {
     "mpt_tune_load": (C.c_int, [H, C.c_char_p]),
     "mpt_tune_get": (C.c_int, [H, C.c_uint32, C.c_uint64, C.c_uint32, P(mpt_path_spec), P(C.c_uint32),
                                P(C.c_double)]),
+    "mpt_batch_configure": (C.c_int, [H, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]),
+    "mpt_batch_register": (C.c_int, [H, C.c_void_p, C.c_uint64]),
+    "mpt_batch_submit": (C.c_int, [H, P(mpt_xfer), C.c_size_t, C.c_void_p, P(H)]),
+    "mpt_batch_poll": (C.c_int, [H, P(C.c_size_t), P(C.c_uint8)]),
+    "mpt_batch_wait": (C.c_int, [H, C.c_uint64]),
+    "mpt_batch_times": (C.c_int, [H, P(C.c_uint64)]),
+    "mpt_batch_release": (C.c_int, [H]),
+    "mpt_selftest_flag_timeout": (C.c_int, [H, C.c_uint64, P(C.c_uint32)]),
     "mpt_host_alloc": (C.c_int, [C.c_uint64, P(C.c_void_p)]),
     "mpt_host_free": (C.c_int, [C.c_void_p]),
 }

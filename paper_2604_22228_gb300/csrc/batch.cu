@@ -1,0 +1,370 @@
+// Batched transfers: one persistent kernel walks a device-resident descriptor table and
+// moves many messages of uneven sizes in one launch, replayed as a CUDA graph.
+//
+// The paper's windowed benchmarks keep several messages in flight at once and find that
+// graphs pay off when many operations share one launch (Sec. 5.3, windows 1/4/16; Sec. 6).
+// Here a batch is a table of (src, dst, bytes) descriptors; the kernel's CTAs claim fixed
+// size tiles of the whole batch through one atomic cursor, so short and long messages,
+// device-to-device and host<->device ones, share the SMs without per-message launches.
+// A per-descriptor tile counter detects the last tile of a message; that CTA stamps the
+// completion time and raises the message's flag in page-locked host memory, which is how
+// a host thread (the serving loop) sees individual messages finish while the batch runs.
+//
+// Each context owns a ring of batch slots.  A slot holds the page-locked and device copies
+// of its table, its counters and flags, and one instantiated graph
+//   [table host->device copy] + [counter reset] -> [batch kernel]
+// whose parameters never change: the descriptor count lives in the table header, so any
+// batch up to the slot capacity replays the same graph.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <thread>
+
+#include "ctx.h"
+
+#define CUDA_TRY(expr)                                                                           \
+  do {                                                                                           \
+    cudaError_t e_ = (expr);                                                                     \
+    if (e_ != cudaSuccess)                                                                       \
+      return mpt::fail(MPT_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+namespace mpt {
+
+namespace {
+
+__device__ __forceinline__ uint64_t now_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Copy [0, n) bytes s -> o with the whole CTA: 16-byte vectors when both addresses are
+// 16-byte aligned, bytes for the rest.
+__device__ __forceinline__ void cta_copy(const uint8_t* s, uint8_t* o, uint64_t n) {
+  const uint32_t tid = threadIdx.x;
+  if (((reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(o)) & 15) == 0) {
+    const uint64_t nv = n >> 4;
+    const uint4* sv = reinterpret_cast<const uint4*>(s);
+    uint4* ov = reinterpret_cast<uint4*>(o);
+    uint64_t v = tid;
+    for (; v + 3 * blockDim.x < nv; v += 4 * blockDim.x) {
+      uint4 a = sv[v], b = sv[v + blockDim.x], c = sv[v + 2 * blockDim.x], d = sv[v + 3 * blockDim.x];
+      ov[v] = a;
+      ov[v + blockDim.x] = b;
+      ov[v + 2 * blockDim.x] = c;
+      ov[v + 3 * blockDim.x] = d;
+    }
+    for (; v < nv; v += blockDim.x) ov[v] = sv[v];
+    for (uint64_t b = (nv << 4) + tid; b < n; b += blockDim.x) o[b] = s[b];
+  } else {
+    for (uint64_t b = tid; b < n; b += blockDim.x) o[b] = s[b];
+  }
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kVecThreads) k_batch(BatchArgs a) {
+  __shared__ uint32_t s_item;
+  const BatchHeader h = *a.hdr;
+  if (threadIdx.x == 0) atomicMax(a.start_inv, ~now_ns());
+  while (true) {
+    if (threadIdx.x == 0) s_item = atomicAdd(a.cursor, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    __syncthreads();
+    if (item >= h.total_tiles) break;
+    // descriptor owning this tile: the last one whose first tile is <= item
+    uint32_t lo = 0, hi = h.n - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (a.desc[mid].first_tile <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchDesc d = a.desc[lo];
+    const uint64_t off = (uint64_t)(item - d.first_tile) * h.tile_bytes;
+    if (off < d.bytes) {
+      const uint64_t len = d.bytes - off < h.tile_bytes ? d.bytes - off : h.tile_bytes;
+      cta_copy(reinterpret_cast<const uint8_t*>(d.src) + off, reinterpret_cast<uint8_t*>(d.dst) + off, len);
+    }
+    if (d.flags & kDescHostDst) __threadfence_system();
+    else __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const uint32_t prev = atomicAdd(a.done + lo, 1u);
+      if (prev + 1 == d.ntiles) {
+        a.times[lo] = now_ns();
+        __threadfence_system();
+        asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(a.host_flags + lo), "r"(h.epoch) : "memory");
+      }
+    }
+  }
+}
+
+namespace {
+
+constexpr uint32_t kDefaultSlots = 4;
+constexpr uint32_t kDefaultMaxXfers = 4096;
+constexpr uint32_t kDefaultTile = 64 * 1024;
+
+uint64_t host_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+void slot_free(BatchSlot& s) {
+  if (s.exec) cudaGraphExecDestroy(s.exec);
+  if (s.graph) cudaGraphDestroy(s.graph);
+  if (s.done_ev) cudaEventDestroy(s.done_ev);
+  if (s.h_table) cudaFreeHost(s.h_table);
+  if (s.h_flags) cudaFreeHost(s.h_flags);
+  if (s.d_mem) cudaFree(s.d_mem);
+  s = BatchSlot{};
+}
+
+mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t ctas) {
+  s.max_xfers = max_xfers;
+  s.table_bytes = sizeof(BatchHeader) + (size_t)max_xfers * sizeof(BatchDesc);
+  CUDA_TRY(cudaHostAlloc(&s.h_table, s.table_bytes, cudaHostAllocPortable));
+  CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&s.h_flags), (size_t)max_xfers * sizeof(uint32_t),
+                         cudaHostAllocMapped | cudaHostAllocPortable));
+  std::memset(s.h_flags, 0, (size_t)max_xfers * sizeof(uint32_t));
+  // device block: table | ctrl (cursor, start) | done[max] | times[max]
+  const size_t ctrl_off = (s.table_bytes + 255) & ~(size_t)255;
+  s.ctrl_bytes = 256 + (size_t)max_xfers * sizeof(uint32_t);
+  const size_t times_off = (ctrl_off + s.ctrl_bytes + 255) & ~(size_t)255;
+  CUDA_TRY(cudaMalloc(&s.d_mem, times_off + (size_t)max_xfers * sizeof(uint64_t)));
+  uint8_t* base = static_cast<uint8_t*>(s.d_mem);
+  s.d_table = base;
+  s.d_ctrl = base + ctrl_off;
+  s.d_times = reinterpret_cast<unsigned long long*>(base + times_off);
+  CUDA_TRY(cudaMemset(s.d_mem, 0, times_off + (size_t)max_xfers * sizeof(uint64_t)));
+  CUDA_TRY(cudaEventCreateWithFlags(&s.done_ev, cudaEventDisableTiming));
+  s.args.hdr = reinterpret_cast<const BatchHeader*>(s.d_table);
+  s.args.desc = reinterpret_cast<const BatchDesc*>(s.d_table + sizeof(BatchHeader));
+  s.args.cursor = reinterpret_cast<uint32_t*>(s.d_ctrl);
+  s.args.start_inv = reinterpret_cast<unsigned long long*>(s.d_ctrl + 8);
+  s.args.done = reinterpret_cast<uint32_t*>(s.d_ctrl + 256);
+  s.args.times = s.d_times;
+  uint32_t* hf_dev = nullptr;
+  CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&hf_dev), s.h_flags, 0));
+  s.args.host_flags = hf_dev;
+  // graph: table copy and counter reset, then the kernel
+  CUDA_TRY(cudaGraphCreate(&s.graph, 0));
+  cudaGraphNode_t cp, ms, kn;
+  CUDA_TRY(cudaGraphAddMemcpyNode1D(&cp, s.graph, nullptr, 0, s.d_table, s.h_table, s.table_bytes,
+                                    cudaMemcpyHostToDevice));
+  cudaMemsetParams mp{};
+  mp.dst = s.d_ctrl;
+  mp.value = 0;
+  mp.elementSize = 1;
+  mp.width = s.ctrl_bytes;
+  mp.height = 1;
+  CUDA_TRY(cudaGraphAddMemsetNode(&ms, s.graph, nullptr, 0, &mp));
+  cudaGraphNode_t deps[2] = {cp, ms};
+  void* params[] = {&s.args};
+  cudaKernelNodeParams kp{};
+  kp.func = reinterpret_cast<void*>(&k_batch);
+  kp.gridDim = dim3(ctas);
+  kp.blockDim = dim3(kVecThreads);
+  kp.kernelParams = params;
+  CUDA_TRY(cudaGraphAddKernelNode(&kn, s.graph, deps, 2, &kp));
+  CUDA_TRY(cudaGraphInstantiate(&s.exec, s.graph, 0));
+  return MPT_OK;
+}
+
+// Classify [p, p+n) against registered arenas (fast path) or the CUDA runtime.
+int range_kind(mpt_ctx_t c, const void* p, uint64_t n) {
+  const uint64_t a = (uint64_t)(uintptr_t)p;
+  for (const Arena& r : c->arenas)
+    if (a >= r.base && a + n <= r.base + r.bytes && a + n >= a) return r.kind;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  if ((at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == c->device) return 0;
+  if (at.type == cudaMemoryTypeHost) return 1;
+  return -1;
+}
+
+}  // namespace
+
+mpt_status batch_setup(mpt_ctx_t c) {
+  if (!c->slots.empty()) return MPT_OK;
+  const uint32_t nslots = c->batch_slots ? c->batch_slots : kDefaultSlots;
+  const uint32_t maxx = c->batch_max_xfers ? c->batch_max_xfers : kDefaultMaxXfers;
+  const uint32_t ctas = c->batch_ctas ? c->batch_ctas : 2u * (uint32_t)c->sms;
+  if (!c->batch_tile) c->batch_tile = kDefaultTile;
+  c->slots.resize(nslots);
+  for (auto& s : c->slots) {
+    mpt_status st = slot_init(c, s, maxx, ctas);
+    if (st != MPT_OK) {
+      for (auto& t : c->slots) slot_free(t);
+      c->slots.clear();
+      return st;
+    }
+  }
+  return MPT_OK;
+}
+
+void batch_teardown(mpt_ctx_t c) {
+  for (auto& s : c->slots) slot_free(s);
+  c->slots.clear();
+}
+
+}  // namespace mpt
+
+struct mpt_batch_s {
+  mpt_ctx_t ctx;
+  uint32_t slot;
+  uint32_t epoch;
+  size_t n;
+  uint64_t submit_ns;
+};
+
+using namespace mpt;
+
+extern "C" {
+
+mpt_status mpt_batch_configure(mpt_ctx_t c, uint32_t slots, uint32_t max_xfers, uint32_t ctas, uint32_t tile_bytes) {
+  if (!c) return fail(MPT_EINVAL, "mpt_batch_configure: NULL context");
+  for (auto& s : c->slots)
+    if (s.held) return fail(MPT_EAGAIN, "mpt_batch_configure: a batch is still held");
+  if (slots > 64 || max_xfers > (1u << 20) || (tile_bytes && (tile_bytes < 4096 || tile_bytes % 16)))
+    return fail(MPT_EINVAL, "mpt_batch_configure: slots <= 64, max_xfers <= 2^20, tile >= 4096 and a multiple of 16");
+  CUDA_TRY(cudaSetDevice(c->device));
+  CUDA_TRY(cudaDeviceSynchronize());
+  batch_teardown(c);
+  c->batch_slots = slots;
+  c->batch_max_xfers = max_xfers;
+  c->batch_ctas = ctas;
+  c->batch_tile = tile_bytes;
+  return batch_setup(c);
+}
+
+mpt_status mpt_batch_register(mpt_ctx_t c, const void* base, uint64_t bytes) {
+  if (!c || !base || bytes == 0) return fail(MPT_EINVAL, "mpt_batch_register: bad argument");
+  CUDA_TRY(cudaSetDevice(c->device));
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, base) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(MPT_EINVAL, "mpt_batch_register: %p is not CUDA memory", base);
+  }
+  int kind;
+  if ((at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == c->device) kind = 0;
+  else if (at.type == cudaMemoryTypeHost) kind = 1;
+  else return fail(MPT_EINVAL, "mpt_batch_register: %p is neither this GPU's memory nor page-locked host memory", base);
+  c->arenas.push_back(Arena{(uint64_t)(uintptr_t)base, bytes, kind});
+  return MPT_OK;
+}
+
+mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* stream, mpt_batch_t* out) {
+  if (!c || !out || (n > 0 && !xfers)) return fail(MPT_EINVAL, "mpt_batch_submit: NULL argument");
+  *out = nullptr;
+  CUDA_TRY(cudaSetDevice(c->device));
+  mpt_status st = batch_setup(c);
+  if (st != MPT_OK) return st;
+  if (n == 0 || n > c->slots[0].max_xfers)
+    return fail(MPT_EINVAL, "mpt_batch_submit: %zu transfers (1..%u per batch)", n, c->slots[0].max_xfers);
+  uint32_t si = 0;
+  while (si < c->slots.size() && c->slots[si].held) ++si;
+  if (si == c->slots.size()) return fail(MPT_EAGAIN, "mpt_batch_submit: every batch slot is held");
+  BatchSlot& s = c->slots[si];
+  // validate: direction, memory kinds, and non-overlapping destinations (Sec. 4.5: each
+  // transfer owns its destination region)
+  std::vector<std::pair<uint64_t, uint64_t>> spans;
+  spans.reserve(n);
+  for (size_t i = 0; i < n; ++i) {
+    const mpt_xfer& x = xfers[i];
+    if (x.dir > MPT_D2H) return fail(MPT_EINVAL, "mpt_batch_submit: transfer %zu has direction %u", i, x.dir);
+    if (x.bytes == 0) continue;
+    if (!x.src || !x.dst) return fail(MPT_EINVAL, "mpt_batch_submit: transfer %zu has a NULL pointer", i);
+    const int ks = range_kind(c, x.src, x.bytes), kd = range_kind(c, x.dst, x.bytes);
+    const int want_s = x.dir == MPT_H2D ? 1 : 0, want_d = x.dir == MPT_D2H ? 1 : 0;
+    if (ks != want_s || kd != want_d)
+      return fail(MPT_EINVAL, "mpt_batch_submit: transfer %zu: pointers do not match direction %u", i, x.dir);
+    spans.emplace_back((uint64_t)(uintptr_t)x.dst, (uint64_t)(uintptr_t)x.dst + x.bytes);
+  }
+  std::sort(spans.begin(), spans.end());
+  for (size_t i = 1; i < spans.size(); ++i)
+    if (spans[i].first < spans[i - 1].second)
+      return fail(MPT_EINVAL, "mpt_batch_submit: destination regions overlap");
+  // the slot's previous batch must be done reading its table
+  CUDA_TRY(cudaEventSynchronize(s.done_ev));
+  s.epoch++;
+  if (s.epoch == 0) s.epoch = 1;
+  BatchHeader* h = reinterpret_cast<BatchHeader*>(s.h_table);
+  BatchDesc* d = reinterpret_cast<BatchDesc*>(s.h_table + sizeof(BatchHeader));
+  uint64_t tiles = 0;
+  const uint64_t tile = c->batch_tile;
+  for (size_t i = 0; i < n; ++i) {
+    const mpt_xfer& x = xfers[i];
+    const uint64_t t = std::max<uint64_t>(1, (x.bytes + tile - 1) / tile);
+    d[i] = BatchDesc{(uint64_t)(uintptr_t)x.src, (uint64_t)(uintptr_t)x.dst, x.bytes, (uint32_t)tiles, (uint32_t)t,
+                     x.dir == MPT_D2H ? kDescHostDst : 0u, 0u};
+    tiles += t;
+  }
+  if (tiles >= (1ull << 32)) return fail(MPT_EINVAL, "mpt_batch_submit: batch too large for 32-bit tile indices");
+  *h = BatchHeader{(uint32_t)n, (uint32_t)tiles, (uint32_t)tile, s.epoch};
+  const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  CUDA_TRY(cudaGraphLaunch(s.exec, cs));
+  CUDA_TRY(cudaEventRecord(s.done_ev, cs));
+  s.held = true;
+  s.n = n;
+  mpt_batch_s* b = new mpt_batch_s{c, si, s.epoch, n, host_ns()};
+  *out = b;
+  return MPT_OK;
+}
+
+mpt_status mpt_batch_poll(mpt_batch_t b, size_t* done, uint8_t* flags) {
+  if (!b || !done) return fail(MPT_EINVAL, "mpt_batch_poll: NULL argument");
+  const BatchSlot& s = b->ctx->slots[b->slot];
+  volatile const uint32_t* f = s.h_flags;
+  size_t k = 0;
+  for (size_t i = 0; i < b->n; ++i) {
+    const bool fin = f[i] == b->epoch;
+    k += fin;
+    if (flags) flags[i] = fin ? 1 : 0;
+  }
+  *done = k;
+  return MPT_OK;
+}
+
+mpt_status mpt_batch_wait(mpt_batch_t b, uint64_t timeout_ns) {
+  if (!b) return fail(MPT_EINVAL, "mpt_batch_wait: NULL batch");
+  const BatchSlot& s = b->ctx->slots[b->slot];
+  const uint64_t t0 = host_ns();
+  while (true) {
+    const cudaError_t e = cudaEventQuery(s.done_ev);
+    if (e == cudaSuccess) break;
+    if (e != cudaErrorNotReady) return fail(MPT_ECUDA, "mpt_batch_wait: %s", cudaGetErrorString(e));
+    if (host_ns() - t0 >= timeout_ns) return fail(MPT_ETIMEDOUT, "mpt_batch_wait: batch still running");
+    std::this_thread::yield();
+  }
+  return MPT_OK;
+}
+
+mpt_status mpt_batch_times(mpt_batch_t b, uint64_t* out_ns) {
+  if (!b || !out_ns) return fail(MPT_EINVAL, "mpt_batch_times: NULL argument");
+  const BatchSlot& s = b->ctx->slots[b->slot];
+  CUDA_TRY(cudaEventSynchronize(s.done_ev));
+  std::vector<unsigned long long> t(b->n + 1);
+  unsigned long long start_inv = 0;
+  CUDA_TRY(cudaMemcpy(t.data(), s.d_times, b->n * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(&start_inv, s.args.start_inv, sizeof start_inv, cudaMemcpyDeviceToHost));
+  const unsigned long long start = ~start_inv;
+  for (size_t i = 0; i < b->n; ++i) out_ns[i] = t[i] >= start ? t[i] - start : 0;
+  return MPT_OK;
+}
+
+mpt_status mpt_batch_release(mpt_batch_t b) {
+  if (!b) return MPT_OK;
+  BatchSlot& s = b->ctx->slots[b->slot];
+  if (s.held && s.epoch == b->epoch) s.held = false;
+  delete b;
+  return MPT_OK;
+}
+
+}  // extern "C"

@@ -42,6 +42,34 @@ struct TuneEntry {
   double us = 0;
 };
 
+// A registered arena: batch descriptors inside it skip per-pointer runtime queries.
+struct Arena {
+  uint64_t base, bytes;
+  int kind;  // 0 device, 1 page-locked host
+};
+
+// One slot of the batch ring (see batch.cu).
+struct BatchSlot {
+  uint32_t max_xfers = 0;
+  size_t table_bytes = 0, ctrl_bytes = 0;
+  uint8_t* h_table = nullptr;   // page-locked table, copied to d_table by the graph
+  uint32_t* h_flags = nullptr;  // page-locked, mapped: per-descriptor completion epochs
+  void* d_mem = nullptr;
+  uint8_t* d_table = nullptr;
+  uint8_t* d_ctrl = nullptr;
+  unsigned long long* d_times = nullptr;
+  BatchArgs args{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done_ev = nullptr;
+  uint32_t epoch = 0;
+  bool held = false;
+  size_t n = 0;
+};
+
+mpt_status batch_setup(mpt_ctx_t c);
+void batch_teardown(mpt_ctx_t c);
+
 inline uint32_t tune_key(uint32_t dir, uint32_t mode, uint32_t bucket) { return (dir << 16) | (mode << 8) | bucket; }
 
 uint32_t size_bucket(uint64_t nbytes);
@@ -84,4 +112,8 @@ struct mpt_ctx_s {
   uint64_t tune_host_bytes = 0;
   void* flush = nullptr;              // L2 flush buffer
   uint64_t flush_bytes = 0;
+  // batched transfers
+  std::vector<mpt::BatchSlot> slots;
+  std::vector<mpt::Arena> arenas;
+  uint32_t batch_slots = 0, batch_max_xfers = 0, batch_ctas = 0, batch_tile = 0;
 };

@@ -74,6 +74,36 @@ struct StageArgs {
 
 __global__ void k_stage_consume(StageArgs a);
 
+// ---- batched transfers: persistent descriptor-table kernel --------------------------
+constexpr uint32_t kDescHostDst = 1;  // destination is host memory: publish with system fences
+
+struct BatchHeader {
+  uint32_t n;            // descriptors in this batch
+  uint32_t total_tiles;  // sum of tiles over descriptors
+  uint32_t tile_bytes;
+  uint32_t epoch;        // value written to a finished descriptor's host flag
+};
+
+struct BatchDesc {
+  uint64_t src, dst, bytes;
+  uint32_t first_tile;  // prefix sum of tiles before this descriptor
+  uint32_t ntiles;      // max(1, ceil(bytes / tile))
+  uint32_t flags;
+  uint32_t pad;
+};
+
+struct BatchArgs {
+  const BatchHeader* hdr;
+  const BatchDesc* desc;
+  uint32_t* cursor;              // next tile to claim (reset to 0 per launch)
+  unsigned long long* start_inv; // ~(kernel start time), max over CTAs
+  uint32_t* done;                // tiles finished per descriptor (reset per launch)
+  unsigned long long* times;     // completion time per descriptor (global timer, ns)
+  uint32_t* host_flags;          // device alias of page-locked flags, one per descriptor
+};
+
+__global__ void k_batch(BatchArgs a);
+
 // ---- digest (test utility) -------------------------------------------------------
 __global__ void k_hash(const uint8_t* p, uint64_t n, unsigned long long* out);
 

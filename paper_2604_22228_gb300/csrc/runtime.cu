@@ -542,6 +542,7 @@ mpt_status mpt_ctx_destroy(mpt_ctx_t c) {
   if (!c) return MPT_OK;
   cudaSetDevice(c->device);
   cudaDeviceSynchronize();
+  batch_teardown(c);
   // Drop the cache's references; graphs the caller still holds lose their executable.
   while (!c->lru.empty()) cache_drop(c, c->lru.front());
   for (mpt_graph_s* g : c->live) {
@@ -706,6 +707,37 @@ mpt_status mpt_hash_device(mpt_ctx_t c, const void* ptr, uint64_t nbytes, void* 
   CUDA_TRY(cudaStreamSynchronize(s));
   *out = h;
   return MPT_OK;
+}
+
+mpt_status mpt_selftest_flag_timeout(mpt_ctx_t c, uint64_t timeout_ns, uint32_t* site) {
+  if (!c) return fail(MPT_EINVAL, "mpt_selftest_flag_timeout: NULL context");
+  if (timeout_ns == 0 || timeout_ns > 10000000000ull)
+    return fail(MPT_EINVAL, "mpt_selftest_flag_timeout: timeout must be in (0, 10 s]");
+  CUDA_TRY(cudaSetDevice(c->device));
+  CUDA_TRY(cudaDeviceSynchronize());
+  // one staged chunk whose ready flag nothing ever raises
+  void* mem = nullptr;
+  CUDA_TRY(cudaMalloc(&mem, 8192));
+  CUDA_TRY(cudaMemset(mem, 0, 8192));
+  uint8_t* m8 = static_cast<uint8_t*>(mem);
+  StageChunk ch{0, 0, 1024};
+  CUDA_TRY(cudaMemcpy(m8 + 256, &ch, sizeof ch, cudaMemcpyHostToDevice));
+  StageArgs sa{};
+  sa.stage = m8 + 4096;
+  sa.dst = m8 + 6144;
+  sa.chunks = reinterpret_cast<const StageChunk*>(m8 + 256);
+  sa.ready = reinterpret_cast<uint32_t*>(m8);
+  sa.done = reinterpret_cast<uint32_t*>(m8 + 64);
+  sa.nchunks = 1;
+  sa.tiles_per_chunk = 1;
+  sa.status = c->d_status;
+  sa.timeout_ns = timeout_ns;
+  k_stage_consume<<<1, kVecThreads>>>(sa);
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  cudaFree(mem);
+  if (e != cudaSuccess) return fail(MPT_ECUDA, "mpt_selftest_flag_timeout: %s", cudaGetErrorString(e));
+  return mpt_ctx_status(c, site);
 }
 
 mpt_status mpt_host_alloc(uint64_t nbytes, void** out) {

@@ -1,0 +1,226 @@
+"""GPU parity of the batched path (persistent descriptor-table kernel) against the oracle,
+plus its host-visible completion flags, slot ring, bounded waits and validation."""
+import numpy as np
+import pytest
+
+import paper_2604_22228_gb300 as mpt
+import payload
+from oracle import transfer as T
+
+pytestmark = pytest.mark.gpu
+MiB = 1 << 20
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    torch.cuda.init()
+    from paper_2604_22228_gb300 import build
+    build.build()
+    c = mpt.mpt_ctx_create(0)
+    yield c
+    st, site = mpt.mpt_ctx_status(c)
+    mpt.mpt_ctx_destroy(c)
+    assert st == mpt.MPT_OK, (st, site)
+
+
+class Workload:
+    """Transfers of the batched workload's shape (log-uniform sizes, 70% device-to-device,
+    30% host-to-device, 16-byte gaps) packed into a device source arena, a page-locked host
+    source arena and a device destination arena."""
+
+    def __init__(self, n, seed, max_bytes, kind="bf16", d2h=False):
+        import torch
+        sizes, d2d, gaps = payload.batch_workload(n, seed, 256, max_bytes)
+        self.items = []
+        offs = {"dev": 0, "host": 0, "dst": 0}
+        for sz, is_d2d, gap in zip(sizes, d2d, gaps):
+            arena = "dev" if (is_d2d or d2h) else "host"
+            offs[arena] += gap
+            offs["dst"] += gap
+            self.items.append((arena, offs[arena], offs["dst"], sz))
+            offs[arena] += sz
+            offs["dst"] += sz
+        self.src_np = {a: payload.fill(kind, seed + i + 1, max(16, offs[a] + 64)) for i, a in enumerate(("dev", "host"))}
+        self.src = {"dev": torch.from_numpy(self.src_np["dev"]).cuda(),
+                    "host": torch.from_numpy(self.src_np["host"]).pin_memory()}
+        dst_bytes = offs["dst"] + 64
+        self.d2h = d2h
+        if d2h:
+            self.dst = torch.full((dst_bytes,), 0x5A, dtype=torch.uint8).pin_memory()
+        else:
+            self.dst = torch.full((dst_bytes,), 0x5A, dtype=torch.uint8, device="cuda")
+        self.dst_init = np.full(dst_bytes, 0x5A, dtype=np.uint8)
+        direction = lambda a: (mpt.MPT_D2H if d2h else (mpt.MPT_D2D if a == "dev" else mpt.MPT_H2D))
+        self.xfers = [(self.src[a].data_ptr() + s, self.dst.data_ptr() + d, sz, direction(a))
+                      for a, s, d, sz in self.items]
+
+    def expected(self):
+        return T.batch_expected(self.dst_init, self.src_np, self.items)
+
+    def result(self):
+        import torch
+        torch.cuda.synchronize()
+        return self.dst.cpu().numpy() if not self.d2h else self.dst.numpy().copy()
+
+
+@pytest.mark.parametrize("n,max_bytes", [(1, 4096), (37, 64 * 1024), (300, MiB), (1000, 4 * MiB)])
+def test_batch_matches_oracle(ctx, n, max_bytes):
+    import torch
+    w = Workload(n, payload.SEED_BATCH + n, max_bytes)
+    b = mpt.mpt_batch_submit(ctx, w.xfers, torch.cuda.current_stream())
+    mpt.mpt_batch_wait(b)
+    done, flags = mpt.mpt_batch_poll(b, n)
+    times = mpt.mpt_batch_times(b, n)
+    mpt.mpt_batch_release(b)
+    assert done == n and all(flags)
+    assert all(0 <= t < 10 ** 10 for t in times)
+    assert np.array_equal(w.result(), w.expected())
+
+
+def test_batch_slots_replay_and_reuse(ctx):
+    import torch
+    s = torch.cuda.current_stream()
+    for rep in range(10):
+        w = Workload(64, 900 + rep, 256 * 1024, kind="u32")
+        b = mpt.mpt_batch_submit(ctx, w.xfers, s)
+        mpt.mpt_batch_wait(b)
+        mpt.mpt_batch_release(b)
+        assert np.array_equal(w.result(), w.expected()), rep
+
+
+def test_batch_device_to_host_flags_publish_data(ctx):
+    """Once a transfer's host flag reads done, its destination bytes in page-locked host
+    memory are already there -- no stream synchronisation needed."""
+    import time
+    import torch
+    w = Workload(200, 77, MiB, kind="u8", d2h=True)
+    b = mpt.mpt_batch_submit(ctx, w.xfers, torch.cuda.current_stream())
+    exp = w.expected()
+    host = w.dst.numpy()
+    seen = set()
+    t0 = time.time()
+    while len(seen) < len(w.items) and time.time() - t0 < 30:
+        _, flags = mpt.mpt_batch_poll(b, len(w.items))
+        for i, f in enumerate(flags):
+            if f and i not in seen:
+                _, _, d, sz = w.items[i]
+                assert np.array_equal(host[d:d + sz], exp[d:d + sz]), i
+                seen.add(i)
+    mpt.mpt_batch_wait(b)
+    mpt.mpt_batch_release(b)
+    assert len(seen) == len(w.items)
+
+
+def test_batch_ring_full_then_free(ctx):
+    import torch
+    w = Workload(8, 5, 4096)
+    held = [mpt.mpt_batch_submit(ctx, w.xfers[i:i + 1], torch.cuda.current_stream()) for i in range(4)]
+    with pytest.raises(mpt.MptError) as e:
+        mpt.mpt_batch_submit(ctx, w.xfers[4:5])
+    assert e.value.status == mpt.MPT_EAGAIN
+    mpt.mpt_batch_release(held.pop(0))
+    held.append(mpt.mpt_batch_submit(ctx, w.xfers[4:5], torch.cuda.current_stream()))
+    for b in held:
+        mpt.mpt_batch_wait(b)
+        mpt.mpt_batch_release(b)
+
+
+def test_batch_bounded_host_wait(ctx):
+    import torch
+    src = torch.empty(512 * MiB, dtype=torch.uint8).pin_memory()
+    dst = torch.empty(512 * MiB, dtype=torch.uint8, device="cuda")
+    xfers = [(src.data_ptr() + i * 16 * MiB, dst.data_ptr() + i * 16 * MiB, 16 * MiB, mpt.MPT_H2D) for i in range(32)]
+    b = mpt.mpt_batch_submit(ctx, xfers, torch.cuda.current_stream())
+    with pytest.raises(mpt.MptError) as e:
+        mpt.mpt_batch_wait(b, 1000)  # 1 us: the 512 MiB host-to-device batch is still running
+    assert e.value.status == mpt.MPT_ETIMEDOUT
+    mpt.mpt_batch_wait(b)  # and it completes when waited for again
+    mpt.mpt_batch_release(b)
+    torch.cuda.synchronize()
+    assert torch.equal(src[:MiB].cuda(), dst[:MiB]) and torch.equal(src[-MiB:].cuda(), dst[-MiB:])
+
+
+def test_batch_rejects_bad_descriptors(ctx):
+    import torch
+    a = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    h = torch.zeros(1 << 16, dtype=torch.uint8).pin_memory()
+    p, q = a.data_ptr(), h.data_ptr()
+    bad = [
+        [(p, p + 4096, 100, mpt.MPT_D2D), (p + 8192, p + 4096 + 50, 100, mpt.MPT_D2D)],  # overlapping dst
+        [(p, p + 4096, 100, mpt.MPT_H2D)],  # host-to-device from device memory
+        [(q, p, 100, mpt.MPT_D2D)],         # device-to-device from host memory
+        [(p, 0, 100, mpt.MPT_D2D)],         # NULL destination
+        [(p, p + 4096, 100, 7)],            # unknown direction
+    ]
+    for xf in bad:
+        with pytest.raises(mpt.MptError) as e:
+            mpt.mpt_batch_submit(ctx, xf)
+        assert e.value.status == mpt.MPT_EINVAL, xf
+    with pytest.raises(mpt.MptError):
+        mpt.mpt_batch_submit(ctx, [])
+
+
+def test_device_wait_gives_up_and_reports(ctx):
+    """Failure detection without a fault: a flag nothing raises makes the bounded device
+    wait give up, record MPT_ETIMEDOUT, and leave the GPU usable."""
+    import torch
+    st, site = mpt.mpt_selftest_flag_timeout(ctx, 50_000_000)
+    assert st == mpt.MPT_ETIMEDOUT and site == 2
+    assert mpt.mpt_ctx_status(ctx)[0] == mpt.MPT_OK  # reset after being read
+    x = torch.arange(4096, dtype=torch.int32, device="cuda")
+    y = torch.zeros_like(x)
+    mpt.mpt_sm_copy(ctx, y.data_ptr(), x.data_ptr(), x.numel() * 4)
+    torch.cuda.synchronize()
+    assert torch.equal(x, y)
+
+
+@pytest.mark.slow
+def test_batch_full_size_workload(ctx):
+    """4096 transfers of 256 B..16 MiB (about 5.9 GiB), 70% device-to-device, 30% host-to-
+    device: every destination's digest equals its source's, and sampled transfers equal the
+    oracle byte for byte."""
+    import torch
+    period = 64 * MiB
+    sizes, d2d, gaps = payload.batch_workload(4096)
+    items, offs = [], {"dev": 0, "host": 0, "dst": 0}
+    for sz, is_d2d, gap in zip(sizes, d2d, gaps):
+        a = "dev" if is_d2d else "host"
+        offs[a] += gap
+        offs["dst"] += gap
+        items.append((a, offs[a], offs["dst"], sz))
+        offs[a] += sz
+        offs["dst"] += sz
+    base = payload.fill("bf16", payload.SEED_BATCH, period)
+    base_t = torch.from_numpy(base)
+
+    def arena(nbytes, pinned):
+        t = torch.empty(nbytes, dtype=torch.uint8).pin_memory() if pinned else \
+            torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        src = base_t.to(t.device)
+        for o in range(0, nbytes, period):
+            m = min(period, nbytes - o)
+            t[o:o + m].copy_(src[:m])
+        return t
+
+    src = {"dev": arena(offs["dev"] + 64, False), "host": arena(offs["host"] + 64, True)}
+    dst = torch.zeros(offs["dst"] + 64, dtype=torch.uint8, device="cuda")
+    mpt.mpt_batch_register(ctx, src["dev"].data_ptr(), src["dev"].numel())
+    mpt.mpt_batch_register(ctx, src["host"].data_ptr(), src["host"].numel())
+    mpt.mpt_batch_register(ctx, dst.data_ptr(), dst.numel())
+    xfers = [(src[a].data_ptr() + s, dst.data_ptr() + d, sz, mpt.MPT_D2D if a == "dev" else mpt.MPT_H2D)
+             for a, s, d, sz in items]
+    b = mpt.mpt_batch_submit(ctx, xfers, torch.cuda.current_stream())
+    mpt.mpt_batch_wait(b, 60 * 10 ** 9)
+    assert mpt.mpt_batch_poll(b)[0] == 4096
+    mpt.mpt_batch_release(b)
+    for a, s, d, sz in items:
+        assert mpt.mpt_hash_device(ctx, dst.data_ptr() + d, sz) == \
+            mpt.mpt_hash_device(ctx, src[a].data_ptr() + s, sz)
+    rng = np.random.default_rng(4)
+    out = dst.cpu().numpy()
+    for i in rng.choice(len(items), 48, replace=False):
+        a, s, d, sz = items[i]
+        want = np.concatenate([base, base])[s % period: s % period + sz] if sz <= period else None
+        if want is not None:
+            assert np.array_equal(out[d:d + sz], want), i
