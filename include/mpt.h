@@ -350,6 +350,24 @@ MPT_API mpt_status mpt_batch_release(mpt_batch_t batch);
  * Demonstrates that bounded device waits report instead of hanging. */
 MPT_API mpt_status mpt_selftest_flag_timeout(mpt_ctx_t ctx, uint64_t timeout_ns, uint32_t* site);
 
+/* ---- digests without allocation ------------------------------------------------------ */
+
+/* Digests (the mpt_hash_device function) of n device byte ranges, computed on `stream`,
+ * waited for, and written to out[0..n).  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need it (a caller-owned
+ * memory budget or allocator that must not be bypassed, or code that must not trigger the
+ * device synchronisation cudaMalloc/cudaFree can cause).  It allocates nothing: the
+ * per-range accumulators live in a static device array of MPT_NOALLOC_MAX_RANGES entries
+ * (8 KiB) that every GPU loading the library holds until the process exits.  No context
+ * is needed; it runs on the current device.  The first call on a device looks up the
+ * array's device address once; make that first call before any stream capture.  Every
+ * call shares the array, so calls whose work overlaps on the GPU (different streams or
+ * host threads at the same time) race and must be serialised by the caller.  Errors:
+ * EINVAL (n above the maximum, NULL argument), ECUDA. */
+#define MPT_NOALLOC_MAX_RANGES 1024u
+MPT_API mpt_status mpt_hash_ranges_noalloc(const void* const* ptrs, const uint64_t* nbytes, uint32_t n, void* stream,
+                                           uint64_t* out);
+
 /* ---- page-locked host memory ---------------------------------------------------- */
 
 /* Allocate `nbytes` of page-locked, device-mapped host memory (usable by copy engines and

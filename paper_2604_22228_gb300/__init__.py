@@ -17,7 +17,7 @@ import ctypes as C
 
 from . import _ffi
 from ._ffi import (MPT_D2D, MPT_D2H, MPT_H2D, MPT_LAYOUT_CONTIG, MPT_LAYOUT_INTERLEAVE, MPT_MAX_CHUNKS,  # noqa: F401
-                   MPT_MAX_PATHS, MPT_PATH_CE, MPT_PATH_HS, MPT_PATH_SM, MPT_PATH_ZC, MPT_SHARE_ONE, MPT_SM_BULK,
+                   MPT_NOALLOC_MAX_RANGES, MPT_MAX_PATHS, MPT_PATH_CE, MPT_PATH_HS, MPT_PATH_SM, MPT_PATH_ZC, MPT_SHARE_ONE, MPT_SM_BULK,
                    MPT_SM_VEC128, MPT_PLAN_EAGER, MPT_MODE_GRAPH, MPT_MODE_EAGER, STATUS_NAMES)
 from ._ffi import MPT_EAGAIN, MPT_ECUDA, MPT_EINVAL, MPT_ENOMEM, MPT_ENOTSUP, MPT_ETIMEDOUT, MPT_OK  # noqa: F401
 
@@ -272,6 +272,16 @@ def mpt_selftest_flag_timeout(ctx: int, timeout_ns: int):
     site = C.c_uint32()
     st = lib().mpt_selftest_flag_timeout(ctx, timeout_ns, C.byref(site))
     return st, site.value
+
+
+def mpt_hash_ranges_noalloc(ranges, stream=None) -> list[int]:
+    """Digests of [(pointer, nbytes), ...] without any allocation (see include/mpt.h)."""
+    n = len(ranges)
+    ptrs = (C.c_void_p * max(1, n))(*[_ptr(p) for p, _ in ranges])
+    sizes = (C.c_uint64 * max(1, n))(*[b for _, b in ranges])
+    out = (C.c_uint64 * max(1, n))()
+    _check(lib().mpt_hash_ranges_noalloc(ptrs, sizes, n, _stream(stream), out), "mpt_hash_ranges_noalloc")
+    return list(out[:n])
 
 
 def mpt_host_alloc(nbytes: int) -> int:

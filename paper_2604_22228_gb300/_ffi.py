@@ -26,6 +26,7 @@ MPT_MODE_GRAPH, MPT_MODE_EAGER = 0, 1
 MPT_SHARE_ONE = 65536
 MPT_MAX_PATHS = 8
 MPT_MAX_CHUNKS = 1 << 20
+MPT_NOALLOC_MAX_RANGES = 1024
 
 
 class mpt_path_spec(C.Structure):
@@ -100,6 +101,7 @@ SIGNATURES = {
     "mpt_batch_times": (C.c_int, [H, P(C.c_uint64)]),
     "mpt_batch_release": (C.c_int, [H]),
     "mpt_selftest_flag_timeout": (C.c_int, [H, C.c_uint64, P(C.c_uint32)]),
+    "mpt_hash_ranges_noalloc": (C.c_int, [P(C.c_void_p), P(C.c_uint64), C.c_uint32, C.c_void_p, P(C.c_uint64)]),
     "mpt_host_alloc": (C.c_int, [C.c_uint64, P(C.c_void_p)]),
     "mpt_host_free": (C.c_int, [C.c_void_p]),
 }
