@@ -57,6 +57,23 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
+def roofline_traffic(variant: str, ctas: int):
+    """DRAM bytes per 1 GiB launch from the committed ncu summary, or None when the kernel
+    source changed since the capture (or no capture exists for this variant/launch)."""
+    import hashlib
+    import re
+    prof = os.path.join(ROOT, "profiles", f"k_sm_copy_{variant}_1GiB.md")
+    if not os.path.exists(prof) or ctas not in (0,):
+        return None
+    text = open(prof).read()
+    m = re.search(r"traffic_bytes_per_launch \| (\d+)", text)
+    h = re.search(r"copy_kernels.cu\): ([0-9a-f]{64})", text)
+    src = os.path.join(ROOT, "paper_2604_22228_gb300", "csrc", "copy_kernels.cu")
+    if not m or not h or hashlib.sha256(open(src, "rb").read()).hexdigest() != h.group(1):
+        return None
+    return int(m.group(1))
+
+
 # ---- clocks sampled during the timed region ---------------------------------------------
 
 class ClockSampler:
@@ -446,18 +463,7 @@ def run_ours(args):
                 if per_size_tuned[i] > 0 else None})
         sweep.append(row)
 
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "roofline_traffic.json")
-    if os.path.exists(prof):
-        try:
-            import hashlib
-            info = json.load(open(prof))
-            src_sha = hashlib.sha256(open(os.path.join(ROOT, "paper_2604_22228_gb300", "csrc",
-                                                       "copy_kernels.cu"), "rb").read()).hexdigest()
-            if info.get("kernel_source_sha256") == src_sha and info.get("variant") == int(variant):
-                traffic = info.get("traffic_bytes_per_launch_1GiB")
-        except Exception:
-            traffic = None
+    traffic = roofline_traffic("vec" if variant == 0 else "bulk", ctas)
 
     for g in tuned_graphs:
         mpt.mpt_graph_release(g)
