@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -363,6 +364,7 @@ def run_ours(args):
     reps = args.baseline_reps
     base = {}
     if not args.no_baselines:
+        base["tuned"] = time_graphs(tuned_graphs, reps)
         for kind in ("ce", "sm", "split"):
             plans, graphs = capture_all(kind)
             base[kind] = time_graphs(graphs, reps)
@@ -441,6 +443,20 @@ def run_ours(args):
         for p in (up, down):
             mpt.mpt_plan_destroy(p)
 
+    lifecycle = run_graph_lifecycle(mpt, torch, ctx, stream)
+    host_sweep = None
+    if not args.no_host_sweep:
+        host_sweep = run_host_sweep(mpt, torch, ctx, stream)
+        ok = ok and host_sweep["parity_ok"]
+    batched = None
+    if not args.no_batched:
+        batched = run_batched(mpt, torch, ctx, stream)
+        ok = ok and batched["parity_ok"]
+    serving = None
+    if args.serve_seconds > 0:
+        serving = run_serving(mpt, torch, ctx, [float(r) for r in args.serve_rates.split(",")], args.serve_seconds)
+        ok = ok and all(r["errors"] == 0 for r in serving)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         gbs, el, moved, desc = cpu_oracle_sample({}, budget_s=args.cpu_seconds)
@@ -449,18 +465,18 @@ def run_ours(args):
     sweep = []
     for i, n in enumerate(SIZES):
         gb = lambda ms: round(n / (ms / 1e3) / 1e9, 3) if ms and ms > 0 else None
-        row = {"bytes": n, "tuned_graph_gbs": gb(per_size_tuned[i]),
+        row = {"bytes": n, "in_sweep_gbs": gb(per_size_tuned[i]),
                "plan": [(p["kind"], p["share"], p["chunk_bytes"], p["ctas"], p["flags"])
                         for p in mpt.mpt_plan_paths(tuned_plans[i])]}
         if base:
             best_single = min(base["ce"][i], base["sm"][i])
             row.update({
+                "tuned_graph_gbs": gb(base["tuned"][i]),
                 "ce_graph_gbs": gb(base["ce"][i]), "sm_graph_gbs": gb(base["sm"][i]),
                 "split50_graph_gbs": gb(base["split"][i]), "split50_eager_gbs": gb(base["split_eager"][i]),
                 "tuned_eager_gbs": gb(base["tuned_eager"][i]), "best_single_gbs": gb(best_single),
-                "tuned_vs_best_single": round(best_single / per_size_tuned[i], 3) if per_size_tuned[i] > 0 else None,
-                "tuned_graph_vs_tuned_eager": round(base["tuned_eager"][i] / per_size_tuned[i], 3)
-                if per_size_tuned[i] > 0 else None})
+                "tuned_vs_best_single": round(best_single / base["tuned"][i], 3),
+                "tuned_graph_vs_tuned_eager": round(base["tuned_eager"][i] / base["tuned"][i], 3)})
         sweep.append(row)
 
     traffic = roofline_traffic("vec" if variant == 0 else "bulk", ctas)
@@ -488,10 +504,360 @@ def run_ours(args):
                          "peak_source": f"{peak_kind} hbm_gbs (burst)"},
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": kernels_per_step * args.steps,
             "clocks": clk, "parity_ok": ok, "host_elapsed_s": round(host_elapsed, 4), "tune_s": round(tune_s, 2),
+            "batched": batched, "serving": serving, "host_sweep": host_sweep, "graph_lifecycle": lifecycle,
             "sweep": sweep, "wall_s": round(time.perf_counter() - t_wall0, 2),
         }
         print(json.dumps(line), flush=True)
     return 0 if ok else 1
+
+
+def _percentile(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    i = min(len(xs) - 1, max(0, int(math.ceil(q / 100.0 * len(xs))) - 1))
+    return xs[i]
+
+
+def _tiled_arena(torch, nbytes, pinned, base_t, period):
+    """An arena filled with repeats of one seeded payload period (fast to build)."""
+    t = torch.empty(nbytes, dtype=torch.uint8).pin_memory() if pinned else \
+        torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    src = base_t.to(t.device)
+    for o in range(0, nbytes, period):
+        m = min(period, nbytes - o)
+        t[o:o + m].copy_(src[:m])
+    return t
+
+
+def run_batched(mpt, torch, ctx, stream, reps=5):
+    """Batched workload: 4096 transfers of 256 B..16 MiB (log-uniform), 70% device-to-device
+    and 30% host-to-device, 16-byte aligned gaps, bf16 payload; one persistent-kernel batch
+    per launch against 4096 per-transfer eager copies (cudaMemcpyAsync through torch)."""
+    import payload
+    period = 64 * MiB
+    sizes, d2d, gaps = payload.batch_workload(4096)
+    items, offs = [], {"dev": 0, "host": 0, "dst": 0}
+    for sz, is_d2d, gap in zip(sizes, d2d, gaps):
+        a = "dev" if is_d2d else "host"
+        offs[a] += gap
+        offs["dst"] += gap
+        items.append((a, offs[a], offs["dst"], sz))
+        offs[a] += sz
+        offs["dst"] += sz
+    base_t = torch.from_numpy(payload.fill("bf16", payload.SEED_BATCH, period))
+    src = {"dev": _tiled_arena(torch, offs["dev"] + 64, False, base_t, period),
+           "host": _tiled_arena(torch, offs["host"] + 64, True, base_t, period)}
+    dst = torch.zeros(offs["dst"] + 64, dtype=torch.uint8, device="cuda")
+    for t in (src["dev"], src["host"], dst):
+        mpt.mpt_batch_register(ctx, t.data_ptr(), t.numel())
+    xf = mpt.make_xfers([(src[a].data_ptr() + so, dst.data_ptr() + do, sz, mpt.MPT_D2D if a == "dev" else mpt.MPT_H2D)
+                         for a, so, do, sz in items])
+    total = sum(sizes)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    batch_ms, lat = [], []
+    for r in range(reps + 2):
+        e0.record(stream)
+        b = mpt.mpt_batch_submit(ctx, xf, stream)
+        e1.record(stream)
+        mpt.mpt_batch_wait(b, 60 * 10 ** 9)
+        t = mpt.mpt_batch_times(b, len(items))
+        mpt.mpt_batch_release(b)
+        e1.synchronize()
+        if r >= 2:
+            batch_ms.append(e0.elapsed_time(e1))
+            lat += [x / 1e3 for x in t]
+    ok = all(mpt.mpt_hash_device(ctx, dst.data_ptr() + do, sz) == mpt.mpt_hash_device(ctx, src[a].data_ptr() + so, sz)
+             for a, so, do, sz in items[::64])
+    # per-transfer eager copies, one event per transfer for its completion time
+    views = [(dst[do:do + sz], src[a][so:so + sz]) for a, so, do, sz in items]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in items]
+    eager_ms, eager_lat = [], []
+    for r in range(reps + 1):
+        dst.zero_()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for (d, s_), ev in zip(views, evs):
+                d.copy_(s_, non_blocking=True)
+                ev.record(stream)
+            e1.record(stream)
+        e1.synchronize()
+        if r >= 1:
+            eager_ms.append(e0.elapsed_time(e1))
+            eager_lat += [e0.elapsed_time(ev) * 1e3 for ev in evs]
+    med = statistics.median(batch_ms)
+    emed = statistics.median(eager_ms)
+    return {
+        "workload": "4096 transfers, 256 B..16 MiB log-uniform, 70% D2D / 30% H2D, bf16, 16 B gaps",
+        "bytes_per_batch": total, "batch_ms": round(med, 3), "transfers_per_s": round(4096 / (med / 1e3), 1),
+        "gbs": round(total / (med / 1e3) / 1e9, 2),
+        "p50_us": round(_percentile(lat, 50), 1), "p99_us": round(_percentile(lat, 99), 1),
+        "eager_ms": round(emed, 3), "eager_transfers_per_s": round(4096 / (emed / 1e3), 1),
+        "eager_p50_us": round(_percentile(eager_lat, 50), 1), "eager_p99_us": round(_percentile(eager_lat, 99), 1),
+        "latency": "per-transfer completion after the batch kernel started (batched) / after the first "
+                   "copy was enqueued (eager), device clocks", "parity_ok": bool(ok)}
+
+
+def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30):
+    """Open-loop Poisson arrivals (lognormal sizes, median 1 MiB, sigma 1.5, cap 256 MiB,
+    50/25/25 directions) through the continuous-batching server; latency from the scheduled
+    arrival to the completion flag; 1% of requests and every request above 64 MiB verified
+    by digest right after completion."""
+    import collections
+
+    import payload
+    cap = 256 * MiB
+    src_dev = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    src_host = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+    base_t = torch.from_numpy(payload.fill("u32", payload.SEED_SERVE, 64 * MiB))
+    for t in (src_dev, src_host):
+        for o in range(0, t.numel(), 64 * MiB):
+            t[o:o + 64 * MiB].copy_(base_t.to(t.device))
+    ring = {"dev": torch.empty(12 << 30, dtype=torch.uint8, device="cuda"),
+            "host": torch.empty(4 << 30, dtype=torch.uint8).pin_memory()}
+    for t in (src_dev, src_host, ring["dev"], ring["host"]):
+        mpt.mpt_batch_register(ctx, t.data_ptr(), t.numel())
+    vstream = torch.cuda.Stream()
+    out = []
+    for rate in rates:
+        sched = payload.serving_schedule(rate, seconds)
+        heads = {"dev": 0, "host": 0}
+        outstanding = {"dev": collections.deque(), "host": collections.deque()}
+        finished = set()
+        lat, late, verified, bad = [], [], 0, 0
+        moved = 0
+        server = mpt.mpt_serve_start(ctx, staging_budget_bytes=budget)
+        meta = {}
+
+        def harvest():
+            nonlocal verified, bad, moved
+            for tag, arr, adm, comp, nb, st in mpt.mpt_serve_poll(server):
+                kind, off, sp, dp = meta.pop(tag)
+                finished.add(tag)
+                if st != mpt.MPT_OK:
+                    bad += 1
+                    continue
+                lat.append((comp - arr) / 1e3)
+                moved += nb
+                if tag % 100 == 0 or nb > 64 * MiB:
+                    h = mpt.mpt_hash_ranges_noalloc([(dp, nb), (sp, nb)], vstream)
+                    verified += 1
+                    bad += h[0] != h[1]
+            for kind in ("dev", "host"):
+                q = outstanding[kind]
+                while q and q[0][0] in finished:
+                    finished.discard(q.popleft()[0])
+
+        def ring_alloc(kind, nb):
+            """FIFO ring over the destination arena: a new region may not reach into the oldest
+            request still outstanding (which keeps in-flight destinations disjoint)."""
+            size = ring[kind].numel()
+            q = outstanding[kind]
+            head = heads[kind] if q else 0
+            step = (nb + 255) // 256 * 256
+            if not q:
+                start = 0
+            else:
+                tail = q[0][1]
+                if head > tail:
+                    start = head if head + step <= size else (0 if step < tail else None)
+                else:
+                    start = head if head + step < tail else None
+            if start is None:
+                return None
+            heads[kind] = start + step
+            q.append((k, start))
+            return start
+
+        t0 = mpt.mpt_now_ns() + 20_000_000
+        for k, (t_arr, nb, d) in enumerate(sched):
+            due = t0 + int(t_arr * 1e9)
+            while mpt.mpt_now_ns() < due:
+                harvest()
+            kind = "host" if d == mpt.MPT_D2H else "dev"
+            start = None
+            while start is None:
+                start = ring_alloc(kind, nb)
+                if start is None:
+                    harvest()
+            s_t = src_host if d == mpt.MPT_H2D else src_dev
+            soff = (payload.splitmix64_scalar(payload.SEED_SERVE, 1 << 40 | k) % (s_t.numel() - nb)) & ~255
+            sp, dp = s_t.data_ptr() + soff, ring[kind].data_ptr() + start
+            meta[k] = (kind, start, sp, dp)
+            late.append((mpt.mpt_now_ns() - due) / 1e3)
+            mpt.mpt_serve_submit(server, sp, dp, nb, d, k, due)
+        t_end_sched = t0 + int(seconds * 1e9)
+        while meta:
+            harvest()
+        wall = (mpt.mpt_now_ns() - t0) / 1e9
+        stats = mpt.mpt_serve_stats(server)
+        mpt.mpt_serve_stop(server)
+        out.append({"rate_per_s": rate, "seconds": seconds, "requests": len(sched),
+                    "p50_us": round(_percentile(lat, 50), 1), "p99_us": round(_percentile(lat, 99), 1),
+                    "gbs": round(moved / max(wall, 1e-9) / 1e9, 2), "offered_gbs": round(sum(x[1] for x in sched) / seconds / 1e9, 2),
+                    "batches": stats["batches"], "max_inflight_bytes": stats["max_inflight_bytes"],
+                    "submit_late_p99_us": round(_percentile(late, 99), 1), "verified": verified, "errors": bad,
+                    "drain_s": round((mpt.mpt_now_ns() - t_end_sched) / 1e9, 3)})
+    return out
+
+
+def run_host_sweep(mpt, torch, ctx, stream, max_bytes=2 << 30, reps=3, tune=True):
+    """Host<->device sweep: 4 KiB .. 2 GiB in powers of two, u32 payload from page-locked host
+    memory; per size and direction the copy engine alone, the zero-copy kernel alone, the
+    staged path alone and the tuned plan, each one graph replay (median of reps); plus both
+    directions at once with their tuned plans."""
+    import payload
+    sizes = [1 << k for k in range(12, 32) if (1 << k) <= max_bytes]
+    top = sizes[-1]
+    host_src = torch.empty(top, dtype=torch.uint8).pin_memory()
+    host_dst = torch.empty(top, dtype=torch.uint8).pin_memory()
+    dev_a = torch.empty(top, dtype=torch.uint8, device="cuda")
+    dev_b = torch.empty(top, dtype=torch.uint8, device="cuda")
+    base = torch.from_numpy(payload.fill("u32", payload.SEED_HOST_SWEEP, 64 * MiB))
+    for o in range(0, top, 64 * MiB):
+        host_src[o:o + 64 * MiB].copy_(base[:min(64 * MiB, top - o)])
+    dev_b.copy_(host_src)
+    flush = torch.empty(256 * MiB, dtype=torch.uint8, device="cuda")
+    s2 = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(launch, n_reps):
+        ts = []
+        for _ in range(n_reps + 1):
+            flush.fill_(1)
+            e0.record(stream)
+            launch()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts[1:])
+
+    rows = []
+    for n in sizes:
+        row = {"bytes": n}
+        for direction, name in ((mpt.MPT_H2D, "h2d"), (mpt.MPT_D2H, "d2h")):
+            src = host_src if direction == mpt.MPT_H2D else dev_b
+            dst = dev_a if direction == mpt.MPT_H2D else host_dst
+            if tune:
+                mpt.mpt_tune(ctx, direction, n, mpt.MPT_MODE_GRAPH)
+            chunk = min(n, 8 * MiB)
+            sets = {"ce": [(mpt.MPT_PATH_CE, 65536, chunk)], "zc": [(mpt.MPT_PATH_ZC, 65536, chunk)],
+                    "hs": [(mpt.MPT_PATH_HS, 65536, chunk)], "tuned": None}
+            for label, specs in sets.items():
+                plan = mpt.mpt_plan(ctx, n, direction, specs)
+                g = mpt.mpt_capture(ctx, plan, dst.data_ptr(), src.data_ptr())
+                ms = timed(lambda: mpt.mpt_launch(g, stream), reps if n < (512 << 20) else 1)
+                row[f"{name}_{label}_gbs"] = round(n / (ms / 1e3) / 1e9, 2)
+                if label == "tuned":
+                    row[f"{name}_plan"] = [(p["kind"], p["share"], p["chunk_bytes"]) for p in mpt.mpt_plan_paths(plan)]
+                mpt.mpt_graph_release(g)
+                mpt.mpt_plan_destroy(plan)
+            row[f"{name}_best_single_gbs"] = max(row[f"{name}_{k}_gbs"] for k in ("ce", "zc", "hs"))
+        # both directions at once (tuned plans, two streams)
+        up = mpt.mpt_plan(ctx, n, mpt.MPT_H2D, None)
+        down = mpt.mpt_plan(ctx, n, mpt.MPT_D2H, None)
+        gu = mpt.mpt_capture(ctx, up, dev_a.data_ptr(), host_src.data_ptr())
+        gd = mpt.mpt_capture(ctx, down, host_dst.data_ptr(), dev_b.data_ptr())
+
+        def both():
+            s2.wait_stream(stream)
+            mpt.mpt_launch(gu, stream)
+            mpt.mpt_launch(gd, s2)
+            stream.wait_stream(s2)
+        ms = timed(both, reps if n < (512 << 20) else 1)
+        row["bidir_gbs_per_direction"] = round(n / (ms / 1e3) / 1e9, 2)
+        for g in (gu, gd):
+            mpt.mpt_graph_release(g)
+        for p in (up, down):
+            mpt.mpt_plan_destroy(p)
+        rows.append(row)
+    ok = bool(torch.equal(host_dst[:1 << 20], dev_b[:1 << 20].cpu())) and bool(torch.equal(dev_a[:1 << 20].cpu(), host_src[:1 << 20]))
+    return {"rows": rows, "parity_ok": ok,
+            "note": "GB/s of message bytes; host link measured at 211 GB/s H2D and 193 GB/s D2H for copy engine and zero-copy alike"}
+
+
+def run_graph_lifecycle(mpt, torch, ctx, stream):
+    """Graph lifecycle vs node count (the paper's Sec. 5.5 analysis, dual path 2 MiB..512 MiB):
+    copy engine + SM kernel at 50/50 with 8 MiB copy-engine chunks, so a message of N bytes
+    has N/16 MiB memcpy nodes + 1 kernel node.  Creation, construction and instantiation
+    come from mpt_graph_info (first call); launch is the host-side cost of mpt_launch, first
+    call and median of later calls; update is an in-place retarget at other addresses
+    (mpt_graph_rebind) in place of a new instantiation."""
+    rows = []
+    n_max = 512 * MiB
+    a = torch.empty(2 * n_max, dtype=torch.uint8, device="cuda")
+    b = torch.empty(2 * n_max, dtype=torch.uint8, device="cuda")
+    for n in [2 * MiB << k for k in range(9)]:
+        chunk = 8 * MiB
+        plan = mpt.mpt_plan(ctx, n, mpt.MPT_D2D, [(mpt.MPT_PATH_CE, 32768, chunk), (mpt.MPT_PATH_SM, 32768, chunk)])
+        torch.cuda.synchronize()
+        g = mpt.mpt_capture(ctx, plan, b.data_ptr(), a.data_ptr())
+        info = mpt.mpt_graph_get_info(g)
+        t0 = time.perf_counter()
+        mpt.mpt_launch(g, stream)
+        first = (time.perf_counter() - t0) * 1e6
+        stream.synchronize()
+        later = []
+        for _ in range(20):
+            t0 = time.perf_counter()
+            mpt.mpt_launch(g, stream)
+            later.append((time.perf_counter() - t0) * 1e6)
+            stream.synchronize()
+        mpt.mpt_graph_rebind(g, plan, b.data_ptr() + n_max, a.data_ptr() + n_max)
+        upd = mpt.mpt_graph_get_info(g)["update_us"]
+        mpt.mpt_graph_rebind(g, plan, b.data_ptr(), a.data_ptr())
+        rows.append({"bytes": n, "nodes": info["nodes"], "create_us": round(info["create_us"], 1),
+                     "construct_us": round(info["construct_us"], 1), "instantiate_us": round(info["instantiate_us"], 1),
+                     "launch_first_us": round(first, 1), "launch_later_us": round(statistics.median(later), 1),
+                     "update_us": round(upd, 1)})
+        mpt.mpt_graph_release(g)
+        mpt.mpt_graph_evict(ctx, b.data_ptr())
+        mpt.mpt_plan_destroy(plan)
+    return rows
+
+
+def run_batch_only(args):
+    """One batch configuration alone (for profiling): the batched workload's sizes with every
+    transfer device-to-device, host-to-device, or mixed 70/30."""
+    import torch
+
+    import payload
+    import paper_2604_22228_gb300 as mpt
+    from paper_2604_22228_gb300 import build
+    build.build()
+    ctx = mpt.mpt_ctx_create(0)
+    mpt.mpt_batch_configure(ctx, 2, 4096, args.batch_ctas, args.batch_tile)
+    sizes, d2d, gaps = payload.batch_workload(args.batch_n)
+    items, offs = [], {"dev": 0, "host": 0, "dst": 0}
+    for sz, is_d2d, gap in zip(sizes, d2d, gaps):
+        a = "dev" if (args.batch_only == "d2d" or (args.batch_only == "mix" and is_d2d)) else "host"
+        offs[a] += gap
+        offs["dst"] += gap
+        items.append((a, offs[a], offs["dst"], sz))
+        offs[a] += sz
+        offs["dst"] += sz
+    src = {"dev": torch.zeros(offs["dev"] + 64, dtype=torch.uint8, device="cuda"),
+           "host": torch.zeros(offs["host"] + 64, dtype=torch.uint8).pin_memory()}
+    dst = torch.empty(offs["dst"] + 64, dtype=torch.uint8, device="cuda")
+    xf = mpt.make_xfers([(src[a].data_ptr() + so, dst.data_ptr() + do, sz, mpt.MPT_D2D if a == "dev" else mpt.MPT_H2D)
+                         for a, so, do, sz in items])
+    s = torch.cuda.Stream()
+    ks = []
+    for r in range(args.warmup + args.steps):
+        b = mpt.mpt_batch_submit(ctx, xf, s)
+        mpt.mpt_batch_wait(b, 60 * 10 ** 9)
+        t = mpt.mpt_batch_times(b, len(items))
+        mpt.mpt_batch_release(b)
+        if r >= args.warmup:
+            ks.append(max(t) / 1e6)
+    st, _ = mpt.mpt_ctx_status(ctx)
+    mpt.mpt_ctx_destroy(ctx)
+    nb = sum(sizes)
+    k = statistics.median(ks)
+    print(json.dumps({"batch": args.batch_only, "transfers": len(items), "bytes": nb, "kernel_ms": round(k, 3),
+                      "gbs": round(nb / k / 1e6, 1), "ok": st == 0}), flush=True)
+    return 0 if st == 0 else 1
 
 
 def run_kernel_only(args):
@@ -544,6 +910,10 @@ def main(argv=None):
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-baselines", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-host-sweep", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=2.0, help="per arrival rate; 0 skips serving")
+    ap.add_argument("--serve-rates", default="1000,10000,50000")
     ap.add_argument("--tune", choices=["online", "model"], default="online",
                     help="online: measure every size bucket with mpt_tune before capturing; model: cost model only")
     ap.add_argument("--tune-out", default=None, help="write the tuned table (JSON lines) here")
@@ -551,6 +921,11 @@ def main(argv=None):
                     help="time one copy kernel alone on --kernel-bytes (profiling)")
     ap.add_argument("--kernel-bytes", type=int, default=256 * MiB)
     ap.add_argument("--kernel-ctas", type=int, default=0)
+    ap.add_argument("--batch-only", choices=["mix", "d2d", "h2d"], default=None,
+                    help="run one batch of the batched workload's shape alone (profiling)")
+    ap.add_argument("--batch-n", type=int, default=4096)
+    ap.add_argument("--batch-ctas", type=int, default=0)
+    ap.add_argument("--batch-tile", type=int, default=0)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")
@@ -558,6 +933,8 @@ def main(argv=None):
         return run_reference(args)
     if args.kernel_only:
         return run_kernel_only(args)
+    if args.batch_only:
+        return run_batch_only(args)
     return run_ours(args)
 
 

@@ -118,6 +118,9 @@ typedef struct {
   double construct_us;     /* adding nodes and edges */
   double instantiate_us;   /* cudaGraphInstantiate */
   uint64_t staging_bytes;  /* staging memory this graph owns */
+  double update_us;        /* last in-place retarget (mpt_graph_rebind or a capture that reused it) */
+  uint32_t rebinds;        /* in-place retargets so far */
+  uint32_t reserved;
 } mpt_graph_info;
 
 /* Cost model of one path kind: per-chunk issue latency and bandwidth (the staged path's
@@ -205,7 +208,9 @@ MPT_API mpt_status mpt_plan_destroy(mpt_plan_t plan);
 /* Return the executable graph that moves plan's message from src to dst, building,
  * instantiating and caching it on a miss (key: src, dst, N, direction, plan hash;
  * fixed-capacity LRU, capacity MPT_GRAPH_CACHE, default 64; Sec. 4.2 "CUDA Graph
- * Cache").  src/dst must match the plan's direction (device or page-locked host memory)
+ * Cache").  On a miss, a cached graph of the same plan that only the cache holds is
+ * retargeted in place (cudaGraphExecUpdate) instead of instantiating a new one, the graph
+ * update Sec. 6 leaves as future work; MPT_GRAPH_REBIND=0 disables this.  src/dst must match the plan's direction (device or page-locked host memory)
  * and must stay allocated while the graph can run: a graph is bound to its addresses.
  * *out is a new reference owned by the caller (mpt_graph_release); eviction from the
  * cache never invalidates a held reference.  Graphs with a staged path own their
@@ -220,6 +225,16 @@ MPT_API mpt_status mpt_launch(mpt_graph_t graph, void* stream);
 
 /* Lifecycle figures of a captured graph. */
 MPT_API mpt_status mpt_graph_get_info(mpt_graph_t graph, mpt_graph_info* out);
+
+/* Retarget a captured graph at new addresses of the same sizes without re-instantiating
+ * it: the node set is rebuilt for (dst, src) with the graph's own staging buffers and the
+ * executable is updated in place.  `plan` must be the plan the graph was captured from.
+ * Every holder of the handle sees the new addresses; its cache entry is re-keyed.  The
+ * update applies to later launches.  Errors: EINVAL (other plan, wrong pointer kinds),
+ * EAGAIN (another cached graph already serves those addresses), ENOTSUP (the runtime
+ * cannot update in place, e.g. the SM kernel variant changes with the new alignment --
+ * capture anew). */
+MPT_API mpt_status mpt_graph_rebind(mpt_graph_t graph, mpt_plan_t plan, void* dst, const void* src);
 
 /* Drop a graph reference obtained from mpt_capture. */
 MPT_API mpt_status mpt_graph_release(mpt_graph_t graph);
@@ -304,7 +319,7 @@ MPT_API mpt_status mpt_tune_get(mpt_ctx_t ctx, uint32_t dir, uint64_t nbytes, ui
 
 /* Size the context's batch ring: `slots` batches in flight at once (default 4), up to
  * `max_xfers` transfers per batch (default 4096), `ctas` CTAs of the batch kernel
- * (default 2 x SMs) and `tile_bytes` per work item (default 64 KiB; >= 4096, multiple of
+ * (default 4 x SMs) and `tile_bytes` per work item (default 256 KiB; >= 4096, multiple of
  * 16).  0 keeps a default.  Waits for the device; fails with EAGAIN while a batch is held.
  * The ring is built on first use with defaults when this is never called. */
 MPT_API mpt_status mpt_batch_configure(mpt_ctx_t ctx, uint32_t slots, uint32_t max_xfers, uint32_t ctas,
@@ -341,6 +356,59 @@ MPT_API mpt_status mpt_batch_times(mpt_batch_t batch, uint64_t* out_ns);
 
 /* Release the handle and its slot. */
 MPT_API mpt_status mpt_batch_release(mpt_batch_t batch);
+
+/* ---- serving loop (continuous batching over the batch ring) ------------------------ */
+
+typedef struct mpt_server_s* mpt_server_t;
+
+typedef struct {
+  uint64_t staging_budget_bytes;  /* admission limit on bytes in flight (0 = 8 GiB) */
+  uint32_t max_batch;             /* transfers per batch (0 = the slot capacity) */
+  uint32_t max_inflight_batches;  /* batches on the GPU at once (0 = every slot) */
+} mpt_serve_config;
+
+/* One finished request: its tag, the arrival time the caller gave, when it was admitted
+ * into a batch and when its completion flag was seen (mpt_now_ns clock), its size, and
+ * MPT_OK or the error that refused it. */
+typedef struct {
+  uint64_t tag;
+  uint64_t arrival_ns;
+  uint64_t admit_ns;
+  uint64_t complete_ns;
+  uint64_t bytes;
+  uint32_t status;
+  uint32_t reserved;
+} mpt_completion;
+
+typedef struct {
+  uint64_t submitted, completed, batches, inflight_bytes, max_inflight_bytes, rejected;
+} mpt_serve_stats_t;
+
+/* The clock of mpt_serve_submit / mpt_completion (steady, nanoseconds). */
+MPT_API uint64_t mpt_now_ns(void);
+
+/* Start a serving loop on `ctx` (cfg nullable = defaults).  A worker thread owns the
+ * context until mpt_serve_stop: do not use the context from other threads meanwhile.  It
+ * admits waiting requests oldest first while the bytes in flight stay within the budget (a
+ * request larger than the whole budget runs alone), packs them into the next batch, and
+ * launches it as soon as a batch slot is free, so requests arriving while earlier batches
+ * run overlap with them on the device.  Each request completes individually when the
+ * batch kernel raises its flag. */
+MPT_API mpt_status mpt_serve_start(mpt_ctx_t ctx, const mpt_serve_config* cfg, mpt_server_t* out);
+
+/* Enqueue one request (thread-safe).  arrival_ns: the request's scheduled arrival on the
+ * mpt_now_ns clock (0 = now); latency is measured from it.  The same rules as
+ * mpt_batch_submit apply to the transfer; in-flight destinations must not overlap. */
+MPT_API mpt_status mpt_serve_submit(mpt_server_t server, const mpt_xfer* xfer, uint64_t tag, uint64_t arrival_ns);
+
+/* Move up to `cap` finished requests into `out` (thread-safe); *n gets the count. */
+MPT_API mpt_status mpt_serve_poll(mpt_server_t server, mpt_completion* out, size_t cap, size_t* n);
+
+MPT_API mpt_status mpt_serve_stats(mpt_server_t server, mpt_serve_stats_t* out);
+
+/* Finish every request already submitted, stop the worker and free the server.
+ * Completions not yet polled are dropped. */
+MPT_API mpt_status mpt_serve_stop(mpt_server_t server);
 
 /* ---- failure detection self-test ---------------------------------------------------- */
 

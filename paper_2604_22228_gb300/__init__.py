@@ -139,6 +139,10 @@ def mpt_graph_get_info(graph: int) -> dict:
     return {name: getattr(info, name) for name, _ in _ffi.mpt_graph_info._fields_}
 
 
+def mpt_graph_rebind(graph: int, plan: int, dst, src) -> None:
+    _check(lib().mpt_graph_rebind(graph, plan, _ptr(dst), _ptr(src)), "mpt_graph_rebind")
+
+
 def mpt_graph_release(graph: int) -> None:
     _check(lib().mpt_graph_release(graph), "mpt_graph_release")
 
@@ -265,6 +269,45 @@ def mpt_batch_times(batch: int, n: int) -> list[int]:
 
 def mpt_batch_release(batch: int) -> None:
     _check(lib().mpt_batch_release(batch), "mpt_batch_release")
+
+
+def mpt_now_ns() -> int:
+    return lib().mpt_now_ns()
+
+
+def mpt_serve_start(ctx: int, staging_budget_bytes: int = 0, max_batch: int = 0, max_inflight_batches: int = 0) -> int:
+    cfg = _ffi.mpt_serve_config(staging_budget_bytes, max_batch, max_inflight_batches)
+    h = C.c_void_p()
+    _check(lib().mpt_serve_start(ctx, C.byref(cfg), C.byref(h)), "mpt_serve_start")
+    return h.value
+
+
+def mpt_serve_submit(server: int, src, dst, nbytes: int, direction: int, tag: int, arrival_ns: int = 0) -> None:
+    x = _ffi.mpt_xfer(_ptr(src), _ptr(dst), nbytes, direction, 0)
+    _check(lib().mpt_serve_submit(server, C.byref(x), tag, arrival_ns), "mpt_serve_submit")
+
+
+_COMPLETION_BUF = None
+
+
+def mpt_serve_poll(server: int, cap: int = 4096) -> list[tuple]:
+    """Finished requests as (tag, arrival_ns, admit_ns, complete_ns, bytes, status)."""
+    global _COMPLETION_BUF
+    if _COMPLETION_BUF is None or len(_COMPLETION_BUF) < cap:
+        _COMPLETION_BUF = (_ffi.mpt_completion * cap)()
+    n = C.c_size_t()
+    _check(lib().mpt_serve_poll(server, _COMPLETION_BUF, cap, C.byref(n)), "mpt_serve_poll")
+    return [(c.tag, c.arrival_ns, c.admit_ns, c.complete_ns, c.bytes, c.status) for c in _COMPLETION_BUF[:n.value]]
+
+
+def mpt_serve_stats(server: int) -> dict:
+    st = _ffi.mpt_serve_stats_t()
+    _check(lib().mpt_serve_stats(server, C.byref(st)), "mpt_serve_stats")
+    return {name: getattr(st, name) for name, _ in _ffi.mpt_serve_stats_t._fields_}
+
+
+def mpt_serve_stop(server: int) -> None:
+    _check(lib().mpt_serve_stop(server), "mpt_serve_stop")
 
 
 def mpt_selftest_flag_timeout(ctx: int, timeout_ns: int):

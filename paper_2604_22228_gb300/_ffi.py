@@ -47,7 +47,8 @@ class mpt_xfer(C.Structure):
 class mpt_graph_info(C.Structure):
     _fields_ = [("nodes", C.c_uint32), ("memcpy_nodes", C.c_uint32), ("kernel_nodes", C.c_uint32),
                 ("memset_nodes", C.c_uint32), ("create_us", C.c_double), ("construct_us", C.c_double),
-                ("instantiate_us", C.c_double), ("staging_bytes", C.c_uint64)]
+                ("instantiate_us", C.c_double), ("staging_bytes", C.c_uint64), ("update_us", C.c_double),
+                ("rebinds", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class mpt_path_model(C.Structure):
@@ -58,6 +59,22 @@ class mpt_model(C.Structure):
     _fields_ = [("launch_ps", C.c_uint64), ("hbm_Bps", C.c_uint64), ("link_h2d_Bps", C.c_uint64),
                 ("link_d2h_Bps", C.c_uint64), ("ce", mpt_path_model), ("sm", mpt_path_model),
                 ("hs", mpt_path_model), ("zc", mpt_path_model)]
+
+
+class mpt_serve_config(C.Structure):
+    _fields_ = [("staging_budget_bytes", C.c_uint64), ("max_batch", C.c_uint32),
+                ("max_inflight_batches", C.c_uint32)]
+
+
+class mpt_completion(C.Structure):
+    _fields_ = [("tag", C.c_uint64), ("arrival_ns", C.c_uint64), ("admit_ns", C.c_uint64),
+                ("complete_ns", C.c_uint64), ("bytes", C.c_uint64), ("status", C.c_uint32),
+                ("reserved", C.c_uint32)]
+
+
+class mpt_serve_stats_t(C.Structure):
+    _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "batches", "inflight_bytes",
+                                          "max_inflight_bytes", "rejected")]
 
 
 H = C.c_void_p  # opaque handles
@@ -78,6 +95,7 @@ SIGNATURES = {
     "mpt_capture": (C.c_int, [H, H, C.c_void_p, C.c_void_p, P(H)]),
     "mpt_launch": (C.c_int, [H, C.c_void_p]),
     "mpt_graph_get_info": (C.c_int, [H, P(mpt_graph_info)]),
+    "mpt_graph_rebind": (C.c_int, [H, H, C.c_void_p, C.c_void_p]),
     "mpt_graph_release": (C.c_int, [H]),
     "mpt_graph_evict": (C.c_int, [H, C.c_void_p, P(C.c_uint32)]),
     "mpt_launch_eager": (C.c_int, [H, H, C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -100,6 +118,12 @@ SIGNATURES = {
     "mpt_batch_wait": (C.c_int, [H, C.c_uint64]),
     "mpt_batch_times": (C.c_int, [H, P(C.c_uint64)]),
     "mpt_batch_release": (C.c_int, [H]),
+    "mpt_now_ns": (C.c_uint64, []),
+    "mpt_serve_start": (C.c_int, [H, P(mpt_serve_config), P(H)]),
+    "mpt_serve_submit": (C.c_int, [H, P(mpt_xfer), C.c_uint64, C.c_uint64]),
+    "mpt_serve_poll": (C.c_int, [H, P(mpt_completion), C.c_size_t, P(C.c_size_t)]),
+    "mpt_serve_stats": (C.c_int, [H, P(mpt_serve_stats_t)]),
+    "mpt_serve_stop": (C.c_int, [H]),
     "mpt_selftest_flag_timeout": (C.c_int, [H, C.c_uint64, P(C.c_uint32)]),
     "mpt_hash_ranges_noalloc": (C.c_int, [P(C.c_void_p), P(C.c_uint64), C.c_uint32, C.c_void_p, P(C.c_uint64)]),
     "mpt_host_alloc": (C.c_int, [C.c_uint64, P(C.c_void_p)]),

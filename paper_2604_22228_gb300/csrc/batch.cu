@@ -105,7 +105,7 @@ namespace {
 
 constexpr uint32_t kDefaultSlots = 4;
 constexpr uint32_t kDefaultMaxXfers = 4096;
-constexpr uint32_t kDefaultTile = 64 * 1024;
+constexpr uint32_t kDefaultTile = 256 * 1024;
 
 uint64_t host_ns() {
   return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -195,7 +195,8 @@ mpt_status batch_setup(mpt_ctx_t c) {
   if (!c->slots.empty()) return MPT_OK;
   const uint32_t nslots = c->batch_slots ? c->batch_slots : kDefaultSlots;
   const uint32_t maxx = c->batch_max_xfers ? c->batch_max_xfers : kDefaultMaxXfers;
-  const uint32_t ctas = c->batch_ctas ? c->batch_ctas : 2u * (uint32_t)c->sms;
+  // four 512-thread CTAs per SM: full occupancy, which the latency of host-link reads needs
+  const uint32_t ctas = c->batch_ctas ? c->batch_ctas : 4u * (uint32_t)c->sms;
   if (!c->batch_tile) c->batch_tile = kDefaultTile;
   c->slots.resize(nslots);
   for (auto& s : c->slots) {

@@ -1,7 +1,7 @@
 // Data-moving kernels of the transfer paths, written for sm_103a.
 //
-//  k_sm_copy_vec   SM copy kernel, 128-bit loads/stores: each CTA walks 32 KiB tiles of
-//                  the ranges it is given, every thread keeping four 16-byte vectors in
+//  k_sm_copy_vec   SM copy kernel, 128-bit loads/stores: each CTA walks 64 KiB tiles of
+//                  the ranges it is given, every thread keeping eight 16-byte vectors in
 //                  flight.  The device-to-device path the SMs add next to the copy
 //                  engines (Sec. 4.3's horizontal split over paths).
 //  k_sm_copy_bulk  same contract, body moved by cp.async.bulk global->shared->global

@@ -103,6 +103,7 @@ struct mpt_ctx_s {
   std::unordered_set<mpt_graph_s*> live;  // every graph not yet released
   size_t cache_cap = 64;
   uint64_t stage_max = 8ull << 20;
+  bool rebind_enabled = true;  // MPT_GRAPH_REBIND=0 turns the capture fast path off
   std::map<uint32_t, mpt::TuneEntry> tuned;  // tune_key -> choice
   // tuner scratch (grown on demand)
   void* tune_a = nullptr;

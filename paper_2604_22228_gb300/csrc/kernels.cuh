@@ -10,8 +10,8 @@ namespace mpt {
 
 constexpr int kInlineRanges = 16;     // ranges carried by value in one launch
 constexpr int kVecThreads = 512;      // vec128 kernel block size
-constexpr int kVecUnroll = 4;         // 16-byte vectors in flight per thread per tile
-constexpr uint64_t kVecTileVecs = (uint64_t)kVecThreads * kVecUnroll;  // 32 KiB tiles
+constexpr int kVecUnroll = 8;         // 16-byte vectors in flight per thread per tile
+constexpr uint64_t kVecTileVecs = (uint64_t)kVecThreads * kVecUnroll;  // 64 KiB tiles
 constexpr uint64_t kByteTile = 16384; // tile of the bytewise fallback
 constexpr int kBulkThreads = 128;     // bulk kernel block size (thread 0 drives the ring)
 constexpr int kBulkStages = 4;        // shared-memory ring depth

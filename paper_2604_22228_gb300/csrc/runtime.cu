@@ -86,9 +86,13 @@ void cache_drop(mpt_ctx_t c, mpt_graph_s* g) {
   graph_unref(g);
 }
 
+// Default grids, from measurements on GB300: the vec128 kernel needs about 16 CTAs per SM
+// over a large message (four resident, grid-striding over 64 KiB tiles) to keep HBM busy;
+// the bulk ring one CTA per SM, two waves; the zero-copy kernel saturates the host link
+// with one CTA per SM.
 uint32_t default_ctas(mpt_ctx_t c, uint32_t kind, uint32_t variant) {
   if (kind == MPT_PATH_ZC) return (uint32_t)c->sms;
-  return variant == MPT_SM_BULK ? (uint32_t)c->sms : 2u * (uint32_t)c->sms;
+  return variant == MPT_SM_BULK ? 2u * (uint32_t)c->sms : 16u * (uint32_t)c->sms;
 }
 
 // Chunks of one path merged into maximal contiguous ranges (CONTIG plans give one).
@@ -177,8 +181,33 @@ mpt_status for_each_copy(mpt_ctx_t c, const mpt_plan_s* plan, uint32_t p, const 
 
 // ---- graph construction (Algorithm 1 CreateGraph, Algorithm 2 node helpers) ---------------
 
-mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src, mpt_graph_s* g) {
+// Build the graph of `plan` for (dst, src) into g->graph and instantiate it (unless
+// `instantiate` is false).  Staging buffers are allocated and owned by g, or, when `reuse`
+// is given, taken in the same order from that graph (same plan => same buffers).
+mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src, mpt_graph_s* g,
+                       bool instantiate = true, const mpt_graph_s* reuse = nullptr) {
   mpt_graph_info& info = g->info;
+  size_t host_i = 0, dev_i = 0;
+  auto get_host = [&](size_t bytes, void** out) -> mpt_status {
+    if (reuse) {
+      if (host_i >= reuse->host_allocs.size()) return fail(MPT_EINVAL, "rebind: staging layout differs");
+      *out = reuse->host_allocs[host_i++];
+      return MPT_OK;
+    }
+    CUDA_TRY(cudaHostAlloc(out, bytes, cudaHostAllocPortable));
+    g->host_allocs.push_back(*out);
+    return MPT_OK;
+  };
+  auto get_dev = [&](size_t bytes, void** out) -> mpt_status {
+    if (reuse) {
+      if (dev_i >= reuse->dev_allocs.size()) return fail(MPT_EINVAL, "rebind: staging layout differs");
+      *out = reuse->dev_allocs[dev_i++];
+      return MPT_OK;
+    }
+    CUDA_TRY(cudaMalloc(out, bytes));
+    g->dev_allocs.push_back(*out);
+    return MPT_OK;
+  };
   const double t0 = now_us();
   CUDA_TRY(cudaGraphCreate(&g->graph, 0));
   const double t1 = now_us();
@@ -218,8 +247,8 @@ mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const voi
           // Algorithm 2 StageHostCopy: device -> pinned host slot -> device, two slots;
           // hop two of chunk k after its hop one, hop one of chunk k+2 after hop two of k.
           void* stage = nullptr;
-          CUDA_TRY(cudaHostAlloc(&stage, 2 * cb, cudaHostAllocPortable));
-          g->host_allocs.push_back(stage);
+          mpt_status sa = get_host(2 * cb, &stage);
+          if (sa != MPT_OK) return sa;
           info.staging_bytes += 2 * cb;
           uint8_t* st8 = static_cast<uint8_t*>(stage);
           cudaGraphNode_t prev_hop2[2] = {nullptr, nullptr};
@@ -250,13 +279,14 @@ mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const voi
           void* ctrl = nullptr;
           const size_t flags_bytes = (size_t)nch * 2 * sizeof(uint32_t);
           const size_t table_off = (flags_bytes + 255) & ~(size_t)255;
-          CUDA_TRY(cudaMalloc(&dstage, std::max<uint64_t>(stage_bytes, 256)));
-          g->dev_allocs.push_back(dstage);
-          CUDA_TRY(cudaMalloc(&ctrl, table_off + nch * sizeof(StageChunk)));
-          g->dev_allocs.push_back(ctrl);
-          CUDA_TRY(cudaMemset(ctrl, 0, flags_bytes));
-          CUDA_TRY(cudaMemcpy(static_cast<uint8_t*>(ctrl) + table_off, table.data(), nch * sizeof(StageChunk),
-                              cudaMemcpyHostToDevice));
+          mpt_status ga = get_dev(std::max<uint64_t>(stage_bytes, 256), &dstage);
+          if (ga == MPT_OK) ga = get_dev(table_off + nch * sizeof(StageChunk), &ctrl);
+          if (ga != MPT_OK) return ga;
+          if (!reuse) {  // a reused control block already holds this table and resting flags
+            CUDA_TRY(cudaMemset(ctrl, 0, flags_bytes));
+            CUDA_TRY(cudaMemcpy(static_cast<uint8_t*>(ctrl) + table_off, table.data(), nch * sizeof(StageChunk),
+                                cudaMemcpyHostToDevice));
+          }
           info.staging_bytes += stage_bytes;
           uint32_t* ready = static_cast<uint32_t*>(ctrl);
           uint8_t* ds8 = static_cast<uint8_t*>(dstage);
@@ -301,8 +331,8 @@ mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const voi
           // Device-to-host through a two-slot device stage: SM copy into the slot, then a
           // copy-engine hop to the host; a slot is refilled after its previous hop two.
           void* dstage = nullptr;
-          CUDA_TRY(cudaMalloc(&dstage, 2 * cb));
-          g->dev_allocs.push_back(dstage);
+          mpt_status sa = get_dev(2 * cb, &dstage);
+          if (sa != MPT_OK) return sa;
           info.staging_bytes += 2 * cb;
           uint8_t* ds8 = static_cast<uint8_t*>(dstage);
           cudaGraphNode_t prev_hop2[2] = {nullptr, nullptr};
@@ -334,7 +364,7 @@ mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const voi
   size_t nodes = 0;
   CUDA_TRY(cudaGraphGetNodes(g->graph, nullptr, &nodes));
   info.nodes = (uint32_t)nodes;
-  if (nodes > 0) CUDA_TRY(cudaGraphInstantiate(&g->exec, g->graph, 0));
+  if (nodes > 0 && instantiate) CUDA_TRY(cudaGraphInstantiate(&g->exec, g->graph, 0));
   const double t3 = now_us();
   info.create_us = t1 - t0;
   info.construct_us = t2 - t1;
@@ -353,6 +383,45 @@ mpt_status check_pointers(mpt_ctx_t c, uint32_t dir, const void* dst, const void
     return fail(MPT_EINVAL, "destination %p is not %s memory", dst,
                 want_d == kMemHost ? "page-locked host" : "device (this context's GPU)");
   return MPT_OK;
+}
+
+// Retarget g at (dst, src) without instantiating: rebuild the node set for the new
+// addresses (same plan, same staging buffers) and update the executable in place
+// (cudaGraphExecUpdate).  ENOTSUP when the runtime cannot update (e.g. the kernel variant
+// changes with the new alignment); g is then unchanged.
+mpt_status rebind(mpt_ctx_t c, mpt_graph_s* g, const mpt_plan_s* plan, void* dst, const void* src) {
+  const double t0 = now_us();
+  if (!g->exec) {  // empty message: nothing to retarget
+    g->info.update_us = now_us() - t0;
+    g->info.rebinds++;
+    return MPT_OK;
+  }
+  mpt_graph_s tmp;
+  tmp.ctx = c;
+  mpt_status st = build_graph(c, plan, dst, src, &tmp, false, g);
+  if (st != MPT_OK) {
+    if (tmp.graph) cudaGraphDestroy(tmp.graph);
+    return st;
+  }
+  cudaGraphExecUpdateResultInfo ri{};
+  const cudaError_t e = cudaGraphExecUpdate(g->exec, tmp.graph, &ri);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cudaGraphDestroy(tmp.graph);
+    return fail(MPT_ENOTSUP, "rebind: the runtime cannot update this graph in place (%s)", cudaGetErrorString(e));
+  }
+  cudaGraphDestroy(g->graph);
+  g->graph = tmp.graph;
+  g->info.update_us = now_us() - t0;
+  g->info.rebinds++;
+  return MPT_OK;
+}
+
+void set_range(mpt_graph_s* g, uint64_t nbytes, const void* dst, const void* src) {
+  g->src_lo = (uint64_t)(uintptr_t)src;
+  g->src_hi = g->src_lo + nbytes;
+  g->dst_lo = (uint64_t)(uintptr_t)dst;
+  g->dst_hi = g->dst_lo + nbytes;
 }
 
 // ---- eager engine (Sec. 4.3 static runtime pipelining; Sec. 4.5 contention avoidance) ------
@@ -529,6 +598,7 @@ mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out) {
     return bail(fail(MPT_ECUDA, "mpt_ctx_create: bulk kernel shared memory"));
   c->cache_cap = (size_t)std::max<uint64_t>(1, env_u64("MPT_GRAPH_CACHE", 64));
   c->stage_max = std::max<uint64_t>(4096, env_u64("MPT_STAGE_BYTES", 8ull << 20));
+  c->rebind_enabled = env_u64("MPT_GRAPH_REBIND", 1) != 0;
   const char* tf = tune_file && *tune_file ? tune_file : std::getenv("MPT_TUNE_FILE");
   if (tf && *tf) {
     mpt_status st = mpt_tune_load(c, tf);
@@ -601,13 +671,28 @@ mpt_status mpt_capture(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void* src,
     *out = g;
     return MPT_OK;
   }
+  // An idle cached graph of the same plan (held by the cache alone) is retargeted in place
+  // instead of instantiating a new one.
+  if (c->rebind_enabled) {
+    for (auto lit = c->lru.rbegin(); lit != c->lru.rend(); ++lit) {
+      mpt_graph_s* g = *lit;
+      if (g->refs != 1 || g->key.nbytes != key.nbytes || g->key.dir != key.dir || g->key.plan_hash != key.plan_hash)
+        continue;
+      if (rebind(c, g, plan, dst, src) != MPT_OK) break;
+      c->cache.erase(g->key);
+      g->key = key;
+      set_range(g, plan->nbytes, dst, src);
+      c->cache.emplace(key, g);
+      c->lru.splice(c->lru.begin(), c->lru, g->lru_it);
+      g->refs++;
+      *out = g;
+      return MPT_OK;
+    }
+  }
   mpt_graph_s* g = new mpt_graph_s;
   g->ctx = c;
   g->key = key;
-  g->src_lo = key.src;
-  g->src_hi = key.src + plan->nbytes;
-  g->dst_lo = key.dst;
-  g->dst_hi = key.dst + plan->nbytes;
+  set_range(g, plan->nbytes, dst, src);
   mpt_status st = build_graph(c, plan, dst, src, g);
   if (st != MPT_OK) {
     graph_destroy_exec(g);
@@ -636,6 +721,34 @@ mpt_status mpt_launch(mpt_graph_t g, void* stream) {
 mpt_status mpt_graph_get_info(mpt_graph_t g, mpt_graph_info* out) {
   if (!g || !out) return fail(MPT_EINVAL, "mpt_graph_get_info: NULL argument");
   *out = g->info;
+  return MPT_OK;
+}
+
+mpt_status mpt_graph_rebind(mpt_graph_t g, mpt_plan_t plan, void* dst, const void* src) {
+  if (!g || !plan) return fail(MPT_EINVAL, "mpt_graph_rebind: NULL argument");
+  mpt_ctx_t c = g->ctx;
+  if (!c) return fail(MPT_EINVAL, "mpt_graph_rebind: the graph's context was destroyed");
+  if (plan->hash != g->key.plan_hash || plan->nbytes != g->key.nbytes || plan->dir != g->key.dir)
+    return fail(MPT_EINVAL, "mpt_graph_rebind: the plan is not the one the graph was captured from");
+  CUDA_TRY(cudaSetDevice(c->device));
+  if (plan->nbytes > 0) {
+    mpt_status st = check_pointers(c, plan->dir, dst, src);
+    if (st != MPT_OK) return st;
+  }
+  GraphKey key{(uint64_t)(uintptr_t)src, (uint64_t)(uintptr_t)dst, plan->nbytes, plan->dir, plan->hash};
+  if (g->cached) {
+    auto it = c->cache.find(key);
+    if (it != c->cache.end() && it->second != g)
+      return fail(MPT_EAGAIN, "mpt_graph_rebind: another cached graph already serves these addresses");
+  }
+  mpt_status st = rebind(c, g, plan, dst, src);
+  if (st != MPT_OK) return st;
+  if (g->cached) {
+    c->cache.erase(g->key);
+    c->cache.emplace(key, g);
+  }
+  g->key = key;
+  set_range(g, plan->nbytes, dst, src);
   return MPT_OK;
 }
 

@@ -1,0 +1,269 @@
+// Serving loop: continuous batching of transfer requests over the batch ring.
+//
+// Requests arrive on any host thread (mpt_serve_submit).  One worker thread owns the
+// context while the server runs and repeats:
+//   1. harvest: read the host-mapped completion flags of every batch in flight and
+//      complete each finished request individually (its completion time, the bytes it
+//      held against the budget returned); a batch whose requests are all done and whose
+//      graph has finished gives its slot back;
+//   2. admit: move waiting requests, oldest first, into the batch under construction while
+//      the bytes in flight stay within the staging budget and the batch has room;
+//   3. launch: when a slot is free, submit the batch under construction (one graph replay
+//      of the persistent batch kernel).  Requests that arrive while earlier batches are
+//      still on the GPU wait only for a slot, not for those batches to finish, so their
+//      work overlaps on the device -- the windowed, many-in-flight regime where the paper
+//      finds graphs pay off (Sec. 5.3).
+// Latency is measured from the scheduled arrival time the caller passes, so a late caller
+// does not hide queueing delay.
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "ctx.h"
+
+namespace mpt {
+namespace {
+
+uint64_t steady_ns() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct Request {
+  mpt_xfer x;
+  uint64_t tag, arrival_ns, admit_ns;
+};
+
+struct InFlight {
+  mpt_batch_t batch;
+  std::vector<Request> reqs;
+  std::vector<uint8_t> flags;     // last poll: 1 = finished
+  std::vector<uint8_t> reported;  // completion already handed out
+  size_t ndone = 0;
+};
+
+}  // namespace
+}  // namespace mpt
+
+struct mpt_server_s {
+  mpt_ctx_t ctx = nullptr;
+  mpt_serve_config cfg{};
+  cudaStream_t stream = nullptr;
+  std::thread worker;
+  std::mutex mu;  // guards incoming, completions, stop, error
+  std::condition_variable cv;
+  std::deque<mpt::Request> incoming;
+  std::vector<mpt_completion> completions;
+  bool stop = false;
+  mpt_status error = MPT_OK;
+  std::string error_msg;
+  std::atomic<uint64_t> submitted{0}, completed{0}, batches{0}, inflight_bytes{0}, max_inflight_bytes{0};
+  std::atomic<uint64_t> rejected{0};
+};
+
+namespace mpt {
+namespace {
+
+void record_error(mpt_server_s* s, mpt_status st) {
+  std::lock_guard<std::mutex> g(s->mu);
+  if (s->error == MPT_OK) {
+    s->error = st;
+    s->error_msg = mpt_last_error();
+  }
+}
+
+void serve_loop(mpt_server_s* s) {
+  cudaSetDevice(s->ctx->device);
+  std::deque<Request> waiting;
+  std::vector<InFlight> flight;
+  std::vector<Request> building;
+  uint64_t budget_used = 0;
+  std::vector<mpt_xfer> xs;
+  std::vector<mpt_completion> done_local;
+  while (true) {
+    bool stopping;
+    {
+      std::unique_lock<std::mutex> lk(s->mu);
+      if (s->incoming.empty() && waiting.empty() && flight.empty() && building.empty() && !s->stop)
+        s->cv.wait_for(lk, std::chrono::microseconds(200));
+      while (!s->incoming.empty()) {
+        waiting.push_back(s->incoming.front());
+        s->incoming.pop_front();
+      }
+      stopping = s->stop;
+    }
+    // 1. harvest
+    done_local.clear();
+    for (size_t i = 0; i < flight.size();) {
+      InFlight& f = flight[i];
+      size_t n = 0;
+      if (mpt_batch_poll(f.batch, &n, f.flags.data()) != MPT_OK) {
+        record_error(s, MPT_ECUDA);
+        return;
+      }
+      if (n != f.ndone) {
+        const uint64_t now = steady_ns();
+        for (size_t k = 0; k < f.reqs.size(); ++k) {
+          if (!f.flags[k] || f.reported[k]) continue;
+          f.reported[k] = 1;
+          const Request& r = f.reqs[k];
+          done_local.push_back(mpt_completion{r.tag, r.arrival_ns, r.admit_ns, now, r.x.bytes, MPT_OK, 0});
+          budget_used -= r.x.bytes;
+        }
+        f.ndone = n;
+      }
+      if (f.ndone == f.reqs.size() && mpt_batch_wait(f.batch, 0) == MPT_OK) {
+        mpt_batch_release(f.batch);
+        flight[i] = std::move(flight.back());
+        flight.pop_back();
+      } else {
+        ++i;
+      }
+    }
+    // 2. admit, oldest first, within the budget and the batch capacity
+    const uint64_t budget = s->cfg.staging_budget_bytes;
+    while (!waiting.empty() && building.size() < s->cfg.max_batch) {
+      const Request& r = waiting.front();
+      const bool alone = budget_used == 0 && building.empty();
+      if (budget_used + r.x.bytes > budget && !alone) break;  // an oversized request goes alone
+      Request q = r;
+      q.admit_ns = steady_ns();
+      budget_used += q.x.bytes;
+      building.push_back(q);
+      waiting.pop_front();
+    }
+    s->inflight_bytes = budget_used;
+    if (budget_used > s->max_inflight_bytes) s->max_inflight_bytes = budget_used;
+    // 3. launch when a slot is free
+    if (!building.empty() && flight.size() < s->cfg.max_inflight_batches) {
+      xs.resize(building.size());
+      for (size_t k = 0; k < building.size(); ++k) xs[k] = building[k].x;
+      mpt_batch_t b = nullptr;
+      const mpt_status st = mpt_batch_submit(s->ctx, xs.data(), xs.size(), s->stream, &b);
+      if (st == MPT_OK) {
+        InFlight f;
+        f.batch = b;
+        f.reqs = std::move(building);
+        f.flags.assign(f.reqs.size(), 0);
+        f.reported.assign(f.reqs.size(), 0);
+        flight.push_back(std::move(f));
+        building.clear();
+        s->batches++;
+      } else if (st != MPT_EAGAIN) {
+        // a request the batch path refuses: complete it with the error, keep serving
+        const uint64_t now = steady_ns();
+        for (const Request& r : building) {
+          done_local.push_back(mpt_completion{r.tag, r.arrival_ns, r.admit_ns, now, r.x.bytes, (uint32_t)st, 0});
+          budget_used -= r.x.bytes;
+        }
+        s->rejected += building.size();
+        building.clear();
+      }
+    }
+    if (!done_local.empty()) {
+      std::lock_guard<std::mutex> g(s->mu);
+      s->completions.insert(s->completions.end(), done_local.begin(), done_local.end());
+      s->completed += done_local.size();
+    }
+    if (stopping && waiting.empty() && building.empty() && flight.empty()) {
+      std::lock_guard<std::mutex> g(s->mu);
+      if (s->incoming.empty()) return;
+    }
+    if (!flight.empty() && waiting.empty()) std::this_thread::yield();
+  }
+}
+
+}  // namespace
+}  // namespace mpt
+
+using namespace mpt;
+
+extern "C" {
+
+uint64_t mpt_now_ns(void) { return steady_ns(); }
+
+mpt_status mpt_serve_start(mpt_ctx_t ctx, const mpt_serve_config* cfg, mpt_server_t* out) {
+  if (!ctx || !out) return fail(MPT_EINVAL, "mpt_serve_start: NULL argument");
+  *out = nullptr;
+  mpt_status st = batch_setup(ctx);
+  if (st != MPT_OK) return st;
+  for (auto& sl : ctx->slots)
+    if (sl.held) return fail(MPT_EAGAIN, "mpt_serve_start: batches of this context are still held");
+  mpt_server_s* s = new mpt_server_s;
+  s->ctx = ctx;
+  mpt_serve_config c = cfg ? *cfg : mpt_serve_config{};
+  if (c.staging_budget_bytes == 0) c.staging_budget_bytes = 8ull << 30;
+  if (c.max_batch == 0 || c.max_batch > ctx->slots[0].max_xfers) c.max_batch = ctx->slots[0].max_xfers;
+  if (c.max_inflight_batches == 0 || c.max_inflight_batches > ctx->slots.size())
+    c.max_inflight_batches = (uint32_t)ctx->slots.size();
+  s->cfg = c;
+  if (cudaSetDevice(ctx->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete s;
+    return fail(MPT_ECUDA, "mpt_serve_start: stream");
+  }
+  s->worker = std::thread(serve_loop, s);
+  *out = s;
+  return MPT_OK;
+}
+
+mpt_status mpt_serve_submit(mpt_server_t s, const mpt_xfer* x, uint64_t tag, uint64_t arrival_ns) {
+  if (!s || !x) return fail(MPT_EINVAL, "mpt_serve_submit: NULL argument");
+  if (x->dir > MPT_D2H) return fail(MPT_EINVAL, "mpt_serve_submit: direction %u", x->dir);
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    if (s->stop) return fail(MPT_EINVAL, "mpt_serve_submit: server is stopping");
+    if (s->error != MPT_OK) return fail(s->error, "mpt_serve_submit: server failed: %s", s->error_msg.c_str());
+    s->incoming.push_back(Request{*x, tag, arrival_ns ? arrival_ns : steady_ns(), 0});
+  }
+  s->submitted++;
+  s->cv.notify_one();
+  return MPT_OK;
+}
+
+mpt_status mpt_serve_poll(mpt_server_t s, mpt_completion* out, size_t cap, size_t* n) {
+  if (!s || !n || (cap && !out)) return fail(MPT_EINVAL, "mpt_serve_poll: NULL argument");
+  std::lock_guard<std::mutex> g(s->mu);
+  const size_t k = std::min(cap, s->completions.size());
+  std::copy(s->completions.begin(), s->completions.begin() + k, out);
+  s->completions.erase(s->completions.begin(), s->completions.begin() + k);
+  *n = k;
+  if (s->error != MPT_OK) return fail(s->error, "mpt_serve_poll: server failed: %s", s->error_msg.c_str());
+  return MPT_OK;
+}
+
+mpt_status mpt_serve_stats(mpt_server_t s, mpt_serve_stats_t* out) {
+  if (!s || !out) return fail(MPT_EINVAL, "mpt_serve_stats: NULL argument");
+  out->submitted = s->submitted;
+  out->completed = s->completed;
+  out->batches = s->batches;
+  out->inflight_bytes = s->inflight_bytes;
+  out->max_inflight_bytes = s->max_inflight_bytes;
+  out->rejected = s->rejected;
+  return MPT_OK;
+}
+
+mpt_status mpt_serve_stop(mpt_server_t s) {
+  if (!s) return MPT_OK;
+  {
+    std::lock_guard<std::mutex> g(s->mu);
+    s->stop = true;
+  }
+  s->cv.notify_one();
+  if (s->worker.joinable()) s->worker.join();
+  mpt_status st = s->error;
+  if (st != MPT_OK) fail(st, "mpt_serve_stop: server failed: %s", s->error_msg.c_str());
+  // completions not yet polled are dropped with the server
+  cudaStreamSynchronize(s->stream);
+  cudaStreamDestroy(s->stream);
+  delete s;
+  return st;
+}
+
+}  // extern "C"

@@ -141,19 +141,20 @@ def batch_workload(n: int = 4096, seed: int = SEED_BATCH, min_bytes: int = 256,
 
 def serving_schedule(rate_per_s: float, duration_s: float, seed: int = SEED_SERVE,
                      median_bytes: int = 1 << 20, sigma: float = 1.5,
-                     cap_bytes: int = 256 << 20, mix=(0.5, 0.25, 0.25)):
+                     cap_bytes: int = 256 << 20, mix=(0.5, 0.25, 0.25), max_requests: int | None = None):
     """Open-loop Poisson arrivals with lognormal sizes and a direction mix.
 
     Inter-arrival gaps are ``-ln(1-u)/rate``; sizes are
     ``min(cap, max(16, round(median*exp(sigma*z))))`` rounded up to a multiple of 16,
     with ``z`` standard normal from Box-Muller on two splitmix doubles; the direction is
     0 (device-to-device), 1 (host-to-device) or 2 (device-to-host) by ``mix``.
+    Stops at ``duration_s`` or after ``max_requests`` requests, whichever comes first.
     Returns a list of (arrival_s, nbytes, direction).
     """
     out = []
     t = 0.0
     k = 0
-    while True:
+    while max_requests is None or k < max_requests:
         u = unit_double(splitmix64_scalar(seed, 4 * k))
         t += -math.log(1.0 - u) / rate_per_s
         if t >= duration_s:

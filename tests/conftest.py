@@ -11,6 +11,9 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU and the compiled library")
     config.addinivalue_line("markers", "slow: full-size case (minutes)")
+    # a stuck test fails on its own instead of holding the run (pytest-timeout, when present)
+    if config.pluginmanager.hasplugin("timeout") and not getattr(config.option, "timeout", None):
+        config.option.timeout = 300
 
 
 def pytest_collection_modifyitems(config, items):

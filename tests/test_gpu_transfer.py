@@ -240,3 +240,46 @@ def test_staged_chunk_above_stage_size_rejected(ctx):
         mpt.mpt_capture(ctx, plan, dst.ptr, src.ptr)
     assert e.value.status == mpt.MPT_EINVAL
     mpt.mpt_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("specs,direction", [
+    ([(P.CE, 32768, 256 * 1024), (P.SM, 32768, 256 * 1024)], P.D2D),
+    ([(P.CE, 30000, 256 * 1024), (P.SM, 30000, 512 * 1024, 0, mpt.MPT_SM_BULK), (P.HS, 5536, 256 * 1024)], P.D2D),
+    ([(P.CE, 20000, 256 * 1024), (P.ZC, 25536, 256 * 1024), (P.HS, 20000, 128 * 1024)], P.H2D),
+    ([(P.CE, 20000, 256 * 1024), (P.ZC, 25536, 256 * 1024), (P.HS, 20000, 128 * 1024)], P.D2H),
+])
+def test_graph_rebind_in_place(specs, direction):
+    """A captured graph retargeted at new addresses (cudaGraphExecUpdate, no new
+    instantiation) moves the new message exactly, and the capture fast path reuses an
+    idle cached graph of the same plan."""
+    import torch
+    ctx = mpt.mpt_ctx_create(0)
+    n = 3 * MiB + 32
+    sw, dw = ("host" if direction == P.H2D else "dev"), ("host" if direction == P.D2H else "dev")
+    bufs = [(Buf(n, sw), Buf(n, dw)) for _ in range(3)]
+    datas = [seeded("u32", 40 + i, n) for i in range(3)]
+    for (s, _), d in zip(bufs, datas):
+        s.fill(d)
+    plan = mpt.mpt_plan(ctx, n, direction, specs)
+    g = mpt.mpt_capture(ctx, plan, bufs[0][1].ptr, bufs[0][0].ptr)
+    mpt.mpt_launch(g, torch.cuda.current_stream())
+    assert np.array_equal(bufs[0][1].numpy(), datas[0])
+    mpt.mpt_graph_rebind(g, plan, bufs[1][1].ptr, bufs[1][0].ptr)
+    info = mpt.mpt_graph_get_info(g)
+    assert info["rebinds"] == 1 and info["update_us"] > 0
+    mpt.mpt_launch(g, torch.cuda.current_stream())
+    assert np.array_equal(bufs[1][1].numpy(), datas[1]) and bufs[1][1].guards_intact()
+    mpt.mpt_graph_release(g)  # now only the cache holds it
+    g2 = mpt.mpt_capture(ctx, plan, bufs[2][1].ptr, bufs[2][0].ptr)  # fast path: retarget, no instantiate
+    assert g2 == g and mpt.mpt_graph_get_info(g2)["rebinds"] == 2
+    mpt.mpt_launch(g2, torch.cuda.current_stream())
+    assert np.array_equal(bufs[2][1].numpy(), datas[2])
+    other = mpt.mpt_plan(ctx, n, direction, [(specs[0][0], 65536, 64 * 1024)])
+    with pytest.raises(mpt.MptError) as e:
+        mpt.mpt_graph_rebind(g2, other, bufs[0][1].ptr, bufs[0][0].ptr)
+    assert e.value.status == mpt.MPT_EINVAL
+    mpt.mpt_graph_release(g2)
+    mpt.mpt_plan_destroy(other)
+    mpt.mpt_plan_destroy(plan)
+    assert mpt.mpt_ctx_status(ctx)[0] == mpt.MPT_OK
+    mpt.mpt_ctx_destroy(ctx)

@@ -125,3 +125,9 @@ def test_batch_and_serving_workloads_shape():
     assert all(16 <= nb <= 256 << 20 and nb % 16 == 0 for _, nb, _ in sched)
     med = sorted(nb for _, nb, _ in sched)[len(sched) // 2]
     assert (1 << 20) * 0.8 < med < (1 << 20) * 1.25
+
+
+def test_serving_schedule_request_cap():
+    assert len(payload.serving_schedule(1e6, 1e9, max_requests=25)) == 25
+    capped = payload.serving_schedule(1000.0, 0.5, max_requests=10 ** 9)
+    assert 400 < len(capped) < 600 and capped[-1][0] < 0.5
