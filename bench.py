@@ -289,13 +289,33 @@ def run_ours(args):
             mpt.mpt_tune_save(ctx, args.tune_out)
 
     tuned_plans, tuned_graphs = capture_all("tuned")
-    kernels_per_step = sum(mpt.mpt_graph_get_info(g)["kernel_nodes"] for g in tuned_graphs)
+    # the step's handles: graph or direct issue per size, as the tuner measured faster
+    # (graph and eager modes tuned separately); graph when no measurement exists
+    step_plans, step_handles, step_modes = [], [], []
+    for n, o in zip(SIZES, offs):
+        mode = mpt.MPT_PREPARE_GRAPH
+        try:
+            _, g_us = mpt.mpt_tune_get(ctx, mpt.MPT_D2D, n, mpt.MPT_MODE_GRAPH)
+            _, e_us = mpt.mpt_tune_get(ctx, mpt.MPT_D2D, n, mpt.MPT_MODE_EAGER)
+            if e_us < g_us:
+                mode = mpt.MPT_PREPARE_EAGER
+        except mpt.MptError:
+            pass
+        p = mpt.mpt_plan(ctx, n, mpt.MPT_D2D, None, 16,
+                         mpt.MPT_PLAN_EAGER if mode == mpt.MPT_PREPARE_EAGER else mpt.MPT_LAYOUT_CONTIG)
+        step_plans.append(p)
+        step_handles.append(mpt.mpt_prepare(ctx, p, base_d + o, base_s + o, mode))
+        step_modes.append("eager" if mode == mpt.MPT_PREPARE_EAGER else "graph")
+
+    def kernels_of(p):
+        return sum(1 for q in mpt.mpt_plan_paths(p) if q["kind"] in (mpt.MPT_PATH_SM, mpt.MPT_PATH_ZC))
+    kernels_per_step = sum(kernels_of(p) for p in step_plans)
     total_bytes = sum(SIZES)
 
     clocks = ClockSampler(local)
     clocks.start()
     for _ in range(args.warmup):
-        for g in tuned_graphs:
+        for g in step_handles:
             mpt.mpt_launch(g, stream)
     stream.synchronize()
 
@@ -307,7 +327,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     t_start.record(stream)
     for k in range(args.steps):
-        for g in tuned_graphs:
+        for g in step_handles:
             mpt.mpt_launch(g, stream)
     t_end.record(stream)
     stream.synchronize()
@@ -322,7 +342,7 @@ def run_ours(args):
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nsz + 1)] for _ in range(bk)]
     for k in range(bk):
         ev[k][0].record(stream)
-        for i, g in enumerate(tuned_graphs):
+        for i, g in enumerate(step_handles):
             mpt.mpt_launch(g, stream)
             ev[k][i + 1].record(stream)
     stream.synchronize()
@@ -364,7 +384,8 @@ def run_ours(args):
     reps = args.baseline_reps
     base = {}
     if not args.no_baselines:
-        base["tuned"] = time_graphs(tuned_graphs, reps)
+        base["tuned"] = time_graphs(step_handles, reps)
+        base["tuned_graph_only"] = time_graphs(tuned_graphs, reps)
         for kind in ("ce", "sm", "split"):
             plans, graphs = capture_all(kind)
             base[kind] = time_graphs(graphs, reps)
@@ -419,7 +440,7 @@ def run_ours(args):
         e2e_steps = max(1, min(args.steps, 10))
         for _ in range(2):
             mpt.mpt_launch(g_up, stream)
-            for g in tuned_graphs:
+            for g in step_handles:
                 mpt.mpt_launch(g, stream)
             mpt.mpt_launch(g_down, stream)
         stream.synchronize()
@@ -427,7 +448,7 @@ def run_ours(args):
         e0.record(stream)
         for _ in range(e2e_steps):
             mpt.mpt_launch(g_up, stream)
-            for g in tuned_graphs:
+            for g in step_handles:
                 mpt.mpt_launch(g, stream)
             mpt.mpt_launch(g_down, stream)
         e1.record(stream)
@@ -457,6 +478,9 @@ def run_ours(args):
         serving = run_serving(mpt, torch, ctx, [float(r) for r in args.serve_rates.split(",")], args.serve_seconds)
         ok = ok and all(r["errors"] == 0 for r in serving)
 
+    if args.tune_out:
+        mpt.mpt_tune_save(ctx, args.tune_out)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         gbs, el, moved, desc = cpu_oracle_sample({}, budget_s=args.cpu_seconds)
@@ -465,13 +489,13 @@ def run_ours(args):
     sweep = []
     for i, n in enumerate(SIZES):
         gb = lambda ms: round(n / (ms / 1e3) / 1e9, 3) if ms and ms > 0 else None
-        row = {"bytes": n, "in_sweep_gbs": gb(per_size_tuned[i]),
+        row = {"bytes": n, "in_sweep_gbs": gb(per_size_tuned[i]), "mode": step_modes[i],
                "plan": [(p["kind"], p["share"], p["chunk_bytes"], p["ctas"], p["flags"])
-                        for p in mpt.mpt_plan_paths(tuned_plans[i])]}
+                        for p in mpt.mpt_plan_paths(step_plans[i])]}
         if base:
             best_single = min(base["ce"][i], base["sm"][i])
             row.update({
-                "tuned_graph_gbs": gb(base["tuned"][i]),
+                "tuned_gbs": gb(base["tuned"][i]), "tuned_graph_gbs": gb(base["tuned_graph_only"][i]),
                 "ce_graph_gbs": gb(base["ce"][i]), "sm_graph_gbs": gb(base["sm"][i]),
                 "split50_graph_gbs": gb(base["split"][i]), "split50_eager_gbs": gb(base["split_eager"][i]),
                 "tuned_eager_gbs": gb(base["tuned_eager"][i]), "best_single_gbs": gb(best_single),
@@ -481,9 +505,9 @@ def run_ours(args):
 
     traffic = roofline_traffic("vec" if variant == 0 else "bulk", ctas)
 
-    for g in tuned_graphs:
+    for g in tuned_graphs + step_handles:
         mpt.mpt_graph_release(g)
-    for p in tuned_plans:
+    for p in tuned_plans + step_plans:
         mpt.mpt_plan_destroy(p)
     mpt.mpt_ctx_destroy(ctx)
 
@@ -493,7 +517,8 @@ def run_ours(args):
             "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(slowest / args.steps * 1e3, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": "d2d sweep 8B-1GiB fp32 seed 0x5EED0002, tuned multi-path graphs",
+            "config": {"workload": "d2d sweep 8B-1GiB fp32 seed 0x5EED0002, tuned multi-path plans, "
+                                   "graph or direct issue per size as tuned",
                        "messages_per_step": len(SIZES), "bytes_per_step": total_bytes,
                        "l2": "cold: every message has its own region; 4 GiB touched per step > 129 MiB L2",
                        "parallelism": f"replicas x{world}"},
@@ -537,14 +562,7 @@ def run_batched(mpt, torch, ctx, stream, reps=5):
     import payload
     period = 64 * MiB
     sizes, d2d, gaps = payload.batch_workload(4096)
-    items, offs = [], {"dev": 0, "host": 0, "dst": 0}
-    for sz, is_d2d, gap in zip(sizes, d2d, gaps):
-        a = "dev" if is_d2d else "host"
-        offs[a] += gap
-        offs["dst"] += gap
-        items.append((a, offs[a], offs["dst"], sz))
-        offs[a] += sz
-        offs["dst"] += sz
+    items, offs = payload.batch_layout(sizes, d2d, gaps)
     base_t = torch.from_numpy(payload.fill("bf16", payload.SEED_BATCH, period))
     src = {"dev": _tiled_arena(torch, offs["dev"] + 64, False, base_t, period),
            "host": _tiled_arena(torch, offs["host"] + 64, True, base_t, period)}
@@ -725,7 +743,8 @@ def run_host_sweep(mpt, torch, ctx, stream, max_bytes=2 << 30, reps=3, tune=True
     def timed(launch, n_reps):
         ts = []
         for _ in range(n_reps + 1):
-            flush.fill_(1)
+            with torch.cuda.stream(stream):  # the flush must finish before the timed launch
+                flush.fill_(1)
             e0.record(stream)
             launch()
             e1.record(stream)
@@ -829,14 +848,8 @@ def run_batch_only(args):
     ctx = mpt.mpt_ctx_create(0)
     mpt.mpt_batch_configure(ctx, 2, 4096, args.batch_ctas, args.batch_tile)
     sizes, d2d, gaps = payload.batch_workload(args.batch_n)
-    items, offs = [], {"dev": 0, "host": 0, "dst": 0}
-    for sz, is_d2d, gap in zip(sizes, d2d, gaps):
-        a = "dev" if (args.batch_only == "d2d" or (args.batch_only == "mix" and is_d2d)) else "host"
-        offs[a] += gap
-        offs["dst"] += gap
-        items.append((a, offs[a], offs["dst"], sz))
-        offs[a] += sz
-        offs["dst"] += sz
+    which = {"d2d": [True] * len(sizes), "h2d": [False] * len(sizes), "mix": d2d}[args.batch_only]
+    items, offs = payload.batch_layout(sizes, which, gaps, align=args.batch_align)
     src = {"dev": torch.zeros(offs["dev"] + 64, dtype=torch.uint8, device="cuda"),
            "host": torch.zeros(offs["host"] + 64, dtype=torch.uint8).pin_memory()}
     dst = torch.empty(offs["dst"] + 64, dtype=torch.uint8, device="cuda")
@@ -926,6 +939,7 @@ def main(argv=None):
     ap.add_argument("--batch-n", type=int, default=4096)
     ap.add_argument("--batch-ctas", type=int, default=0)
     ap.add_argument("--batch-tile", type=int, default=0)
+    ap.add_argument("--batch-align", type=int, default=16, help="1 packs transfers back to back (misaligned)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("at least 3 warm-up steps")

@@ -120,7 +120,7 @@ typedef struct {
   uint64_t staging_bytes;  /* staging memory this graph owns */
   double update_us;        /* last in-place retarget (mpt_graph_rebind or a capture that reused it) */
   uint32_t rebinds;        /* in-place retargets so far */
-  uint32_t reserved;
+  uint32_t mode;           /* 0: a CUDA graph; 1: prepared for direct issue (mpt_prepare) */
 } mpt_graph_info;
 
 /* Cost model of one path kind: per-chunk issue latency and bandwidth (the staged path's
@@ -218,6 +218,18 @@ MPT_API mpt_status mpt_plan_destroy(mpt_plan_t plan);
  * staged path above the stage size), ECUDA, ENOMEM. */
 MPT_API mpt_status mpt_capture(mpt_ctx_t ctx, mpt_plan_t plan, void* dst, const void* src, mpt_graph_t* out);
 
+/* Prepare a transfer for repeated launches with mpt_launch, as a graph (mode
+ * MPT_PREPARE_GRAPH, exactly mpt_capture), for direct issue on the launching stream
+ * (MPT_PREPARE_EAGER: the eager engine of mpt_launch_eager, with no fork/join at all when
+ * the plan uses a single copy-engine or kernel path), or whichever of the two the
+ * context's tuner measured faster for this direction and log2 size bucket
+ * (MPT_PREPARE_AUTO; graph when either measurement is missing).  The paper finds graphs
+ * help only above a few MB and tunes graph and non-graph execution separately (Sec. 4.4,
+ * Sec. 5.3).  Release with mpt_graph_release; eager handles are not cached. */
+typedef enum { MPT_PREPARE_GRAPH = 0, MPT_PREPARE_EAGER = 1, MPT_PREPARE_AUTO = 2 } mpt_prepare_mode;
+MPT_API mpt_status mpt_prepare(mpt_ctx_t ctx, mpt_plan_t plan, void* dst, const void* src, uint32_t mode,
+                               mpt_graph_t* out);
+
 /* Launch a captured graph on `stream`: it starts after the work already queued on the
  * stream and later work on the stream waits for all of its chunks (Sec. 4.5 "Final
  * Synchronization").  Asynchronous.  Launches of one graph run one after another. */
@@ -296,9 +308,11 @@ MPT_API mpt_status mpt_model_optimize(const mpt_model* m, uint64_t nbytes, uint3
  * mode `mode` (MPT_MODE_GRAPH or MPT_MODE_EAGER) on this context's GPU -- single copy
  * engine paths with 1..8 chunks, the SM kernel (vec128/bulk, several CTA counts), the
  * zero-copy kernel, copy engine + kernel splits at several shares and chunk counts, the
- * staged path -- each the median of `reps` timed runs (0 = default) with the L2 flushed
- * before every run, and store the fastest for the message's log2 size bucket.  Blocking;
- * allocates scratch buffers of `nbytes` (kept by the context).  out (capacity 4, nullable),
+ * staged path -- each the median of `reps` timed runs (0 = default), every run starting
+ * with a cold L2 full of dirty lines (a 256 MiB write first, as after the kernel that
+ * produced the data), and store the fastest for the message's log2 size bucket.  Blocking;
+ * allocates scratch buffers of `nbytes` (kept by the context).  MPT_TUNE_VERBOSE=1 prints
+ * every candidate's timing to stderr.  out (capacity 4, nullable),
  * out_n and out_us (nullable) receive the winner.  Errors: EINVAL, ECUDA, ENOMEM. */
 MPT_API mpt_status mpt_tune(mpt_ctx_t ctx, uint32_t dir, uint64_t nbytes, uint32_t mode, uint32_t reps,
                             mpt_path_spec* out, uint32_t* out_n, double* out_us);
@@ -319,7 +333,7 @@ MPT_API mpt_status mpt_tune_get(mpt_ctx_t ctx, uint32_t dir, uint64_t nbytes, ui
 
 /* Size the context's batch ring: `slots` batches in flight at once (default 4), up to
  * `max_xfers` transfers per batch (default 4096), `ctas` CTAs of the batch kernel
- * (default 4 x SMs) and `tile_bytes` per work item (default 256 KiB; >= 4096, multiple of
+ * (default 3 x SMs) and `tile_bytes` per work item (default 256 KiB; >= 4096, multiple of
  * 16).  0 keeps a default.  Waits for the device; fails with EAGAIN while a batch is held.
  * The ring is built on first use with defaults when this is never called. */
 MPT_API mpt_status mpt_batch_configure(mpt_ctx_t ctx, uint32_t slots, uint32_t max_xfers, uint32_t ctas,

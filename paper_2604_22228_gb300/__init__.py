@@ -18,7 +18,8 @@ import ctypes as C
 from . import _ffi
 from ._ffi import (MPT_D2D, MPT_D2H, MPT_H2D, MPT_LAYOUT_CONTIG, MPT_LAYOUT_INTERLEAVE, MPT_MAX_CHUNKS,  # noqa: F401
                    MPT_NOALLOC_MAX_RANGES, MPT_MAX_PATHS, MPT_PATH_CE, MPT_PATH_HS, MPT_PATH_SM, MPT_PATH_ZC, MPT_SHARE_ONE, MPT_SM_BULK,
-                   MPT_SM_VEC128, MPT_PLAN_EAGER, MPT_MODE_GRAPH, MPT_MODE_EAGER, STATUS_NAMES)
+                   MPT_SM_VEC128, MPT_PLAN_EAGER, MPT_MODE_GRAPH, MPT_MODE_EAGER, MPT_PREPARE_GRAPH,
+                   MPT_PREPARE_EAGER, MPT_PREPARE_AUTO, STATUS_NAMES)
 from ._ffi import MPT_EAGAIN, MPT_ECUDA, MPT_EINVAL, MPT_ENOMEM, MPT_ENOTSUP, MPT_ETIMEDOUT, MPT_OK  # noqa: F401
 
 
@@ -126,6 +127,12 @@ def mpt_plan_destroy(plan: int) -> None:
 def mpt_capture(ctx: int, plan: int, dst, src) -> int:
     h = C.c_void_p()
     _check(lib().mpt_capture(ctx, plan, _ptr(dst), _ptr(src), C.byref(h)), "mpt_capture")
+    return h.value
+
+
+def mpt_prepare(ctx: int, plan: int, dst, src, mode: int = MPT_PREPARE_AUTO) -> int:
+    h = C.c_void_p()
+    _check(lib().mpt_prepare(ctx, plan, _ptr(dst), _ptr(src), mode, C.byref(h)), "mpt_prepare")
     return h.value
 
 

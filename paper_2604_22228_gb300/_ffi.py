@@ -23,6 +23,7 @@ MPT_LAYOUT_CONTIG, MPT_LAYOUT_INTERLEAVE = 0, 1
 MPT_SM_VEC128, MPT_SM_BULK = 0, 1
 MPT_PLAN_EAGER = 0x100
 MPT_MODE_GRAPH, MPT_MODE_EAGER = 0, 1
+MPT_PREPARE_GRAPH, MPT_PREPARE_EAGER, MPT_PREPARE_AUTO = 0, 1, 2
 MPT_SHARE_ONE = 65536
 MPT_MAX_PATHS = 8
 MPT_MAX_CHUNKS = 1 << 20
@@ -48,7 +49,7 @@ class mpt_graph_info(C.Structure):
     _fields_ = [("nodes", C.c_uint32), ("memcpy_nodes", C.c_uint32), ("kernel_nodes", C.c_uint32),
                 ("memset_nodes", C.c_uint32), ("create_us", C.c_double), ("construct_us", C.c_double),
                 ("instantiate_us", C.c_double), ("staging_bytes", C.c_uint64), ("update_us", C.c_double),
-                ("rebinds", C.c_uint32), ("reserved", C.c_uint32)]
+                ("rebinds", C.c_uint32), ("mode", C.c_uint32)]
 
 
 class mpt_path_model(C.Structure):
@@ -93,6 +94,7 @@ SIGNATURES = {
     "mpt_plan_paths": (C.c_int, [H, P(mpt_path_spec), C.c_uint32, P(C.c_uint32)]),
     "mpt_plan_destroy": (C.c_int, [H]),
     "mpt_capture": (C.c_int, [H, H, C.c_void_p, C.c_void_p, P(H)]),
+    "mpt_prepare": (C.c_int, [H, H, C.c_void_p, C.c_void_p, C.c_uint32, P(H)]),
     "mpt_launch": (C.c_int, [H, C.c_void_p]),
     "mpt_graph_get_info": (C.c_int, [H, P(mpt_graph_info)]),
     "mpt_graph_rebind": (C.c_int, [H, H, C.c_void_p, C.c_void_p]),

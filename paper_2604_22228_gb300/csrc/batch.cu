@@ -20,6 +20,7 @@
 #include <cstring>
 #include <thread>
 
+#include "copy_device.cuh"
 #include "ctx.h"
 
 #define CUDA_TRY(expr)                                                                           \
@@ -39,32 +40,10 @@ __device__ __forceinline__ uint64_t now_ns() {
   return t;
 }
 
-// Copy [0, n) bytes s -> o with the whole CTA: 16-byte vectors when both addresses are
-// 16-byte aligned, bytes for the rest.
-__device__ __forceinline__ void cta_copy(const uint8_t* s, uint8_t* o, uint64_t n) {
-  const uint32_t tid = threadIdx.x;
-  if (((reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(o)) & 15) == 0) {
-    const uint64_t nv = n >> 4;
-    const uint4* sv = reinterpret_cast<const uint4*>(s);
-    uint4* ov = reinterpret_cast<uint4*>(o);
-    uint64_t v = tid;
-    for (; v + 3 * blockDim.x < nv; v += 4 * blockDim.x) {
-      uint4 a = sv[v], b = sv[v + blockDim.x], c = sv[v + 2 * blockDim.x], d = sv[v + 3 * blockDim.x];
-      ov[v] = a;
-      ov[v + blockDim.x] = b;
-      ov[v + 2 * blockDim.x] = c;
-      ov[v + 3 * blockDim.x] = d;
-    }
-    for (; v < nv; v += blockDim.x) ov[v] = sv[v];
-    for (uint64_t b = (nv << 4) + tid; b < n; b += blockDim.x) o[b] = s[b];
-  } else {
-    for (uint64_t b = tid; b < n; b += blockDim.x) o[b] = s[b];
-  }
-}
-
 }  // namespace
 
-__global__ void __launch_bounds__(kVecThreads) k_batch(BatchArgs a) {
+template <bool kAny>
+__device__ __forceinline__ void batch_body(const BatchArgs& a) {
   __shared__ uint32_t s_item;
   const BatchHeader h = *a.hdr;
   if (threadIdx.x == 0) atomicMax(a.start_inv, ~now_ns());
@@ -85,7 +64,11 @@ __global__ void __launch_bounds__(kVecThreads) k_batch(BatchArgs a) {
     const uint64_t off = (uint64_t)(item - d.first_tile) * h.tile_bytes;
     if (off < d.bytes) {
       const uint64_t len = d.bytes - off < h.tile_bytes ? d.bytes - off : h.tile_bytes;
-      cta_copy(reinterpret_cast<const uint8_t*>(d.src) + off, reinterpret_cast<uint8_t*>(d.dst) + off, len);
+      const uint8_t* src = reinterpret_cast<const uint8_t*>(d.src) + off;
+      uint8_t* dst = reinterpret_cast<uint8_t*>(d.dst) + off;
+      // coherent loads for every descriptor: one copy loop keeps the kernel at 40
+      // registers (three 512-thread CTAs per SM); host-memory sources need them anyway
+      cta_copy<true, kAny>(src, dst, len);
     }
     if (d.flags & kDescHostDst) __threadfence_system();
     else __threadfence();
@@ -101,6 +84,9 @@ __global__ void __launch_bounds__(kVecThreads) k_batch(BatchArgs a) {
   }
 }
 
+__global__ void __launch_bounds__(kVecThreads, 3) k_batch(BatchArgs a) { batch_body<false>(a); }
+__global__ void __launch_bounds__(kVecThreads) k_batch_any(BatchArgs a) { batch_body<true>(a); }
+
 namespace {
 
 constexpr uint32_t kDefaultSlots = 4;
@@ -114,8 +100,10 @@ uint64_t host_ns() {
 }
 
 void slot_free(BatchSlot& s) {
-  if (s.exec) cudaGraphExecDestroy(s.exec);
-  if (s.graph) cudaGraphDestroy(s.graph);
+  for (int i = 0; i < 2; ++i) {
+    if (s.exec[i]) cudaGraphExecDestroy(s.exec[i]);
+    if (s.graph[i]) cudaGraphDestroy(s.graph[i]);
+  }
   if (s.done_ev) cudaEventDestroy(s.done_ev);
   if (s.h_table) cudaFreeHost(s.h_table);
   if (s.h_flags) cudaFreeHost(s.h_flags);
@@ -150,27 +138,30 @@ mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t cta
   uint32_t* hf_dev = nullptr;
   CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&hf_dev), s.h_flags, 0));
   s.args.host_flags = hf_dev;
-  // graph: table copy and counter reset, then the kernel
-  CUDA_TRY(cudaGraphCreate(&s.graph, 0));
-  cudaGraphNode_t cp, ms, kn;
-  CUDA_TRY(cudaGraphAddMemcpyNode1D(&cp, s.graph, nullptr, 0, s.d_table, s.h_table, s.table_bytes,
-                                    cudaMemcpyHostToDevice));
-  cudaMemsetParams mp{};
-  mp.dst = s.d_ctrl;
-  mp.value = 0;
-  mp.elementSize = 1;
-  mp.width = s.ctrl_bytes;
-  mp.height = 1;
-  CUDA_TRY(cudaGraphAddMemsetNode(&ms, s.graph, nullptr, 0, &mp));
-  cudaGraphNode_t deps[2] = {cp, ms};
-  void* params[] = {&s.args};
-  cudaKernelNodeParams kp{};
-  kp.func = reinterpret_cast<void*>(&k_batch);
-  kp.gridDim = dim3(ctas);
-  kp.blockDim = dim3(kVecThreads);
-  kp.kernelParams = params;
-  CUDA_TRY(cudaGraphAddKernelNode(&kn, s.graph, deps, 2, &kp));
-  CUDA_TRY(cudaGraphInstantiate(&s.exec, s.graph, 0));
+  // graphs: table copy and counter reset, then the kernel (aligned-only or any alignment)
+  for (int gi = 0; gi < 2; ++gi) {
+    CUDA_TRY(cudaGraphCreate(&s.graph[gi], 0));
+    cudaGraphNode_t cp, ms, kn;
+    CUDA_TRY(cudaGraphAddMemcpyNode1D(&cp, s.graph[gi], nullptr, 0, s.d_table, s.h_table, s.table_bytes,
+                                      cudaMemcpyHostToDevice));
+    cudaMemsetParams mp{};
+    mp.dst = s.d_ctrl;
+    mp.value = 0;
+    mp.elementSize = 1;
+    mp.width = s.ctrl_bytes;
+    mp.height = 1;
+    CUDA_TRY(cudaGraphAddMemsetNode(&ms, s.graph[gi], nullptr, 0, &mp));
+    cudaGraphNode_t deps[2] = {cp, ms};
+    void* params[] = {&s.args};
+    cudaKernelNodeParams kp{};
+    kp.func = gi == 0 ? reinterpret_cast<void*>(&k_batch) : reinterpret_cast<void*>(&k_batch_any);
+    // the general kernel holds two CTAs per SM (64 registers): keep all of them resident
+    kp.gridDim = dim3(gi == 0 ? ctas : std::min<uint32_t>(ctas, 2u * (uint32_t)c->sms));
+    kp.blockDim = dim3(kVecThreads);
+    kp.kernelParams = params;
+    CUDA_TRY(cudaGraphAddKernelNode(&kn, s.graph[gi], deps, 2, &kp));
+    CUDA_TRY(cudaGraphInstantiate(&s.exec[gi], s.graph[gi], 0));
+  }
   return MPT_OK;
 }
 
@@ -195,8 +186,9 @@ mpt_status batch_setup(mpt_ctx_t c) {
   if (!c->slots.empty()) return MPT_OK;
   const uint32_t nslots = c->batch_slots ? c->batch_slots : kDefaultSlots;
   const uint32_t maxx = c->batch_max_xfers ? c->batch_max_xfers : kDefaultMaxXfers;
-  // four 512-thread CTAs per SM: full occupancy, which the latency of host-link reads needs
-  const uint32_t ctas = c->batch_ctas ? c->batch_ctas : 4u * (uint32_t)c->sms;
+  // three 512-thread CTAs per SM (the aligned kernel's register limit): high occupancy,
+  // which the latency of host-link reads needs; all CTAs resident at once
+  const uint32_t ctas = c->batch_ctas ? c->batch_ctas : 3u * (uint32_t)c->sms;
   if (!c->batch_tile) c->batch_tile = kDefaultTile;
   c->slots.resize(nslots);
   for (auto& s : c->slots) {
@@ -300,17 +292,19 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
   BatchDesc* d = reinterpret_cast<BatchDesc*>(s.h_table + sizeof(BatchHeader));
   uint64_t tiles = 0;
   const uint64_t tile = c->batch_tile;
+  bool any_shift = false;
   for (size_t i = 0; i < n; ++i) {
     const mpt_xfer& x = xfers[i];
+    any_shift |= (((uintptr_t)x.src ^ (uintptr_t)x.dst) & 15) != 0 && x.bytes >= 16;
     const uint64_t t = std::max<uint64_t>(1, (x.bytes + tile - 1) / tile);
-    d[i] = BatchDesc{(uint64_t)(uintptr_t)x.src, (uint64_t)(uintptr_t)x.dst, x.bytes, (uint32_t)tiles, (uint32_t)t,
-                     x.dir == MPT_D2H ? kDescHostDst : 0u, 0u};
+    const uint32_t fl = (x.dir == MPT_D2H ? kDescHostDst : 0u) | (x.dir != MPT_D2D ? kDescHostSide : 0u);
+    d[i] = BatchDesc{(uint64_t)(uintptr_t)x.src, (uint64_t)(uintptr_t)x.dst, x.bytes, (uint32_t)tiles, (uint32_t)t, fl, 0u};
     tiles += t;
   }
   if (tiles >= (1ull << 32)) return fail(MPT_EINVAL, "mpt_batch_submit: batch too large for 32-bit tile indices");
   *h = BatchHeader{(uint32_t)n, (uint32_t)tiles, (uint32_t)tile, s.epoch};
   const cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  CUDA_TRY(cudaGraphLaunch(s.exec, cs));
+  CUDA_TRY(cudaGraphLaunch(s.exec[any_shift ? 1 : 0], cs));
   CUDA_TRY(cudaEventRecord(s.done_ev, cs));
   s.held = true;
   s.n = n;

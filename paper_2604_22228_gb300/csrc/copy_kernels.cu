@@ -18,6 +18,7 @@
 // Every device-side wait is bounded by the global timer and records MPT_ETIMEDOUT in
 // the context's status word instead of spinning forever.
 #include "kernels.cuh"
+#include "copy_device.cuh"
 
 #include <algorithm>
 
@@ -37,35 +38,13 @@ __device__ __forceinline__ void record_timeout(uint32_t* status, uint32_t site) 
   if (status) atomicCAS(status, 0u, (site << 8) | kTimedOut);
 }
 
-__device__ __forceinline__ uint4 ld_stream(const uint4* p) {
-  uint4 v;
-  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(p));
-  return v;
-}
-
-__device__ __forceinline__ uint4 ld_plain(const uint4* p) {
-  uint4 v;
-  asm volatile("ld.global.v4.u32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-               : "l"(p));
-  return v;
-}
-
-__device__ __forceinline__ void st_plain(uint4* p, const uint4& v) {
-  asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z),
-               "r"(v.w)
-               : "memory");
-}
-
 __device__ __forceinline__ int find_range(const CopyArgs& a, uint32_t t) {
   int r = 0;
   while (r + 1 < (int)a.nranges && t >= a.tile_start[r + 1]) ++r;
   return r;
 }
 
-// Head (bytes before the aligned body) and tail (bytes after it) of a coaligned range;
+// Head (bytes before the destination-aligned body) and tail (bytes after it) of a range;
 // threads 0..15 copy the head, threads 32..47 the tail.
 __device__ __forceinline__ void copy_edges(const uint8_t* s, uint8_t* o, const RangeDesc& d,
                                            uint64_t body_bytes) {
@@ -76,7 +55,7 @@ __device__ __forceinline__ void copy_edges(const uint8_t* s, uint8_t* o, const R
   if (tid >= 32 && tid < 32 + tail) o[tail_start + (tid - 32)] = s[tail_start + (tid - 32)];
 }
 
-template <bool kHostLink>
+template <bool kHostLink, bool kAny>
 __device__ __forceinline__ void copy_tiles_vec(const CopyArgs& a) {
   const uint32_t tid = threadIdx.x;
   for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
@@ -85,12 +64,12 @@ __device__ __forceinline__ void copy_tiles_vec(const CopyArgs& a) {
     const RangeDesc d = a.r[r];
     const uint8_t* s = a.src + d.src_off;
     uint8_t* o = a.dst + d.dst_off;
-    if (d.coaligned) {
-      const uint64_t nvec = (d.bytes - d.head) >> 4;
-      if (lt == 0) copy_edges(s, o, d, nvec << 4);
+    const uint64_t nvec = (d.bytes - d.head) >> 4;
+    if (lt == 0) copy_edges(s, o, d, nvec << 4);
+    uint4* ov = reinterpret_cast<uint4*>(o + d.head);
+    const uint64_t v0 = (uint64_t)lt * kVecTileVecs + tid;
+    if (!kAny || d.shift == 0) {
       const uint4* sv = reinterpret_cast<const uint4*>(s + d.head);
-      uint4* ov = reinterpret_cast<uint4*>(o + d.head);
-      const uint64_t v0 = (uint64_t)lt * kVecTileVecs + tid;
       uint4 buf[kVecUnroll];
 #pragma unroll
       for (int u = 0; u < kVecUnroll; ++u) {
@@ -103,9 +82,26 @@ __device__ __forceinline__ void copy_tiles_vec(const CopyArgs& a) {
         if (i < nvec) st_plain(ov + i, buf[u]);
       }
     } else {
-      const uint64_t b0 = (uint64_t)lt * kByteTile;
-      const uint64_t b1 = b0 + kByteTile < d.bytes ? b0 + kByteTile : d.bytes;
-      for (uint64_t i = b0 + tid; i < b1; i += blockDim.x) o[i] = s[i];
+      // source and destination differ modulo 16: two aligned source words per output word
+      const uint4* sw = reinterpret_cast<const uint4*>(s + d.head - d.shift);
+      const uint32_t k = d.shift >> 2, r = (d.shift & 3u) * 8u;
+#pragma unroll
+      for (int half = 0; half < kVecUnroll; half += kVecUnroll / 2) {
+        uint4 w0[kVecUnroll / 2], w1[kVecUnroll / 2];
+#pragma unroll
+        for (int u = 0; u < kVecUnroll / 2; ++u) {
+          const uint64_t i = v0 + (uint64_t)(half + u) * kVecThreads;
+          if (i < nvec) {
+            w0[u] = kHostLink ? ld_plain(sw + i) : ld_stream(sw + i);
+            w1[u] = kHostLink ? ld_plain(sw + i + 1) : ld_stream(sw + i + 1);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kVecUnroll / 2; ++u) {
+          const uint64_t i = v0 + (uint64_t)(half + u) * kVecThreads;
+          if (i < nvec) st_plain(ov + i, shift16(w0[u], w1[u], k, r));
+        }
+      }
     }
   }
 }
@@ -188,9 +184,10 @@ __device__ __forceinline__ uint32_t bulk_piece(const CopyArgs& a, uint32_t t, co
 
 }  // namespace
 
-__global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec(CopyArgs a) { copy_tiles_vec<false>(a); }
-
-__global__ void __launch_bounds__(kVecThreads) k_zc_copy(CopyArgs a) { copy_tiles_vec<true>(a); }
+__global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec(CopyArgs a) { copy_tiles_vec<false, false>(a); }
+__global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec_any(CopyArgs a) { copy_tiles_vec<false, true>(a); }
+__global__ void __launch_bounds__(kVecThreads) k_zc_copy(CopyArgs a) { copy_tiles_vec<true, false>(a); }
+__global__ void __launch_bounds__(kVecThreads) k_zc_copy_any(CopyArgs a) { copy_tiles_vec<true, true>(a); }
 
 __global__ void __launch_bounds__(kBulkThreads, 1) k_sm_copy_bulk(CopyArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
@@ -294,17 +291,7 @@ __global__ void __launch_bounds__(kVecThreads) k_stage_consume(StageArgs a) {
     const uint64_t off = (uint64_t)lt * kTile;
     if (off < c.bytes) {
       const uint64_t n = c.bytes - off < kTile ? c.bytes - off : kTile;
-      const uint8_t* s = a.stage + c.stage_off + off;
-      uint8_t* o = a.dst + c.dst_off + off;
-      if (((reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(o)) & 15) == 0) {
-        const uint64_t nv = n >> 4;
-        const uint4* sv = reinterpret_cast<const uint4*>(s);
-        uint4* ov = reinterpret_cast<uint4*>(o);
-        for (uint64_t v = tid; v < nv; v += blockDim.x) ov[v] = __ldcg(sv + v);
-        for (uint64_t b = (nv << 4) + tid; b < n; b += blockDim.x) o[b] = __ldcg(s + b);
-      } else {
-        for (uint64_t b = tid; b < n; b += blockDim.x) o[b] = __ldcg(s + b);
-      }
+      cta_copy<false, true>(a.stage + c.stage_off + off, a.dst + c.dst_off + off, n);
     }
     __syncthreads();
     if (tid == 0) {
@@ -364,6 +351,7 @@ int make_copy_args(CopyArgs& a, const void* src, void* dst, const RangeDesc* ran
   a.dst = static_cast<uint8_t*>(dst);
   a.status = status;
   a.nranges = 0;
+  a.any_shift = 0;
   uint64_t tiles = 0;
   a.tile_start[0] = 0;
   for (int i = 0; i < n && i < kInlineRanges; ++i) {
@@ -371,18 +359,13 @@ int make_copy_args(CopyArgs& a, const void* src, void* dst, const RangeDesc* ran
     if (d.bytes == 0) continue;
     const uintptr_t s = reinterpret_cast<uintptr_t>(src) + d.src_off;
     const uintptr_t o = reinterpret_cast<uintptr_t>(dst) + d.dst_off;
-    d.coaligned = ((s ^ o) & 15) == 0 ? 1u : 0u;
-    d.head = d.coaligned ? (uint32_t)std::min<uint64_t>(d.bytes, (16 - (o & 15)) & 15) : 0u;
-    if (variant == 1 && !d.coaligned) return kArgsNeedVec;
-    uint64_t t;
+    d.head = (uint32_t)std::min<uint64_t>(d.bytes, (16 - (o & 15)) & 15);
+    d.shift = (uint32_t)((s + d.head) & 15);
+    if (variant == 1 && d.shift) return kArgsNeedVec;
+    if (d.shift) a.any_shift = 1;
     const uint64_t body = ((d.bytes - d.head) >> 4) << 4;
-    if (!d.coaligned) {
-      t = (d.bytes + kByteTile - 1) / kByteTile;
-    } else if (variant == 1) {
-      t = (body + kBulkStageBytes - 1) / kBulkStageBytes;
-    } else {
-      t = ((body >> 4) + kVecTileVecs - 1) / kVecTileVecs;
-    }
+    uint64_t t = variant == 1 ? (body + kBulkStageBytes - 1) / kBulkStageBytes
+                              : ((body >> 4) + kVecTileVecs - 1) / kVecTileVecs;
     if (t == 0) t = 1;  // a range too short for a body still needs its edge bytes copied
     a.r[a.nranges] = d;
     tiles += t;

@@ -59,8 +59,8 @@ struct BatchSlot {
   uint8_t* d_ctrl = nullptr;
   unsigned long long* d_times = nullptr;
   BatchArgs args{};
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraph_t graph[2] = {nullptr, nullptr};      // [0] k_batch, [1] k_batch_any
+  cudaGraphExec_t exec[2] = {nullptr, nullptr};
   cudaEvent_t done_ev = nullptr;
   uint32_t epoch = 0;
   bool held = false;
@@ -88,6 +88,7 @@ struct mpt_graph_s {
   uint64_t src_lo = 0, src_hi = 0, dst_lo = 0, dst_hi = 0;
   bool cached = false;
   std::list<mpt_graph_s*>::iterator lru_it;
+  mpt_plan_s* eager_plan = nullptr;  // set when prepared for direct issue instead of a graph
 };
 
 struct mpt_ctx_s {

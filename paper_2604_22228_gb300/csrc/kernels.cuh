@@ -12,25 +12,26 @@ constexpr int kInlineRanges = 16;     // ranges carried by value in one launch
 constexpr int kVecThreads = 512;      // vec128 kernel block size
 constexpr int kVecUnroll = 8;         // 16-byte vectors in flight per thread per tile
 constexpr uint64_t kVecTileVecs = (uint64_t)kVecThreads * kVecUnroll;  // 64 KiB tiles
-constexpr uint64_t kByteTile = 16384; // tile of the bytewise fallback
 constexpr int kBulkThreads = 128;     // bulk kernel block size (thread 0 drives the ring)
 constexpr int kBulkStages = 4;        // shared-memory ring depth
 constexpr uint32_t kBulkStageBytes = 48 * 1024;  // one cp.async.bulk per stage
 
 // One contiguous range to copy: src + src_off -> dst + dst_off, `bytes` long.
-// head: bytes before the 16-byte aligned body when src and dst agree modulo 16
-// (coaligned), else unused; the kernel copies such ranges bytewise.
+// head: bytes copied singly until the destination is 16-byte aligned; shift: the source
+// address modulo 16 after the head -- 0 when source and destination agree modulo 16, else
+// each 16-byte destination word is assembled from two aligned source words.
 struct RangeDesc {
   uint64_t src_off;
   uint64_t dst_off;
   uint64_t bytes;
   uint32_t head;
-  uint32_t coaligned;
+  uint32_t shift;
 };
 
 struct CopyArgs {
   const uint8_t* src;
   uint8_t* dst;
+  uint32_t any_shift;                    // some range has shift != 0: launch an *_any kernel
   uint32_t nranges;
   uint32_t ntiles;                       // sum of tiles over ranges
   uint32_t tile_start[kInlineRanges + 1];
@@ -40,14 +41,19 @@ struct CopyArgs {
 
 // Fill `a` for up to kInlineRanges ranges with the tiling of `variant` (0 vec128,
 // 1 bulk, 2 zero-copy).  Returns kArgsOk, kArgsNeedVec when a bulk launch must fall
-// back to vec128 (source and destination differ modulo 16), or kArgsTooLarge.
+// back to vec128 (source and destination differ modulo 16, which cp.async.bulk cannot
+// copy), or kArgsTooLarge.
 constexpr int kArgsOk = 0, kArgsNeedVec = 1, kArgsTooLarge = 2;
 int make_copy_args(CopyArgs& a, const void* src, void* dst, const RangeDesc* ranges, int n,
                    int variant, uint32_t* status);
 
+// *_any variants also copy ranges whose source and destination differ modulo 16
+// (RangeDesc.shift != 0); the plain ones are leaner and need every shift to be 0.
 __global__ void k_sm_copy_vec(CopyArgs a);
+__global__ void k_sm_copy_vec_any(CopyArgs a);
 __global__ void k_sm_copy_bulk(CopyArgs a);
 __global__ void k_zc_copy(CopyArgs a);
+__global__ void k_zc_copy_any(CopyArgs a);
 
 // ---- flag-chained stage consumer (host-to-device staged path) ----------------------
 // The copy engine fills stage chunk k and a memset node then sets ready[k] = 1.  The
@@ -75,7 +81,8 @@ struct StageArgs {
 __global__ void k_stage_consume(StageArgs a);
 
 // ---- batched transfers: persistent descriptor-table kernel --------------------------
-constexpr uint32_t kDescHostDst = 1;  // destination is host memory: publish with system fences
+constexpr uint32_t kDescHostDst = 1;   // destination is host memory: publish with system fences
+constexpr uint32_t kDescHostSide = 2;  // one side is host memory: coherent loads, no read-only path
 
 struct BatchHeader {
   uint32_t n;            // descriptors in this batch
@@ -102,7 +109,10 @@ struct BatchArgs {
   uint32_t* host_flags;          // device alias of page-locked flags, one per descriptor
 };
 
+// k_batch needs every descriptor's source and destination to agree modulo 16;
+// k_batch_any copies any alignment.
 __global__ void k_batch(BatchArgs a);
+__global__ void k_batch_any(BatchArgs a);
 
 // ---- digest (test utility) -------------------------------------------------------
 __global__ void k_hash(const uint8_t* p, uint64_t n, unsigned long long* out);

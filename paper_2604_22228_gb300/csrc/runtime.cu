@@ -62,6 +62,8 @@ namespace mpt {
 namespace {
 
 void graph_destroy_exec(mpt_graph_s* g) {
+  delete g->eager_plan;
+  g->eager_plan = nullptr;
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   g->exec = nullptr;
@@ -109,10 +111,10 @@ std::vector<RangeDesc> path_ranges(const mpt_plan_s* plan, uint32_t p) {
   return out;
 }
 
-void* kernel_fn(int variant) {
+void* kernel_fn(int variant, bool any_shift) {
   if (variant == 1) return reinterpret_cast<void*>(&k_sm_copy_bulk);
-  if (variant == 2) return reinterpret_cast<void*>(&k_zc_copy);
-  return reinterpret_cast<void*>(&k_sm_copy_vec);
+  if (variant == 2) return any_shift ? reinterpret_cast<void*>(&k_zc_copy_any) : reinterpret_cast<void*>(&k_zc_copy);
+  return any_shift ? reinterpret_cast<void*>(&k_sm_copy_vec_any) : reinterpret_cast<void*>(&k_sm_copy_vec);
 }
 
 // Build CopyArgs for up to kInlineRanges ranges; the bulk variant falls back to vec128
@@ -140,7 +142,7 @@ mpt_status add_copy_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndep
   CopyArgs args = a;
   void* params[] = {&args};
   cudaKernelNodeParams kp{};
-  kp.func = kernel_fn(variant);
+  kp.func = kernel_fn(variant, a.any_shift != 0);
   kp.gridDim = grid_for(a, ctas);
   kp.blockDim = dim3(block_for(variant));
   kp.sharedMemBytes = (unsigned)smem_for(variant);
@@ -151,7 +153,7 @@ mpt_status add_copy_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndep
 }
 
 mpt_status launch_copy(cudaStream_t s, int variant, const CopyArgs& a, uint32_t ctas) {
-  void* kfn = kernel_fn(variant);
+  void* kfn = kernel_fn(variant, a.any_shift != 0);
   CopyArgs args = a;
   void* params[] = {&args};
   CUDA_TRY(cudaLaunchKernel(kfn, grid_for(a, ctas), dim3(block_for(variant)), params, smem_for(variant), s));
@@ -448,6 +450,26 @@ mpt_status grow_dev(EagerLane& L, uint64_t bytes) {
 
 mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src, cudaStream_t user) {
   if (plan->nbytes == 0) return MPT_OK;
+  // One copy-engine or kernel path needs no fork and join: issue it on the caller's
+  // stream directly (the cheapest launch for short messages).
+  uint32_t nonempty = 0, only = 0;
+  for (uint32_t p = 0; p < plan->npaths; ++p)
+    if (plan->first_chunk[p + 1] > plan->first_chunk[p]) {
+      nonempty++;
+      only = p;
+    }
+  if (nonempty == 1 && plan->paths[only].kind != MPT_PATH_HS) {
+    if (plan->paths[only].kind == MPT_PATH_CE) {
+      for (uint32_t i = plan->first_chunk[only]; i < plan->first_chunk[only + 1]; ++i) {
+        const mpt_chunk& ch = plan->chunks[i];
+        CUDA_TRY(cudaMemcpyAsync(static_cast<uint8_t*>(dst) + ch.offset, static_cast<const uint8_t*>(src) + ch.offset,
+                                 ch.bytes, cudaMemcpyDefault, user));
+      }
+      return MPT_OK;
+    }
+    return for_each_copy(c, plan, only, src, dst,
+                         [&](int variant, const CopyArgs& a, uint32_t ctas) { return launch_copy(user, variant, a, ctas); });
+  }
   CUDA_TRY(cudaEventRecord(c->fork, user));
   uint8_t* d8 = static_cast<uint8_t*>(dst);
   const uint8_t* s8 = static_cast<const uint8_t*>(src);
@@ -710,9 +732,45 @@ mpt_status mpt_capture(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void* src,
   return MPT_OK;
 }
 
+mpt_status mpt_prepare(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void* src, uint32_t mode, mpt_graph_t* out) {
+  if (!c || !plan || !out) return fail(MPT_EINVAL, "mpt_prepare: NULL argument");
+  if (mode > MPT_PREPARE_AUTO) return fail(MPT_EINVAL, "mpt_prepare: unknown mode %u", mode);
+  *out = nullptr;
+  if (mode == MPT_PREPARE_AUTO) {
+    // graph or direct issue, whichever the tuner measured faster for this size bucket
+    // (Sec. 4.4: tuned separately for graph and non-graph execution)
+    const uint32_t b = size_bucket(plan->nbytes);
+    auto g = c->tuned.find(tune_key(plan->dir, 0, b));
+    auto e = c->tuned.find(tune_key(plan->dir, 1, b));
+    mode = (g != c->tuned.end() && e != c->tuned.end() && e->second.us < g->second.us) ? MPT_PREPARE_EAGER
+                                                                                       : MPT_PREPARE_GRAPH;
+  }
+  if (mode == MPT_PREPARE_GRAPH) return mpt_capture(c, plan, dst, src, out);
+  CUDA_TRY(cudaSetDevice(c->device));
+  if (plan->nbytes > 0) {
+    mpt_status st = check_pointers(c, plan->dir, dst, src);
+    if (st != MPT_OK) return st;
+  }
+  mpt_graph_s* g = new mpt_graph_s;
+  g->ctx = c;
+  g->key = GraphKey{(uint64_t)(uintptr_t)src, (uint64_t)(uintptr_t)dst, plan->nbytes, plan->dir, plan->hash};
+  set_range(g, plan->nbytes, dst, src);
+  g->eager_plan = new mpt_plan_s(*plan);
+  g->info.mode = 1;
+  g->refs = 1;
+  c->live.insert(g);
+  *out = g;
+  return MPT_OK;
+}
+
 mpt_status mpt_launch(mpt_graph_t g, void* stream) {
   if (!g) return fail(MPT_EINVAL, "mpt_launch: NULL graph");
   if (!g->ctx) return fail(MPT_EINVAL, "mpt_launch: the graph's context was destroyed");
+  if (g->eager_plan) {  // prepared for direct issue (mpt_prepare chose eager)
+    CUDA_TRY(cudaSetDevice(g->ctx->device));
+    return eager(g->ctx, g->eager_plan, reinterpret_cast<void*>(g->key.dst), reinterpret_cast<const void*>(g->key.src),
+                 static_cast<cudaStream_t>(stream));
+  }
   if (!g->exec) return MPT_OK;  // empty message: nothing to move
   CUDA_TRY(cudaGraphLaunch(g->exec, static_cast<cudaStream_t>(stream)));
   return MPT_OK;

@@ -332,11 +332,8 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
     CUDA_TRY(cudaHostAlloc(&c->tune_h, nbytes, cudaHostAllocMapped | cudaHostAllocPortable));
     c->tune_host_bytes = nbytes;
   }
-  if (!c->flush) {
-    st = ensure_dev(c->flush, c->flush_bytes, 256ull << 20);
-    if (st != MPT_OK) return st;
-    CUDA_TRY(cudaMemset(c->flush, 0, c->flush_bytes));
-  }
+  st = ensure_dev(c->flush, c->flush_bytes, 256ull << 20);
+  if (st != MPT_OK) return st;
   void* src = dir == MPT_H2D ? c->tune_h : c->tune_a;
   void* dst = dir == MPT_D2H ? c->tune_h : c->tune_b;
   cudaStream_t s = c->lane[MPT_MAX_PATHS - 1].s[0];
@@ -345,6 +342,8 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
   CUDA_TRY(cudaEventCreate(&e1));
   TuneEntry best;
   double best_us = 1e30;
+  const char* vv = std::getenv("MPT_TUNE_VERBOSE");
+  const bool verbose = vv && *vv && *vv != '0';
   for (const Candidate& k : candidates(c, dir, nbytes, mode)) {
     mpt_plan_t plan = nullptr;
     if (mpt_plan(nullptr, nbytes, dir, k.p, k.n, 16, MPT_LAYOUT_CONTIG, &plan) != MPT_OK) continue;
@@ -353,8 +352,9 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
     if (mode == 0) ok = build_private_graph(c, plan, dst, src, &g) == MPT_OK;
     std::vector<float> ts;
     for (uint32_t r = 0; ok && r < reps + 1; ++r) {
-      // read 256 MiB (twice the L2) so the run starts cold, with no dirty lines left behind
-      k_hash<<<4 * c->sms, 256, 0, s>>>(static_cast<const uint8_t*>(c->flush), c->flush_bytes, c->d_hash);
+      // write 256 MiB (twice the L2) first, on the timing stream: each run starts with a cold
+      // L2 full of dirty lines, as after the kernel that produced the data
+      cudaMemsetAsync(c->flush, r & 0xff, c->flush_bytes, s);
       cudaEventRecord(e0, s);
       if (mode == 0) ok = g.exec == nullptr || cudaGraphLaunch(g.exec, s) == cudaSuccess;
       else ok = run_eager(c, plan, dst, src, s) == MPT_OK;
@@ -372,6 +372,14 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
     }
     std::sort(ts.begin(), ts.end());
     const double us = 1e3 * ts[ts.size() / 2];
+    if (verbose) {
+      std::fprintf(stderr, "mpt_tune dir=%u mode=%u n=%llu us=%.2f min=%.2f max=%.2f paths=", dir, mode,
+                   (unsigned long long)nbytes, us, 1e3 * ts.front(), 1e3 * ts.back());
+      for (uint32_t p = 0; p < k.n; ++p)
+        std::fprintf(stderr, "[%u %u %llu %u %u]", k.p[p].kind, k.p[p].share, (unsigned long long)k.p[p].chunk_bytes,
+                     k.p[p].ctas, k.p[p].flags);
+      std::fprintf(stderr, "\n");
+    }
     if (us < best_us) {
       best_us = us;
       best = TuneEntry{};

@@ -139,6 +139,25 @@ def batch_workload(n: int = 4096, seed: int = SEED_BATCH, min_bytes: int = 256,
     return sizes, d2d, gaps
 
 
+def batch_layout(sizes, d2d, gaps, align: int = 16, host_name: str = "host", dev_name: str = "dev"):
+    """Pack the batched workload into arenas: transfer k sits ``gaps[k]`` bytes after the
+    previous transfer's end rounded up to ``align`` (16: offsets on 16-byte multiples, in
+    general not on larger boundaries), in the device source arena when ``d2d[k]`` else the
+    host one, and at the same rule in the destination arena.  Returns (items, arena_bytes)
+    with items (arena, src_offset, dst_offset, nbytes)."""
+    up = lambda x: (x + align - 1) // align * align
+    offs = {dev_name: 0, host_name: 0, "dst": 0}
+    items = []
+    for sz, is_d2d, gap in zip(sizes, d2d, gaps):
+        a = dev_name if is_d2d else host_name
+        offs[a] = up(offs[a]) + gap
+        offs["dst"] = up(offs["dst"]) + gap
+        items.append((a, offs[a], offs["dst"], sz))
+        offs[a] += sz
+        offs["dst"] += sz
+    return items, offs
+
+
 def serving_schedule(rate_per_s: float, duration_s: float, seed: int = SEED_SERVE,
                      median_bytes: int = 1 << 20, sigma: float = 1.5,
                      cap_bytes: int = 256 << 20, mix=(0.5, 0.25, 0.25), max_requests: int | None = None):

@@ -29,18 +29,10 @@ class Workload:
     30% host-to-device, 16-byte gaps) packed into a device source arena, a page-locked host
     source arena and a device destination arena."""
 
-    def __init__(self, n, seed, max_bytes, kind="bf16", d2h=False):
+    def __init__(self, n, seed, max_bytes, kind="bf16", d2h=False, align=16):
         import torch
         sizes, d2d, gaps = payload.batch_workload(n, seed, 256, max_bytes)
-        self.items = []
-        offs = {"dev": 0, "host": 0, "dst": 0}
-        for sz, is_d2d, gap in zip(sizes, d2d, gaps):
-            arena = "dev" if (is_d2d or d2h) else "host"
-            offs[arena] += gap
-            offs["dst"] += gap
-            self.items.append((arena, offs[arena], offs["dst"], sz))
-            offs[arena] += sz
-            offs["dst"] += sz
+        self.items, offs = payload.batch_layout(sizes, [x or d2h for x in d2d], gaps, align=align)
         self.src_np = {a: payload.fill(kind, seed + i + 1, max(16, offs[a] + 64)) for i, a in enumerate(("dev", "host"))}
         self.src = {"dev": torch.from_numpy(self.src_np["dev"]).cuda(),
                     "host": torch.from_numpy(self.src_np["host"]).pin_memory()}
@@ -64,10 +56,13 @@ class Workload:
         return self.dst.cpu().numpy() if not self.d2h else self.dst.numpy().copy()
 
 
+@pytest.mark.parametrize("align", [16, 1])
 @pytest.mark.parametrize("n,max_bytes", [(1, 4096), (37, 64 * 1024), (300, MiB), (1000, 4 * MiB)])
-def test_batch_matches_oracle(ctx, n, max_bytes):
+def test_batch_matches_oracle(ctx, n, max_bytes, align):
+    """align 16: offsets on 16-byte multiples (the aligned kernel); align 1: transfers packed
+    back to back, sources and destinations differing modulo 16 (the general kernel)."""
     import torch
-    w = Workload(n, payload.SEED_BATCH + n, max_bytes)
+    w = Workload(n, payload.SEED_BATCH + n, max_bytes, align=align)
     b = mpt.mpt_batch_submit(ctx, w.xfers, torch.cuda.current_stream())
     mpt.mpt_batch_wait(b)
     done, flags = mpt.mpt_batch_poll(b, n)
@@ -183,14 +178,7 @@ def test_batch_full_size_workload(ctx):
     import torch
     period = 64 * MiB
     sizes, d2d, gaps = payload.batch_workload(4096)
-    items, offs = [], {"dev": 0, "host": 0, "dst": 0}
-    for sz, is_d2d, gap in zip(sizes, d2d, gaps):
-        a = "dev" if is_d2d else "host"
-        offs[a] += gap
-        offs["dst"] += gap
-        items.append((a, offs[a], offs["dst"], sz))
-        offs[a] += sz
-        offs["dst"] += sz
+    items, offs = payload.batch_layout(sizes, d2d, gaps)
     base = payload.fill("bf16", payload.SEED_BATCH, period)
     base_t = torch.from_numpy(base)
 

@@ -283,3 +283,38 @@ def test_graph_rebind_in_place(specs, direction):
     mpt.mpt_plan_destroy(plan)
     assert mpt.mpt_ctx_status(ctx)[0] == mpt.MPT_OK
     mpt.mpt_ctx_destroy(ctx)
+
+
+def test_prepare_eager_and_auto_modes():
+    """mpt_prepare: direct issue (no graph, no fork/join for one path) and AUTO move the
+    message exactly like a graph."""
+    import torch
+    ctx = mpt.mpt_ctx_create(0)
+    n = 2 * MiB + 48
+    for specs in ([(P.SM, 65536, MiB)], [(P.CE, 65536, 512 * 1024)], [(P.CE, 32768, MiB), (P.SM, 32768, MiB)],
+                  [(P.HS, 65536, MiB)]):
+        plan = mpt.mpt_plan(ctx, n, P.D2D, specs)
+        for mode in (mpt.MPT_PREPARE_EAGER, mpt.MPT_PREPARE_AUTO, mpt.MPT_PREPARE_GRAPH):
+            src, dst = Buf(n, "dev", 3), Buf(n, "dev", 3)
+            data = seeded("u8", 11 + mode, n)
+            src.fill(data)
+            h = mpt.mpt_prepare(ctx, plan, dst.ptr, src.ptr, mode)
+            assert mpt.mpt_graph_get_info(h)["mode"] == (1 if mode == mpt.MPT_PREPARE_EAGER else 0)
+            mpt.mpt_launch(h, torch.cuda.current_stream())
+            mpt.mpt_launch(h, torch.cuda.current_stream())
+            assert np.array_equal(dst.numpy(), data) and dst.guards_intact()
+            mpt.mpt_graph_release(h)
+        mpt.mpt_plan_destroy(plan)
+    # AUTO follows the tuner: after tuning both modes the choice is the faster one
+    mpt.mpt_tune(ctx, P.D2D, 4096, mpt.MPT_MODE_GRAPH)
+    mpt.mpt_tune(ctx, P.D2D, 4096, mpt.MPT_MODE_EAGER)
+    g_us = mpt.mpt_tune_get(ctx, P.D2D, 4096, mpt.MPT_MODE_GRAPH)[1]
+    e_us = mpt.mpt_tune_get(ctx, P.D2D, 4096, mpt.MPT_MODE_EAGER)[1]
+    plan = mpt.mpt_plan(ctx, 4096, P.D2D, [(P.SM, 65536, 4096)])
+    src, dst = Buf(4096, "dev"), Buf(4096, "dev")
+    h = mpt.mpt_prepare(ctx, plan, dst.ptr, src.ptr, mpt.MPT_PREPARE_AUTO)
+    assert mpt.mpt_graph_get_info(h)["mode"] == (1 if e_us < g_us else 0)
+    mpt.mpt_graph_release(h)
+    mpt.mpt_plan_destroy(plan)
+    assert mpt.mpt_ctx_status(ctx)[0] == mpt.MPT_OK
+    mpt.mpt_ctx_destroy(ctx)

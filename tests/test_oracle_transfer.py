@@ -131,3 +131,13 @@ def test_serving_schedule_request_cap():
     assert len(payload.serving_schedule(1e6, 1e9, max_requests=25)) == 25
     capped = payload.serving_schedule(1000.0, 0.5, max_requests=10 ** 9)
     assert 400 < len(capped) < 600 and capped[-1][0] < 0.5
+
+
+def test_batch_layout_offsets():
+    sizes, d2d, gaps = [10, 33, 16], [True, False, True], [16, 32, 48]
+    items, offs = payload.batch_layout(sizes, d2d, gaps)
+    # dev: 0+16=16 (10 B, ends 26) -> up16(26)=32 +48 = 80; host: 0+32 = 32; dst: 16, up16(26)+32=64, up16(97)+48=160
+    assert items == [("dev", 16, 16, 10), ("host", 32, 64, 33), ("dev", 80, 160, 16)]
+    assert all(s % 16 == 0 and d % 16 == 0 for _, s, d, _ in items)
+    packed, _ = payload.batch_layout(sizes, d2d, gaps, align=1)
+    assert packed == [("dev", 16, 16, 10), ("host", 32, 58, 33), ("dev", 74, 139, 16)]
