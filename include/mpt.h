@@ -157,7 +157,9 @@ MPT_API const char* mpt_version(void);
 MPT_API const char* mpt_last_error(void);
 
 /* Create a context on `device` (makes it current).  tune_file: path of a tuner cache to
- * load (JSON written by mpt_tune_save), or NULL.  Sec. 4.2 "Base Module": probes the
+ * load (JSON written by mpt_tune_save), or NULL for $MPT_TUNE_FILE, else the offline-tuned
+ * defaults shipped next to the library as tuned/<device name>.jsonl when they exist
+ * (MPT_TUNE_DEFAULTS=0 skips them).  Sec. 4.2 "Base Module": probes the
  * device and creates streams, events and the status word.  Errors: EINVAL (bad device),
  * ECUDA, ENOMEM. */
 MPT_API mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out);

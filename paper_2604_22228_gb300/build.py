@@ -50,7 +50,7 @@ def build(force: bool = False) -> str:
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(nvcc, s), SOURCES))
     tmp = OUT + ".tmp"
-    cmd = [nvcc, ARCH, "-shared", "-o", tmp] + objs
+    cmd = [nvcc, ARCH, "-shared", "-o", tmp] + objs + ["-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

@@ -2,7 +2,10 @@
 // LRU cache (Sec. 4.2), graph construction per path kind (Algorithms 1 and 2), the eager
 // runtime pipelining engine (Sec. 4.3), and the C ABI entry points of mpt.h that need
 // the GPU.
+#include <dlfcn.h>
+
 #include <algorithm>
+#include <cctype>
 #include <chrono>
 #include <cstdlib>
 #include <cstring>
@@ -625,6 +628,25 @@ mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out) {
   if (tf && *tf) {
     mpt_status st = mpt_tune_load(c, tf);
     if (st != MPT_OK) return bail(st);
+  } else if (env_u64("MPT_TUNE_DEFAULTS", 1) != 0) {
+    // offline-tuned defaults for this device model, shipped next to the library as
+    // tuned/<device name>.jsonl (Sec. 4.4: tuned values are the defaults)
+    cudaDeviceProp prop;
+    Dl_info info;
+    if (cudaGetDeviceProperties(&prop, device) == cudaSuccess &&
+        dladdr(reinterpret_cast<void*>(&mpt_ctx_create), &info) && info.dli_fname) {
+      std::string dir(info.dli_fname);
+      dir = dir.substr(0, dir.find_last_of('/') + 1);
+      std::string name(prop.name);
+      for (char& ch : name)
+        if (!std::isalnum((unsigned char)ch)) ch = '_';
+      const std::string path = dir + "tuned/" + name + ".jsonl";
+      if (FILE* f = std::fopen(path.c_str(), "r")) {
+        std::fclose(f);
+        mpt_status st = mpt_tune_load(c, path.c_str());
+        if (st != MPT_OK) return bail(st);
+      }
+    }
   }
   *out = c;
   return MPT_OK;

@@ -426,6 +426,7 @@ mpt_status mpt_tune_load(mpt_ctx_t c, const char* path) {
   uint32_t lineno = 0;
   while (std::fgets(line, sizeof line, f)) {
     ++lineno;
+    if (line[0] == '#') continue;  // comment lines (e.g. the device the table was tuned on)
     double v[5 + 5 * 4];
     int n = 0;
     for (char* p = line; *p && n < (int)(sizeof v / sizeof v[0]);) {

@@ -285,10 +285,11 @@ def test_graph_rebind_in_place(specs, direction):
     mpt.mpt_ctx_destroy(ctx)
 
 
-def test_prepare_eager_and_auto_modes():
+def test_prepare_eager_and_auto_modes(monkeypatch):
     """mpt_prepare: direct issue (no graph, no fork/join for one path) and AUTO move the
     message exactly like a graph."""
     import torch
+    monkeypatch.setenv("MPT_TUNE_DEFAULTS", "0")  # empty tuner table: AUTO falls back to a graph
     ctx = mpt.mpt_ctx_create(0)
     n = 2 * MiB + 48
     for specs in ([(P.SM, 65536, MiB)], [(P.CE, 65536, 512 * 1024)], [(P.CE, 32768, MiB), (P.SM, 32768, MiB)],

@@ -64,6 +64,7 @@ def test_tuner_needs_context_without_env(monkeypatch):
 def test_tune_persist_and_use(tmp_path, monkeypatch):
     import torch
     monkeypatch.delenv("MPT_PATHS", raising=False)
+    monkeypatch.setenv("MPT_TUNE_DEFAULTS", "0")  # start from an empty table
     ctx = mpt.mpt_ctx_create(0)
     try:
         results = {}
@@ -121,5 +122,33 @@ def test_model_fallback_plans_are_valid(monkeypatch):
                 chunks = [P.Chunk(*c) for c in mpt.mpt_plan_chunks(h)]
                 assert chunks == P.plan(n, d, paths)
                 mpt.mpt_plan_destroy(h)
+    finally:
+        mpt.mpt_ctx_destroy(ctx)
+
+
+@pytest.mark.gpu
+def test_shipped_defaults_load(monkeypatch):
+    """The offline-tuned table for this device model (tuned/<device>.jsonl next to the
+    library) is loaded by a new context, and every entry in it is a valid path set."""
+    import os
+    import re
+
+    import torch
+    name = re.sub(r"[^0-9A-Za-z]", "_", torch.cuda.get_device_name(0))
+    path = os.path.join(os.path.dirname(mpt._ffi.LIB_PATH), "tuned", name + ".jsonl")
+    if not os.path.exists(path):
+        pytest.skip(f"no shipped table for {name}")
+    monkeypatch.delenv("MPT_TUNE_FILE", raising=False)
+    ctx = mpt.mpt_ctx_create(0)
+    try:
+        paths, us = mpt.mpt_tune_get(ctx, P.D2D, 1 << 30, mpt.MPT_MODE_GRAPH)
+        assert paths and us > 0
+    finally:
+        mpt.mpt_ctx_destroy(ctx)
+    monkeypatch.setenv("MPT_TUNE_DEFAULTS", "0")
+    ctx = mpt.mpt_ctx_create(0)
+    try:
+        with pytest.raises(mpt.MptError):
+            mpt.mpt_tune_get(ctx, P.D2D, 1 << 30, mpt.MPT_MODE_GRAPH)
     finally:
         mpt.mpt_ctx_destroy(ctx)
