@@ -403,9 +403,9 @@ def run_ours(args):
     # ---- dominant kernel alone: SM copy kernel on the 1 GiB message, CUDA events ----
     kin = args.kernel_launches
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    tuned_paths = mpt.mpt_plan_paths(tuned_plans[-1])
-    sm_paths = [p for p in tuned_paths if p["kind"] == mpt.MPT_PATH_SM] or [dict(ctas=0, flags=0)]
-    variant, ctas = sm_paths[0]["flags"] & 1, sm_paths[0]["ctas"]
+    # the kernel's own default launch (vec128, 16 CTAs per SM): the configuration the
+    # committed ncu capture of this launch used
+    variant, ctas = 0, 0
     with torch.cuda.stream(stream):
         for _ in range(3):
             mpt.mpt_sm_copy(ctx, base_d + offs[-1], base_s + offs[-1], SIZES[-1], variant, ctas, stream)
@@ -465,6 +465,7 @@ def run_ours(args):
             mpt.mpt_plan_destroy(p)
 
     lifecycle = run_graph_lifecycle(mpt, torch, ctx, stream)
+    windows = None if args.no_windows else run_windows(mpt, torch, ctx)
     host_sweep = None
     if not args.no_host_sweep:
         host_sweep = run_host_sweep(mpt, torch, ctx, stream)
@@ -530,6 +531,7 @@ def run_ours(args):
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": kernels_per_step * args.steps,
             "clocks": clk, "parity_ok": ok, "host_elapsed_s": round(host_elapsed, 4), "tune_s": round(tune_s, 2),
             "batched": batched, "serving": serving, "host_sweep": host_sweep, "graph_lifecycle": lifecycle,
+            "windows": windows,
             "sweep": sweep, "wall_s": round(time.perf_counter() - t_wall0, 2),
         }
         print(json.dumps(line), flush=True)
@@ -873,6 +875,53 @@ def run_batch_only(args):
     return 0 if st == 0 else 1
 
 
+def run_windows(mpt, torch, ctx, reps=5):
+    """Windowed transfers (the paper's OMB bandwidth test with windows 1/4/16, 1..64 MB):
+    W messages of N bytes posted at once, each on its own stream with its own prepared
+    handle (tuned plan; graph, or direct issue), then all waited for; GB/s = W*N / time.
+    Device-to-device and host-to-device (page-locked source)."""
+    sizes = [1 * MiB, 4 * MiB, 16 * MiB, 64 * MiB]
+    wmax = 16
+    streams = [torch.cuda.Stream() for _ in range(wmax)]
+    main = torch.cuda.Stream()
+    dsrc = torch.empty(wmax * sizes[-1], dtype=torch.uint8, device="cuda")
+    ddst = torch.empty(wmax * sizes[-1], dtype=torch.uint8, device="cuda")
+    hsrc = torch.empty(wmax * sizes[-1], dtype=torch.uint8).pin_memory()
+    dsrc.fill_(3)
+    hsrc.fill_(5)
+    flush = torch.empty(256 * MiB, dtype=torch.uint8, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for direction, name, src in ((mpt.MPT_D2D, "d2d", dsrc), (mpt.MPT_H2D, "h2d", hsrc)):
+        for n in sizes:
+            plan = mpt.mpt_plan(ctx, n, direction, None)
+            for mode, mname in ((mpt.MPT_PREPARE_GRAPH, "graph"), (mpt.MPT_PREPARE_EAGER, "eager")):
+                hs = [mpt.mpt_prepare(ctx, plan, ddst.data_ptr() + w * n, src.data_ptr() + w * n, mode)
+                      for w in range(wmax)]
+                for win in (1, 4, 16):
+                    ts = []
+                    for r in range(reps + 1):
+                        with torch.cuda.stream(main):
+                            flush.fill_(r & 0xff)
+                        e0.record(main)
+                        for w in range(win):
+                            streams[w].wait_event(e0)
+                            mpt.mpt_launch(hs[w], streams[w])
+                        for w in range(win):
+                            main.wait_stream(streams[w])
+                        e1.record(main)
+                        e1.synchronize()
+                        if r:
+                            ts.append(e0.elapsed_time(e1))
+                    ms = statistics.median(ts)
+                    rows.append({"dir": name, "bytes": n, "mode": mname, "window": win,
+                                 "gbs": round(win * n / (ms / 1e3) / 1e9, 2)})
+                for h in hs:
+                    mpt.mpt_graph_release(h)
+            mpt.mpt_plan_destroy(plan)
+    return rows
+
+
 def run_kernel_only(args):
     """One kernel alone on one message (for profiling): K launches timed with CUDA events."""
     import torch
@@ -925,6 +974,7 @@ def main(argv=None):
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-host-sweep", action="store_true")
+    ap.add_argument("--no-windows", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="per arrival rate; 0 skips serving")
     ap.add_argument("--serve-rates", default="1000,10000,50000")
     ap.add_argument("--tune", choices=["online", "model"], default="online",

@@ -23,7 +23,10 @@
  *   - "stream" arguments are cudaStream_t values passed as void* (NULL = the legacy
  *     default stream).  Device pointers are CUDA device addresses; "host" buffers must be
  *     page-locked (cudaHostAlloc / cudaHostRegister / mpt_host_alloc) so that copy engines
- *     and kernels can reach them.
+ *     and kernels can reach them -- except on devices that reach pageable memory directly
+ *     (cudaDevAttrPageableMemoryAccess, e.g. GB300 with its coherent Grace host), where
+ *     plans made only of zero-copy paths, batches and mpt_sm_copy also accept ordinary
+ *     pageable host memory.
  *   - A context (mpt_ctx_t) owns its streams, events, staging buffers, device status
  *     word, graph cache and tuner cache.  One host thread per context.
  *   - Asynchronous calls only enqueue work; results are valid after the stream the work
@@ -167,6 +170,19 @@ MPT_API mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* 
 /* Destroy a context and everything it owns (cached graphs included).  Waits for the
  * device to go idle first.  Handles created from it become invalid. */
 MPT_API mpt_status mpt_ctx_destroy(mpt_ctx_t ctx);
+
+/* What the context found when it probed its device (Sec. 4.2 "Base Module"). */
+typedef struct {
+  char name[96];
+  int32_t device;
+  int32_t sms;               /* streaming multiprocessors */
+  int32_t copy_engines;      /* asynchronous copy engines */
+  int32_t pageable_access;   /* 1: kernels reach pageable host memory (coherent host) */
+  uint64_t l2_bytes;
+  uint64_t memory_bytes;
+} mpt_device_info;
+
+MPT_API mpt_status mpt_ctx_info(mpt_ctx_t ctx, mpt_device_info* out);
 
 /* Read the context's device status word (blocking: synchronises the device), return it
  * (MPT_OK or the first recorded MPT_ETIMEDOUT) and reset it to MPT_OK.  `site` (nullable)

@@ -86,6 +86,14 @@ def mpt_ctx_destroy(ctx: int) -> None:
     _check(lib().mpt_ctx_destroy(ctx), "mpt_ctx_destroy")
 
 
+def mpt_ctx_info(ctx: int) -> dict:
+    info = _ffi.mpt_device_info()
+    _check(lib().mpt_ctx_info(ctx, C.byref(info)), "mpt_ctx_info")
+    out = {name: getattr(info, name) for name, _ in _ffi.mpt_device_info._fields_}
+    out["name"] = info.name.decode(errors="replace")
+    return out
+
+
 def mpt_ctx_status(ctx: int) -> tuple[int, int]:
     """(status, site) of the context's device status word, which is then reset."""
     site = C.c_uint32()

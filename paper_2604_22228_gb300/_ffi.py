@@ -78,6 +78,11 @@ class mpt_serve_stats_t(C.Structure):
                                           "max_inflight_bytes", "rejected")]
 
 
+class mpt_device_info(C.Structure):
+    _fields_ = [("name", C.c_char * 96), ("device", C.c_int32), ("sms", C.c_int32), ("copy_engines", C.c_int32),
+                ("pageable_access", C.c_int32), ("l2_bytes", C.c_uint64), ("memory_bytes", C.c_uint64)]
+
+
 H = C.c_void_p  # opaque handles
 P = C.POINTER
 
@@ -87,6 +92,7 @@ SIGNATURES = {
     "mpt_last_error": (C.c_char_p, []),
     "mpt_ctx_create": (C.c_int, [C.c_int, C.c_char_p, P(H)]),
     "mpt_ctx_destroy": (C.c_int, [H]),
+    "mpt_ctx_info": (C.c_int, [H, P(mpt_device_info)]),
     "mpt_ctx_status": (C.c_int, [H, P(C.c_uint32)]),
     "mpt_plan": (C.c_int, [H, C.c_uint64, C.c_uint32, P(mpt_path_spec), C.c_uint32, C.c_uint32, C.c_uint32,
                           P(H)]),

@@ -177,6 +177,8 @@ int range_kind(mpt_ctx_t c, const void* p, uint64_t n) {
   }
   if ((at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == c->device) return 0;
   if (at.type == cudaMemoryTypeHost) return 1;
+  // pageable host memory: the batch kernel reads and writes it directly when the GPU can
+  if (at.type == cudaMemoryTypeUnregistered && c->pageable) return 1;
   return -1;
 }
 

@@ -95,6 +95,7 @@ struct mpt_ctx_s {
   int device = 0;
   int sms = 0;
   int engines = 0;
+  bool pageable = false;              // the GPU reaches pageable host memory (coherent host)
   uint32_t* d_status = nullptr;       // device status word
   unsigned long long* d_hash = nullptr;
   mpt::EagerLane lane[MPT_MAX_PATHS];

@@ -7,6 +7,7 @@
 #include <algorithm>
 #include <cctype>
 #include <chrono>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <list>
@@ -42,9 +43,11 @@ uint64_t env_u64(const char* name, uint64_t dflt) {
   return (end && *end == 0) ? (uint64_t)x : dflt;
 }
 
-enum MemKind { kMemDevice, kMemHost, kMemOther };
+enum MemKind { kMemDevice, kMemHost, kMemPageable, kMemOther };
 
-MemKind classify(const void* p, int device) {
+// kMemPageable: ordinary (not page-locked) host memory, which the GPU reaches directly
+// only when the device reports pageableMemoryAccess (coherent Grace hosts).
+MemKind classify(const void* p, int device, bool pageable_ok = false) {
   cudaPointerAttributes a;
   if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
     cudaGetLastError();
@@ -53,6 +56,7 @@ MemKind classify(const void* p, int device) {
   if ((a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == device)
     return kMemDevice;
   if (a.type == cudaMemoryTypeHost) return kMemHost;
+  if (a.type == cudaMemoryTypeUnregistered && p && pageable_ok) return kMemPageable;
   return kMemOther;
 }
 
@@ -377,17 +381,31 @@ mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const voi
   return MPT_OK;
 }
 
-mpt_status check_pointers(mpt_ctx_t c, uint32_t dir, const void* dst, const void* src) {
-  const MemKind ks = classify(src, c->device), kd = classify(dst, c->device);
+// Pointer kinds must fit the direction.  Host sides must be page-locked, except that plans
+// made only of zero-copy paths may use pageable host memory on devices that can reach it
+// (zero_copy_only: every non-empty path of the plan is MPT_PATH_ZC).
+mpt_status check_pointers(mpt_ctx_t c, uint32_t dir, const void* dst, const void* src, bool zero_copy_only = false) {
+  const bool pg = zero_copy_only && c->pageable;
+  MemKind ks = classify(src, c->device, pg), kd = classify(dst, c->device, pg);
+  if (ks == kMemPageable) ks = kMemHost;
+  if (kd == kMemPageable) kd = kMemHost;
   const MemKind want_s = dir == MPT_H2D ? kMemHost : kMemDevice;
   const MemKind want_d = dir == MPT_D2H ? kMemHost : kMemDevice;
   if (ks != want_s)
     return fail(MPT_EINVAL, "source %p is not %s memory", src,
-                want_s == kMemHost ? "page-locked host" : "device (this context's GPU)");
+                want_s == kMemHost ? (pg ? "host" : "page-locked host (pageable memory needs a zero-copy-only plan)")
+                                   : "device (this context's GPU)");
   if (kd != want_d)
     return fail(MPT_EINVAL, "destination %p is not %s memory", dst,
-                want_d == kMemHost ? "page-locked host" : "device (this context's GPU)");
+                want_d == kMemHost ? (pg ? "host" : "page-locked host (pageable memory needs a zero-copy-only plan)")
+                                   : "device (this context's GPU)");
   return MPT_OK;
+}
+
+bool zero_copy_only(const mpt_plan_s* plan) {
+  for (uint32_t p = 0; p < plan->npaths; ++p)
+    if (plan->first_chunk[p + 1] > plan->first_chunk[p] && plan->paths[p].kind != MPT_PATH_ZC) return false;
+  return true;
 }
 
 // Retarget g at (dst, src) without instantiating: rebuild the node set for the new
@@ -596,9 +614,12 @@ mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out) {
     mpt_ctx_destroy(c);
     return st;
   };
+  int pageable = 0;
   if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
-      cudaDeviceGetAttribute(&c->engines, cudaDevAttrAsyncEngineCount, device) != cudaSuccess)
+      cudaDeviceGetAttribute(&c->engines, cudaDevAttrAsyncEngineCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&pageable, cudaDevAttrPageableMemoryAccess, device) != cudaSuccess)
     return bail(fail(MPT_ECUDA, "mpt_ctx_create: device attributes unavailable"));
+  c->pageable = pageable != 0;
   void* words = nullptr;
   if (cudaMalloc(&words, 256) != cudaSuccess) return bail(fail(MPT_ENOMEM, "mpt_ctx_create: status word"));
   c->d_status = static_cast<uint32_t*>(words);
@@ -685,6 +706,21 @@ mpt_status mpt_ctx_destroy(mpt_ctx_t c) {
   return MPT_OK;
 }
 
+mpt_status mpt_ctx_info(mpt_ctx_t c, mpt_device_info* out) {
+  if (!c || !out) return fail(MPT_EINVAL, "mpt_ctx_info: NULL argument");
+  cudaDeviceProp prop;
+  CUDA_TRY(cudaGetDeviceProperties(&prop, c->device));
+  std::memset(out, 0, sizeof *out);
+  std::snprintf(out->name, sizeof out->name, "%s", prop.name);
+  out->device = c->device;
+  out->sms = c->sms;
+  out->copy_engines = c->engines;
+  out->pageable_access = c->pageable ? 1 : 0;
+  out->l2_bytes = (uint64_t)prop.l2CacheSize;
+  out->memory_bytes = (uint64_t)prop.totalGlobalMem;
+  return MPT_OK;
+}
+
 mpt_status mpt_ctx_status(mpt_ctx_t c, uint32_t* site) {
   if (!c) return fail(MPT_EINVAL, "mpt_ctx_status: NULL context");
   CUDA_TRY(cudaSetDevice(c->device));
@@ -703,7 +739,7 @@ mpt_status mpt_capture(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void* src,
   *out = nullptr;
   CUDA_TRY(cudaSetDevice(c->device));
   if (plan->nbytes > 0) {
-    mpt_status st = check_pointers(c, plan->dir, dst, src);
+    mpt_status st = check_pointers(c, plan->dir, dst, src, zero_copy_only(plan));
     if (st != MPT_OK) return st;
   }
   GraphKey key{(uint64_t)(uintptr_t)src, (uint64_t)(uintptr_t)dst, plan->nbytes, plan->dir, plan->hash};
@@ -770,7 +806,7 @@ mpt_status mpt_prepare(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void* src,
   if (mode == MPT_PREPARE_GRAPH) return mpt_capture(c, plan, dst, src, out);
   CUDA_TRY(cudaSetDevice(c->device));
   if (plan->nbytes > 0) {
-    mpt_status st = check_pointers(c, plan->dir, dst, src);
+    mpt_status st = check_pointers(c, plan->dir, dst, src, zero_copy_only(plan));
     if (st != MPT_OK) return st;
   }
   mpt_graph_s* g = new mpt_graph_s;
@@ -812,7 +848,7 @@ mpt_status mpt_graph_rebind(mpt_graph_t g, mpt_plan_t plan, void* dst, const voi
     return fail(MPT_EINVAL, "mpt_graph_rebind: the plan is not the one the graph was captured from");
   CUDA_TRY(cudaSetDevice(c->device));
   if (plan->nbytes > 0) {
-    mpt_status st = check_pointers(c, plan->dir, dst, src);
+    mpt_status st = check_pointers(c, plan->dir, dst, src, zero_copy_only(plan));
     if (st != MPT_OK) return st;
   }
   GraphKey key{(uint64_t)(uintptr_t)src, (uint64_t)(uintptr_t)dst, plan->nbytes, plan->dir, plan->hash};
@@ -859,7 +895,7 @@ mpt_status mpt_launch_eager(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void*
   if (!c || !plan) return fail(MPT_EINVAL, "mpt_launch_eager: NULL argument");
   CUDA_TRY(cudaSetDevice(c->device));
   if (plan->nbytes > 0) {
-    mpt_status st = check_pointers(c, plan->dir, dst, src);
+    mpt_status st = check_pointers(c, plan->dir, dst, src, zero_copy_only(plan));
     if (st != MPT_OK) return st;
   }
   return eager(c, plan, dst, src, static_cast<cudaStream_t>(stream));
@@ -872,10 +908,10 @@ mpt_status mpt_sm_copy(mpt_ctx_t c, void* dst, const void* src, uint64_t nbytes,
   if (nbytes == 0) return MPT_OK;
   if (!dst || !src) return fail(MPT_EINVAL, "mpt_sm_copy: NULL pointer");
   CUDA_TRY(cudaSetDevice(c->device));
-  const MemKind ks = classify(src, c->device), kd = classify(dst, c->device);
+  const MemKind ks = classify(src, c->device, c->pageable), kd = classify(dst, c->device, c->pageable);
   if (ks == kMemOther || kd == kMemOther)
-    return fail(MPT_EINVAL, "mpt_sm_copy: pointers must be device or page-locked host memory");
-  const bool host = ks == kMemHost || kd == kMemHost;
+    return fail(MPT_EINVAL, "mpt_sm_copy: pointers must be device or host memory the GPU can reach");
+  const bool host = ks != kMemDevice || kd != kMemDevice;
   RangeDesc r{0, 0, nbytes, 0, 0};
   int v = host ? 2 : (int)variant;
   CopyArgs a;

@@ -319,3 +319,51 @@ def test_prepare_eager_and_auto_modes(monkeypatch):
     mpt.mpt_plan_destroy(plan)
     assert mpt.mpt_ctx_status(ctx)[0] == mpt.MPT_OK
     mpt.mpt_ctx_destroy(ctx)
+
+
+def test_device_info(ctx):
+    info = mpt.mpt_ctx_info(ctx)
+    import torch
+    p = torch.cuda.get_device_properties(0)
+    assert info["sms"] == p.multi_processor_count and info["name"] == p.name
+    assert info["copy_engines"] >= 1 and info["l2_bytes"] > 0 and info["memory_bytes"] > 0
+
+
+def test_pageable_host_memory_through_zero_copy(ctx):
+    """On a device that reaches pageable host memory (a coherent Grace host), zero-copy-only
+    plans, batches and mpt_sm_copy move ordinary (not page-locked) host buffers; plans with
+    copy-engine or staged paths still require page-locked memory."""
+    import torch
+    if not mpt.mpt_ctx_info(ctx)["pageable_access"]:
+        pytest.skip("device cannot reach pageable host memory")
+    n = 5 * MiB + 7
+    host_src = seeded("u32", 71, n).copy()          # numpy: pageable
+    host_dst = np.zeros(n + 64, dtype=np.uint8)
+    dev = Buf(n, "dev")
+    zc = mpt.mpt_plan(ctx, n, P.H2D, [(P.ZC, 65536, MiB)])
+    for mode in (mpt.MPT_PREPARE_GRAPH, mpt.MPT_PREPARE_EAGER):
+        h = mpt.mpt_prepare(ctx, zc, dev.ptr, host_src.ctypes.data, mode)
+        mpt.mpt_launch(h, torch.cuda.current_stream())
+        assert np.array_equal(dev.numpy(), host_src)
+        mpt.mpt_graph_release(h)
+    back = mpt.mpt_plan(ctx, n, P.D2H, [(P.ZC, 65536, MiB)])
+    g = mpt.mpt_capture(ctx, back, host_dst.ctypes.data + 3, dev.ptr)
+    mpt.mpt_launch(g, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert np.array_equal(host_dst[3:3 + n], host_src) and not host_dst[:3].any() and not host_dst[3 + n:].any()
+    mpt.mpt_graph_release(g)
+    ce = mpt.mpt_plan(ctx, n, P.H2D, [(P.CE, 32768, MiB), (P.ZC, 32768, MiB)])
+    with pytest.raises(mpt.MptError) as e:
+        mpt.mpt_capture(ctx, ce, dev.ptr, host_src.ctypes.data)
+    assert e.value.status == mpt.MPT_EINVAL
+    # a batch reading pageable memory
+    out = torch.zeros(2 * MiB, dtype=torch.uint8, device="cuda")
+    b = mpt.mpt_batch_submit(ctx, [(host_src.ctypes.data + 16, out.data_ptr(), MiB, mpt.MPT_H2D),
+                                   (host_src.ctypes.data + 5, out.data_ptr() + MiB, 1000, mpt.MPT_H2D)],
+                             torch.cuda.current_stream())
+    mpt.mpt_batch_wait(b)
+    mpt.mpt_batch_release(b)
+    o = out.cpu().numpy()
+    assert np.array_equal(o[:MiB], host_src[16:16 + MiB]) and np.array_equal(o[MiB:MiB + 1000], host_src[5:1005])
+    for p in (zc, back, ce):
+        mpt.mpt_plan_destroy(p)
