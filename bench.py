@@ -466,6 +466,7 @@ def run_ours(args):
 
     lifecycle = run_graph_lifecycle(mpt, torch, ctx, stream)
     windows = None if args.no_windows else run_windows(mpt, torch, ctx)
+    jacobi = None if args.no_jacobi else run_jacobi(mpt, torch, ctx)
     host_sweep = None
     if not args.no_host_sweep:
         host_sweep = run_host_sweep(mpt, torch, ctx, stream)
@@ -531,7 +532,7 @@ def run_ours(args):
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": kernels_per_step * args.steps,
             "clocks": clk, "parity_ok": ok, "host_elapsed_s": round(host_elapsed, 4), "tune_s": round(tune_s, 2),
             "batched": batched, "serving": serving, "host_sweep": host_sweep, "graph_lifecycle": lifecycle,
-            "windows": windows,
+            "windows": windows, "jacobi": jacobi,
             "sweep": sweep, "wall_s": round(time.perf_counter() - t_wall0, 2),
         }
         print(json.dumps(line), flush=True)
@@ -922,6 +923,94 @@ def run_windows(mpt, torch, ctx, reps=5):
     return rows
 
 
+def run_jacobi(mpt, torch, ctx, iters=20):
+    """Compute plus communication (the paper's Jacobi study, Sec. 5.4, on one GPU): 4
+    subdomains of 8 rows x W fp32 columns in a ring; each iteration one Jacobi sweep per
+    subdomain, then 8 halo-row exchanges (W*4 bytes each).  Per halo size: single-path halos
+    (copy engine only, the single-path baseline), tuned multi-path halos issued directly,
+    tuned multi-path halos as transfer graphs (the paper's setup: only transfers in graphs),
+    and one captured graph holding the sweeps and the halo exchanges of two iterations."""
+    rows, nsub = 8, 4
+    out = []
+    s = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for cols in (1 << 20, 1 << 22, 1 << 24):
+        bufs = [[torch.zeros((rows + 2, cols), dtype=torch.float32, device="cuda") for _ in range(nsub)]
+                for _ in range(2)]
+        for i in range(nsub):
+            bufs[0][i].uniform_(-1, 1)
+
+        def exchanges(b):
+            ex = []
+            for i in range(nsub):
+                ex.append((bufs[b][(i - 1) % nsub][rows + 1].data_ptr(), bufs[b][i][1].data_ptr()))
+                ex.append((bufs[b][(i + 1) % nsub][0].data_ptr(), bufs[b][i][rows].data_ptr()))
+            return ex
+
+        def sweep(b):
+            for i in range(nsub):
+                mpt.mpt_demo_jacobi_step(bufs[b][i], bufs[1 - b][i], rows, cols, s)
+
+        hb = cols * 4
+        single = mpt.mpt_plan(ctx, hb, mpt.MPT_D2D, [(mpt.MPT_PATH_CE, 65536, hb)])
+        tuned_g = mpt.mpt_plan(ctx, hb, mpt.MPT_D2D, None)
+        tuned_e = mpt.mpt_plan(ctx, hb, mpt.MPT_D2D, None, 16, mpt.MPT_PLAN_EAGER)
+        variants = {
+            "single_path_direct": {b: [mpt.mpt_prepare(ctx, single, d, x, mpt.MPT_PREPARE_EAGER) for d, x in exchanges(b)]
+                                   for b in (0, 1)},
+            "multi_path_direct": {b: [mpt.mpt_prepare(ctx, tuned_e, d, x, mpt.MPT_PREPARE_EAGER) for d, x in exchanges(b)]
+                                  for b in (0, 1)},
+            "multi_path_transfer_graphs": {b: [mpt.mpt_capture(ctx, tuned_g, d, x) for d, x in exchanges(b)]
+                                           for b in (0, 1)},
+        }
+        row = {"halo_bytes": hb, "subdomain_bytes": (rows + 2) * cols * 4,
+               "plan_graph": [(q["kind"], q["share"]) for q in mpt.mpt_plan_paths(tuned_g)],
+               "plan_direct": [(q["kind"], q["share"]) for q in mpt.mpt_plan_paths(tuned_e)]}
+        for name, hs in variants.items():
+            for warm in (True, False):
+                e0.record(s)
+                for it in range(2 if warm else iters):
+                    b = it % 2
+                    sweep(b)
+                    for h in hs[1 - b]:
+                        mpt.mpt_launch(h, s)
+                e1.record(s)
+                e1.synchronize()
+            row[name + "_ms_per_iter"] = round(e0.elapsed_time(e1) / iters, 4)
+        # one graph: two sweeps and their halo exchanges (direct-issue handles captured)
+        hs = variants["multi_path_direct"]
+        s.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s, capture_error_mode="thread_local"):
+            for b in (0, 1):
+                sweep(b)
+                for h in hs[1 - b]:
+                    mpt.mpt_launch(h, s)
+        g.replay()
+        torch.cuda.synchronize()
+        e0.record(s)
+        with torch.cuda.stream(s):
+            for _ in range(iters // 2):
+                g.replay()
+        e1.record(s)
+        e1.synchronize()
+        row["multi_path_one_graph_ms_per_iter"] = round(e0.elapsed_time(e1) / iters, 4)
+        base = row["single_path_direct_ms_per_iter"]
+        for k in ("multi_path_direct", "multi_path_transfer_graphs", "multi_path_one_graph"):
+            row[k + "_speedup"] = round(base / row[k + "_ms_per_iter"], 3)
+        out.append(row)
+        del g
+        for hs in variants.values():
+            for lst in hs.values():
+                for h in lst:
+                    mpt.mpt_graph_release(h)
+        for p in (single, tuned_g, tuned_e):
+            mpt.mpt_plan_destroy(p)
+        del bufs
+        torch.cuda.empty_cache()
+    return out
+
+
 def run_kernel_only(args):
     """One kernel alone on one message (for profiling): K launches timed with CUDA events."""
     import torch
@@ -975,6 +1064,7 @@ def main(argv=None):
     ap.add_argument("--no-batched", action="store_true")
     ap.add_argument("--no-host-sweep", action="store_true")
     ap.add_argument("--no-windows", action="store_true")
+    ap.add_argument("--no-jacobi", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="per arrival rate; 0 skips serving")
     ap.add_argument("--serve-rates", default="1000,10000,50000")
     ap.add_argument("--tune", choices=["online", "model"], default="online",

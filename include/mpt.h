@@ -442,6 +442,17 @@ MPT_API mpt_status mpt_serve_stats(mpt_server_t server, mpt_serve_stats_t* out);
  * Completions not yet polled are dropped. */
 MPT_API mpt_status mpt_serve_stop(mpt_server_t server);
 
+/* ---- compute for the compute-plus-communication demonstration ------------------------ */
+
+/* One Jacobi sweep over a subdomain (the paper's application study, Sec. 5.4: subdomains in
+ * a ring exchange boundary rows with both neighbours), so that stencil kernels and
+ * multi-path halo exchanges can be captured together into one graph.  in/out: (rows + 2)
+ * x cols fp32 row-major device arrays, rows 0 and rows+1 the halos.  Interior points:
+ * out[r][c] = ((in[r-1][c] + in[r+1][c]) + (in[r][c-1] + in[r][c+1])) * 0.25, each operation
+ * rounded to fp32 in that order; columns 0 and cols-1 copied; out's halo rows untouched.
+ * Asynchronous on `stream` (legal inside a stream capture).  Errors: EINVAL. */
+MPT_API mpt_status mpt_demo_jacobi_step(const float* in, float* out, uint32_t rows, uint64_t cols, void* stream);
+
 /* ---- failure detection self-test ---------------------------------------------------- */
 
 /* Launch the staged path's consumer kernel on one chunk whose ready flag nothing raises,

@@ -19,9 +19,12 @@ What the oracle states, in plain slow code, and where it comes from:
 * ``transfer`` -- the result every transfer must produce: ``dst == src`` byte for
   byte (a memcpy), the 64-bit order-independent digest used to compare large
   buffers, and the expected arenas of a batch of transfers.
+* ``jacobi``   -- the compute-plus-communication demonstration (Sec. 5.4's Jacobi
+  solver): sweeps of the undivided periodic grid, which subdomains exchanging halo
+  rows over the transfer paths must reproduce exactly.
 
 Parity of the planner is pinned by hand-derived plans and invariants, the cost model
 by closed forms, and the copy is its own definition.  Nothing here is "parity
 unpinned".
 """
-from . import planner, cost, transfer  # noqa: F401
+from . import planner, cost, transfer, jacobi  # noqa: F401

@@ -325,6 +325,10 @@ def mpt_serve_stop(server: int) -> None:
     _check(lib().mpt_serve_stop(server), "mpt_serve_stop")
 
 
+def mpt_demo_jacobi_step(inp, out, rows: int, cols: int, stream=None) -> None:
+    _check(lib().mpt_demo_jacobi_step(_ptr(inp), _ptr(out), rows, cols, _stream(stream)), "mpt_demo_jacobi_step")
+
+
 def mpt_selftest_flag_timeout(ctx: int, timeout_ns: int):
     """(status, site) left by a bounded device wait on a flag nothing raises."""
     site = C.c_uint32()

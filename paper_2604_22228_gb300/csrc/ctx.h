@@ -27,6 +27,7 @@ struct EagerLane {
   cudaStream_t s[2] = {nullptr, nullptr};
   cudaEvent_t hop1[2] = {nullptr, nullptr};
   cudaEvent_t hop2[2] = {nullptr, nullptr};
+  unsigned long long hop2_capture[2] = {0, 0};  // capture id the hop2 event was recorded in (0 = none)
   cudaEvent_t done = nullptr;
   void* host_stage = nullptr;
   uint64_t host_stage_bytes = 0;

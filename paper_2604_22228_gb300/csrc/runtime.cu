@@ -491,6 +491,25 @@ mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src
     return for_each_copy(c, plan, only, src, dst,
                          [&](int variant, const CopyArgs& a, uint32_t ctas) { return launch_copy(user, variant, a, ctas); });
   }
+  // A staged path allocates its staging on first use, which a stream capture forbids: refuse
+  // before anything is issued, so the caller's capture stays intact.
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  unsigned long long capture_id = 0;
+  if (cudaStreamGetCaptureInfo(user, &cap, &capture_id) != cudaSuccess) {
+    cudaGetLastError();
+    cap = cudaStreamCaptureStatusNone;
+  }
+  if (cap != cudaStreamCaptureStatusActive) capture_id = 0;
+  if (cap != cudaStreamCaptureStatusNone) {
+    for (uint32_t p = 0; p < plan->npaths; ++p) {
+      if (plan->first_chunk[p + 1] == plan->first_chunk[p] || plan->paths[p].kind != MPT_PATH_HS) continue;
+      const EagerLane& L = c->lane[p];
+      const uint64_t have = plan->dir == MPT_D2D ? L.host_stage_bytes : L.dev_stage_bytes;
+      if (have < 2 * plan->paths[p].chunk_bytes)
+        return fail(MPT_EINVAL, "mpt_launch_eager: the staged path allocates its staging on first use, which a "
+                                "stream capture forbids; run the transfer once before capturing it");
+    }
+  }
   CUDA_TRY(cudaEventRecord(c->fork, user));
   uint8_t* d8 = static_cast<uint8_t*>(dst);
   const uint8_t* s8 = static_cast<const uint8_t*>(src);
@@ -536,8 +555,10 @@ mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src
           const mpt_chunk& ch = plan->chunks[i];
           const uint32_t slot = (i - lo) & 1u;
           uint8_t* sl = stage + slot * cb;
-          // hop one may refill this slot only after the slot's previous hop two
-          CUDA_TRY(cudaStreamWaitEvent(L.s[0], L.hop2[slot], 0));
+          // hop one may refill this slot only after the slot's previous hop two -- when that
+          // hop two belongs to the same capture (or neither is captured): a capture cannot
+          // wait on work recorded outside it
+          if (L.hop2_capture[slot] == capture_id) CUDA_TRY(cudaStreamWaitEvent(L.s[0], L.hop2[slot], 0));
           if (plan->dir == MPT_D2H) {
             RangeDesc r{ch.offset, 0, ch.bytes, 0, 0};
             int variant = 0;
@@ -563,6 +584,7 @@ mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src
             CUDA_TRY(cudaMemcpyAsync(d8 + ch.offset, sl, ch.bytes, cudaMemcpyDefault, L.s[1]));
           }
           CUDA_TRY(cudaEventRecord(L.hop2[slot], L.s[1]));
+          L.hop2_capture[slot] = capture_id;
         }
         last = L.s[1];
         break;
