@@ -168,6 +168,15 @@ def aggregate(world: int, bytes_per_rank: float, seconds: float) -> tuple[float,
 _CPU_SRC = {}
 
 
+def workload_config(world: int) -> dict:
+    """The `config` object both arms report (same workload, same keys)."""
+    return {"workload": "d2d message sweep 8 B..1 GiB (28 sizes), fp32 payload seed 0x5EED0002; tuned "
+                        "multi-path plans, graph or direct issue per size as tuned",
+            "messages_per_step": len(SIZES), "bytes_per_step": sum(SIZES),
+            "l2": "cold: every message has its own region; 4 GiB touched per step > 129 MiB L2",
+            "parallelism": f"replicas x{world}"}
+
+
 def cpu_oracle_sample(plans, budget_s=10.0, max_bytes=256 * MiB):
     """Time the oracle (planner + memcpy) over the sweep's sizes up to max_bytes, repeated
     until budget_s has passed (at least one pass).  Returns (GB/s, seconds, bytes,
@@ -217,7 +226,7 @@ def run_reference(args):
         "value": round(value, 3), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(total_s / args.steps * 1e3, 3), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": "d2d sweep 8B-1GiB fp32 (oracle sample up to 256 MiB)", "l2": "n/a (CPU)"},
+        "config": workload_config(args.gpus),
         "cpu_baseline": {"value": round(value, 3), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc},
         "e2e": {"value": round(value, 3), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "wall_s": round(time.perf_counter() - t0, 2),
@@ -428,41 +437,75 @@ def run_ours(args):
     ok = ok and st == mpt.MPT_OK
 
     # ---- end to end through the C ABI from page-locked host memory ----
+    # Every step copies its 2 GiB of inputs host->device, runs the sweep, and reads its
+    # 2 GiB of results back device->host, all through tuned mpt graphs/handles.  Steps are
+    # pipelined over two device arena sets: step k's results go down while step k+1's
+    # inputs come up, using both directions of the host link at once.
     e2e = None
     if not args.no_e2e:
         hsrc = torch.empty(total, dtype=torch.uint8).pin_memory()
         hdst = torch.empty(total, dtype=torch.uint8).pin_memory()
         hsrc[big:big + SIZES[-1]].copy_(host)
-        up = mpt.mpt_plan(ctx, total, mpt.MPT_H2D, None)
-        down = mpt.mpt_plan(ctx, total, mpt.MPT_D2H, None)
-        g_up = mpt.mpt_capture(ctx, up, base_s, hsrc.data_ptr())
-        g_down = mpt.mpt_capture(ctx, down, hdst.data_ptr(), base_d)
-        e2e_steps = max(1, min(args.steps, 10))
-        for _ in range(2):
-            mpt.mpt_launch(g_up, stream)
-            for g in step_handles:
-                mpt.mpt_launch(g, stream)
-            mpt.mpt_launch(g_down, stream)
-        stream.synchronize()
+        src2 = torch.empty(total, dtype=torch.uint8, device=dev)
+        dst2 = torch.zeros(total, dtype=torch.uint8, device=dev)
+        sets = [(base_s, base_d), (src2.data_ptr(), dst2.data_ptr())]
+        if args.e2e_plan == "tuned":
+            up = mpt.mpt_plan(ctx, total, mpt.MPT_H2D, None)
+            down = mpt.mpt_plan(ctx, total, mpt.MPT_D2H, None)
+        else:  # copy engines only: the link legs leave every SM to the sweep
+            up = mpt.mpt_plan(ctx, total, mpt.MPT_H2D, [(mpt.MPT_PATH_CE, 65536, 512 * MiB)])
+            down = mpt.mpt_plan(ctx, total, mpt.MPT_D2H, [(mpt.MPT_PATH_CE, 65536, 512 * MiB)])
+        g_up = [mpt.mpt_capture(ctx, up, sp, hsrc.data_ptr()) for sp, _ in sets]
+        g_down = [mpt.mpt_capture(ctx, down, hdst.data_ptr(), dp) for _, dp in sets]
+        sweep_h = [step_handles,
+                   [mpt.mpt_prepare(ctx, p, sets[1][1] + o, sets[1][0] + o,
+                                    mpt.MPT_PREPARE_EAGER if m == "eager" else mpt.MPT_PREPARE_GRAPH)
+                    for p, o, m in zip(step_plans, offs, step_modes)]]
+        s_up, s_mid, s_down = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+        ev_up = [torch.cuda.Event() for _ in sets]
+        ev_mid = [torch.cuda.Event() for _ in sets]
+        ev_down = [torch.cuda.Event() for _ in sets]
+
+        def e2e_step(k):
+            i = k % 2
+            s_up.wait_event(ev_mid[i])       # the set's previous sweep has read its inputs
+            mpt.mpt_launch(g_up[i], s_up)
+            ev_up[i].record(s_up)
+            s_mid.wait_event(ev_up[i])
+            s_mid.wait_event(ev_down[i])     # the set's previous results have gone down
+            for h in sweep_h[i]:
+                mpt.mpt_launch(h, s_mid)
+            ev_mid[i].record(s_mid)
+            s_down.wait_event(ev_mid[i])
+            mpt.mpt_launch(g_down[i], s_down)
+            ev_down[i].record(s_down)
+
+        e2e_steps = max(2, min(args.steps, 10))
+        for k in range(2):
+            e2e_step(k)
+        torch.cuda.synchronize()
         dist_barrier(world)
-        e0.record(stream)
-        for _ in range(e2e_steps):
-            mpt.mpt_launch(g_up, stream)
-            for g in step_handles:
-                mpt.mpt_launch(g, stream)
-            mpt.mpt_launch(g_down, stream)
-        e1.record(stream)
+        e0.record(s_up)
+        for k in range(e2e_steps):
+            e2e_step(k)
+        s_up.wait_stream(s_mid)
+        s_up.wait_stream(s_down)
+        e1.record(s_up)
         e1.synchronize()
         dist_barrier(world)
         e2e_s = e0.elapsed_time(e1) / 1e3
         e2e_val, _ = aggregate(world, total_bytes * e2e_steps, e2e_s)
-        ok = ok and bool(torch.equal(hdst[big:big + 4096], hsrc[big:big + 4096]))
+        torch.cuda.synchronize()
+        ok = ok and bool(torch.equal(hdst[big:big + 4096], hsrc[big:big + 4096])) and \
+            bool(torch.equal(hdst[offs[20]:offs[20] + SIZES[20]], hsrc[offs[20]:offs[20] + SIZES[20]]))
         e2e = {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": total, "d2h_bytes_per_step": total,
-               "steps": e2e_steps}
-        for g in (g_up, g_down):
+               "steps": e2e_steps, "pipelined": "2 device arena sets; step k down while step k+1 comes up",
+               "link_plans": args.e2e_plan}
+        for g in g_up + g_down + sweep_h[1]:
             mpt.mpt_graph_release(g)
         for p in (up, down):
             mpt.mpt_plan_destroy(p)
+        del src2, dst2
 
     lifecycle = run_graph_lifecycle(mpt, torch, ctx, stream)
     windows = None if args.no_windows else run_windows(mpt, torch, ctx)
@@ -519,11 +562,7 @@ def run_ours(args):
             "value": round(value, 3), "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(slowest / args.steps * 1e3, 4), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": "d2d sweep 8B-1GiB fp32 seed 0x5EED0002, tuned multi-path plans, "
-                                   "graph or direct issue per size as tuned",
-                       "messages_per_step": len(SIZES), "bytes_per_step": total_bytes,
-                       "l2": "cold: every message has its own region; 4 GiB touched per step > 129 MiB L2",
-                       "parallelism": f"replicas x{world}"},
+            "config": workload_config(world),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
                          "kernel": "k_sm_copy_" + ("bulk" if variant else "vec"),
@@ -1059,6 +1098,8 @@ def main(argv=None):
     ap.add_argument("--kernel-launches", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-plan", choices=["tuned", "ce"], default="ce",
+                    help="plans of the end-to-end link legs: tuned, or copy engines only")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-baselines", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
