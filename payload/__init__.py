@@ -109,6 +109,23 @@ def fill(kind: str, seed: int, nbytes: int, out: np.ndarray | None = None) -> np
     return dst
 
 
+def fill_window(kind: str, seed: int, offset: int, nbytes: int) -> np.ndarray:
+    """Bytes [offset, offset + nbytes) of the payload stream (what ``fill`` would give for a
+    message of offset + nbytes bytes), generated without the bytes before ``offset``."""
+    eb = ELEM_BYTES[kind]
+    first = offset // eb
+    lead = offset - first * eb
+    x = splitmix64_words(seed, first, (lead + nbytes + eb - 1) // eb)
+    if kind == "u8":
+        raw = x.astype("<u8").view(np.uint8)
+    elif kind == "u32":
+        raw = (x & np.uint64(0xFFFFFFFF)).astype("<u4").view(np.uint8)
+    else:
+        f = ((x >> np.uint64(40)).astype(np.float64) * (2.0 ** -23) - 1.0).astype("<f4")
+        raw = f.view(np.uint8) if kind == "f32" else (f.view("<u4") >> np.uint32(16)).astype("<u2").view(np.uint8)
+    return raw[lead:lead + nbytes].copy()
+
+
 def request_seed(seed: int, request_id: int) -> int:
     """Per-request payload seed: splitmix64 output ``request_id`` of stream ``seed``."""
     return splitmix64_scalar(seed, request_id)

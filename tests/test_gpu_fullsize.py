@@ -1,0 +1,96 @@
+"""Parity at the benchmark's largest sizes, in the launch configuration bench.py times:
+the 1 GiB device-to-device message through the tuned handle (graph or direct issue), and
+2 GiB host-to-device and device-to-host through the tuned plans.  Whole-buffer digests must
+match and sampled windows must equal the oracle's bytes (the payload stream, since a
+transfer's result is its source)."""
+import numpy as np
+import pytest
+
+import paper_2604_22228_gb300 as mpt
+import payload
+from oracle import transfer as T
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+MiB, GiB = 1 << 20, 1 << 30
+
+
+def _handle(ctx, n, direction, dst, src):
+    """The bench's choice: graph or direct issue, as the tuner measured faster."""
+    mode = mpt.MPT_PREPARE_GRAPH
+    try:
+        g_us = mpt.mpt_tune_get(ctx, direction, n, mpt.MPT_MODE_GRAPH)[1]
+        e_us = mpt.mpt_tune_get(ctx, direction, n, mpt.MPT_MODE_EAGER)[1]
+        mode = mpt.MPT_PREPARE_EAGER if e_us < g_us else mpt.MPT_PREPARE_GRAPH
+    except mpt.MptError:
+        pass
+    plan = mpt.mpt_plan(ctx, n, direction, None, 16,
+                        mpt.MPT_PLAN_EAGER if mode == mpt.MPT_PREPARE_EAGER else mpt.MPT_LAYOUT_CONTIG)
+    return plan, mpt.mpt_prepare(ctx, plan, dst, src, mode)
+
+
+def _check_windows(got_at, kind, seed, n, rng, count=24, width=4096):
+    for off in [0, n - width] + list(rng.integers(0, n - width, count)):
+        off = int(off)
+        assert np.array_equal(got_at(off, width), payload.fill_window(kind, seed, off, width)), off
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    torch.cuda.init()
+    c = mpt.mpt_ctx_create(0)
+    yield c
+    assert mpt.mpt_ctx_status(c)[0] == mpt.MPT_OK
+    mpt.mpt_ctx_destroy(c)
+
+
+def test_d2d_1gib_tuned(ctx):
+    import torch
+    n = GiB
+    host = torch.empty(n, dtype=torch.uint8).pin_memory()
+    payload.fill("f32", payload.SEED_D2D_SWEEP, n, out=host.numpy())
+    src = host.cuda()
+    dst = torch.zeros(n + 4096, dtype=torch.uint8, device="cuda")
+    plan, h = _handle(ctx, n, mpt.MPT_D2D, dst.data_ptr(), src.data_ptr())
+    for _ in range(2):
+        mpt.mpt_launch(h, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert mpt.mpt_hash_device(ctx, dst.data_ptr(), n) == mpt.mpt_hash_device(ctx, src.data_ptr(), n)
+    assert int(dst[n:].sum()) == 0  # nothing written past the message
+    _check_windows(lambda o, w: dst[o:o + w].cpu().numpy(), "f32", payload.SEED_D2D_SWEEP, n,
+                   np.random.default_rng(1))
+    mpt.mpt_graph_release(h)
+    mpt.mpt_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("direction", [mpt.MPT_H2D, mpt.MPT_D2H])
+def test_host_2gib_tuned(ctx, direction):
+    import torch
+    n = 2 * GiB
+    host = torch.empty(n, dtype=torch.uint8).pin_memory()
+    dev = torch.empty(n, dtype=torch.uint8, device="cuda")
+    if direction == mpt.MPT_H2D:
+        payload.fill("u32", payload.SEED_HOST_SWEEP, n, out=host.numpy())
+        src, dst = host, dev
+    else:
+        dev.copy_(torch.from_numpy(payload.fill("u32", payload.SEED_HOST_SWEEP, n)))
+        host.zero_()
+        src, dst = dev, host
+    plan, h = _handle(ctx, n, direction, dst.data_ptr(), src.data_ptr())
+    mpt.mpt_launch(h, torch.cuda.current_stream())
+    torch.cuda.synchronize()
+    assert mpt.mpt_hash_device(ctx, dst.data_ptr(), n) == mpt.mpt_hash_device(ctx, src.data_ptr(), n)
+    view = (lambda o, w: dst[o:o + w].cpu().numpy()) if direction == mpt.MPT_H2D else \
+        (lambda o, w: dst.numpy()[o:o + w])
+    _check_windows(view, "u32", payload.SEED_HOST_SWEEP, n, np.random.default_rng(2))
+    mpt.mpt_graph_release(h)
+    mpt.mpt_plan_destroy(plan)
+
+
+def test_digest_of_full_message_matches_oracle(ctx):
+    """The GPU digest used above equals the oracle's digest on a 256 MiB payload."""
+    import torch
+    n = 256 * MiB
+    data = payload.fill("f32", payload.SEED_D2D_SWEEP, n)
+    t = torch.from_numpy(data).cuda()
+    assert mpt.mpt_hash_device(ctx, t.data_ptr(), n) == T.hash64(data)

@@ -141,3 +141,10 @@ def test_batch_layout_offsets():
     assert all(s % 16 == 0 and d % 16 == 0 for _, s, d, _ in items)
     packed, _ = payload.batch_layout(sizes, d2d, gaps, align=1)
     assert packed == [("dev", 16, 16, 10), ("host", 32, 58, 33), ("dev", 74, 139, 16)]
+
+
+def test_fill_window_matches_prefix_stream():
+    for kind in ("u8", "u32", "f32", "bf16"):
+        full = payload.fill(kind, 33, 5000)
+        for off, n in [(0, 10), (1, 7), (3, 100), (4095, 905), (17, 0)]:
+            assert np.array_equal(payload.fill_window(kind, 33, off, n), full[off:off + n]), (kind, off, n)
