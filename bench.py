@@ -270,6 +270,8 @@ def run_ours(args):
         chunk = max(16, min(n, 4 * MiB)) // 16 * 16 or 16
         if kind == "ce":
             specs = [(mpt.MPT_PATH_CE, 65536, chunk)]
+        elif kind == "hs":  # device -> page-locked host slot -> device (Algorithm 2 StageHostCopy)
+            specs = [(mpt.MPT_PATH_HS, 65536, chunk)]
         elif kind == "sm":
             specs = [(mpt.MPT_PATH_SM, 65536, chunk)]
         else:  # ce+sm at 50/50
@@ -395,7 +397,7 @@ def run_ours(args):
     if not args.no_baselines:
         base["tuned"] = time_graphs(step_handles, reps)
         base["tuned_graph_only"] = time_graphs(tuned_graphs, reps)
-        for kind in ("ce", "sm", "split"):
+        for kind in ("ce", "sm", "split", "hs"):
             plans, graphs = capture_all(kind)
             base[kind] = time_graphs(graphs, reps)
             for g in graphs:
@@ -543,6 +545,7 @@ def run_ours(args):
                 "tuned_gbs": gb(base["tuned"][i]), "tuned_graph_gbs": gb(base["tuned_graph_only"][i]),
                 "ce_graph_gbs": gb(base["ce"][i]), "sm_graph_gbs": gb(base["sm"][i]),
                 "split50_graph_gbs": gb(base["split"][i]), "split50_eager_gbs": gb(base["split_eager"][i]),
+                "hs_graph_gbs": gb(base["hs"][i]),
                 "tuned_eager_gbs": gb(base["tuned_eager"][i]), "best_single_gbs": gb(best_single),
                 "tuned_vs_best_single": round(best_single / base["tuned"][i], 3),
                 "tuned_graph_vs_tuned_eager": round(base["tuned_eager"][i] / base["tuned"][i], 3)})

@@ -184,6 +184,15 @@ typedef struct {
 
 MPT_API mpt_status mpt_ctx_info(mpt_ctx_t ctx, mpt_device_info* out);
 
+/* Lane timers: while enabled (or MPT_TRACE_LANES=1 at context creation), every multi-path
+ * eager launch (mpt_launch_eager, or mpt_launch of an eager-prepared handle that forks onto
+ * lanes; not inside a stream capture) records CUDA events at the start and end of each
+ * path's lane.  mpt_lane_times waits for the last such launch and writes each path's
+ * duration in milliseconds to out_ms[path index] (-1 for paths it did not time); *n gets
+ * one past the last timed path.  Shows how evenly a split balances its paths. */
+MPT_API mpt_status mpt_trace_lanes(mpt_ctx_t ctx, uint32_t enable);
+MPT_API mpt_status mpt_lane_times(mpt_ctx_t ctx, float* out_ms, uint32_t cap, uint32_t* n);
+
 /* Read the context's device status word (blocking: synchronises the device), return it
  * (MPT_OK or the first recorded MPT_ETIMEDOUT) and reset it to MPT_OK.  `site` (nullable)
  * receives an implementation-defined code of the wait that gave up. */
@@ -394,7 +403,7 @@ MPT_API mpt_status mpt_batch_release(mpt_batch_t batch);
 typedef struct mpt_server_s* mpt_server_t;
 
 typedef struct {
-  uint64_t staging_budget_bytes;  /* admission limit on bytes in flight (0 = 8 GiB) */
+  uint64_t staging_budget_bytes;  /* admission limit on bytes in flight (0 = $MPT_STAGING_BUDGET, else 8 GiB) */
   uint32_t max_batch;             /* transfers per batch (0 = the slot capacity) */
   uint32_t max_inflight_batches;  /* batches on the GPU at once (0 = every slot) */
 } mpt_serve_config;

@@ -94,6 +94,18 @@ def mpt_ctx_info(ctx: int) -> dict:
     return out
 
 
+def mpt_trace_lanes(ctx: int, enable: bool = True) -> None:
+    _check(lib().mpt_trace_lanes(ctx, 1 if enable else 0), "mpt_trace_lanes")
+
+
+def mpt_lane_times(ctx: int) -> list[float]:
+    """Per-path lane durations (ms) of the last traced multi-path eager launch (-1: not timed)."""
+    out = (C.c_float * MPT_MAX_PATHS)()
+    n = C.c_uint32()
+    _check(lib().mpt_lane_times(ctx, out, MPT_MAX_PATHS, C.byref(n)), "mpt_lane_times")
+    return [round(v, 6) for v in out[: n.value]]
+
+
 def mpt_ctx_status(ctx: int) -> tuple[int, int]:
     """(status, site) of the context's device status word, which is then reset."""
     site = C.c_uint32()

@@ -94,6 +94,8 @@ SIGNATURES = {
     "mpt_ctx_destroy": (C.c_int, [H]),
     "mpt_ctx_info": (C.c_int, [H, P(mpt_device_info)]),
     "mpt_ctx_status": (C.c_int, [H, P(C.c_uint32)]),
+    "mpt_trace_lanes": (C.c_int, [H, C.c_uint32]),
+    "mpt_lane_times": (C.c_int, [H, P(C.c_float), C.c_uint32, P(C.c_uint32)]),
     "mpt_plan": (C.c_int, [H, C.c_uint64, C.c_uint32, P(mpt_path_spec), C.c_uint32, C.c_uint32, C.c_uint32,
                           P(H)]),
     "mpt_plan_chunks": (C.c_int, [H, P(mpt_chunk), C.c_size_t, P(C.c_size_t)]),

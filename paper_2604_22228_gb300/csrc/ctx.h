@@ -29,6 +29,7 @@ struct EagerLane {
   cudaEvent_t hop2[2] = {nullptr, nullptr};
   unsigned long long hop2_capture[2] = {0, 0};  // capture id the hop2 event was recorded in (0 = none)
   cudaEvent_t done = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;      // lane timers (MPT_TRACE_LANES)
   void* host_stage = nullptr;
   uint64_t host_stage_bytes = 0;
   void* dev_stage = nullptr;
@@ -107,6 +108,8 @@ struct mpt_ctx_s {
   size_t cache_cap = 64;
   uint64_t stage_max = 8ull << 20;
   bool rebind_enabled = true;  // MPT_GRAPH_REBIND=0 turns the capture fast path off
+  bool trace_lanes = false;    // time every lane of multi-path eager launches
+  uint32_t traced = 0;         // lanes timed by the last such launch
   std::map<uint32_t, mpt::TuneEntry> tuned;  // tune_key -> choice
   // tuner scratch (grown on demand)
   void* tune_a = nullptr;

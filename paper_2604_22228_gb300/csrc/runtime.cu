@@ -511,6 +511,7 @@ mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src
     }
   }
   CUDA_TRY(cudaEventRecord(c->fork, user));
+  c->traced = 0;
   uint8_t* d8 = static_cast<uint8_t*>(dst);
   const uint8_t* s8 = static_cast<const uint8_t*>(src);
   for (uint32_t p = 0; p < plan->npaths; ++p) {
@@ -519,6 +520,8 @@ mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src
     EagerLane& L = c->lane[p];
     const mpt_path_spec& spec = plan->paths[p];
     CUDA_TRY(cudaStreamWaitEvent(L.s[0], c->fork, 0));
+    const bool trace = c->trace_lanes && capture_id == 0 && cap == cudaStreamCaptureStatusNone;
+    if (trace) CUDA_TRY(cudaEventRecord(L.t0, L.s[0]));
     cudaStream_t last = L.s[0];
     switch (spec.kind) {
       case MPT_PATH_CE:
@@ -592,6 +595,10 @@ mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src
       default:
         return fail(MPT_EINVAL, "unknown path kind %u", spec.kind);
     }
+    if (trace) {  // `last` ends after every hop of the lane
+      CUDA_TRY(cudaEventRecord(L.t1, last));
+      c->traced |= 1u << p;
+    }
     CUDA_TRY(cudaEventRecord(L.done, last));
     CUDA_TRY(cudaStreamWaitEvent(user, L.done, 0));
   }
@@ -655,7 +662,8 @@ mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out) {
           cudaEventCreateWithFlags(&L.hop2[i], cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(MPT_ECUDA, "mpt_ctx_create: streams/events"));
     }
-    if (cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess)
+    if (cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&L.t0) != cudaSuccess || cudaEventCreate(&L.t1) != cudaSuccess)
       return bail(fail(MPT_ECUDA, "mpt_ctx_create: events"));
   }
   if (cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess)
@@ -667,6 +675,7 @@ mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out) {
   c->cache_cap = (size_t)std::max<uint64_t>(1, env_u64("MPT_GRAPH_CACHE", 64));
   c->stage_max = std::max<uint64_t>(4096, env_u64("MPT_STAGE_BYTES", 8ull << 20));
   c->rebind_enabled = env_u64("MPT_GRAPH_REBIND", 1) != 0;
+  c->trace_lanes = env_u64("MPT_TRACE_LANES", 0) != 0;
   const char* tf = tune_file && *tune_file ? tune_file : std::getenv("MPT_TUNE_FILE");
   if (tf && *tf) {
     mpt_status st = mpt_tune_load(c, tf);
@@ -715,6 +724,8 @@ mpt_status mpt_ctx_destroy(mpt_ctx_t c) {
       if (L.hop2[i]) cudaEventDestroy(L.hop2[i]);
     }
     if (L.done) cudaEventDestroy(L.done);
+    if (L.t0) cudaEventDestroy(L.t0);
+    if (L.t1) cudaEventDestroy(L.t1);
     if (L.host_stage) cudaFreeHost(L.host_stage);
     if (L.dev_stage) cudaFree(L.dev_stage);
   }
@@ -740,6 +751,31 @@ mpt_status mpt_ctx_info(mpt_ctx_t c, mpt_device_info* out) {
   out->pageable_access = c->pageable ? 1 : 0;
   out->l2_bytes = (uint64_t)prop.l2CacheSize;
   out->memory_bytes = (uint64_t)prop.totalGlobalMem;
+  return MPT_OK;
+}
+
+mpt_status mpt_trace_lanes(mpt_ctx_t c, uint32_t enable) {
+  if (!c) return fail(MPT_EINVAL, "mpt_trace_lanes: NULL context");
+  c->trace_lanes = enable != 0;
+  c->traced = 0;
+  return MPT_OK;
+}
+
+mpt_status mpt_lane_times(mpt_ctx_t c, float* out_ms, uint32_t cap, uint32_t* n) {
+  if (!c || !n || (cap && !out_ms)) return fail(MPT_EINVAL, "mpt_lane_times: NULL argument");
+  uint32_t k = 0;
+  for (uint32_t p = 0; p < MPT_MAX_PATHS; ++p) {
+    if (!(c->traced & (1u << p))) {
+      if (p < cap) out_ms[p] = -1.0f;
+      continue;
+    }
+    float ms = -1.0f;
+    CUDA_TRY(cudaEventSynchronize(c->lane[p].t1));
+    CUDA_TRY(cudaEventElapsedTime(&ms, c->lane[p].t0, c->lane[p].t1));
+    if (p < cap) out_ms[p] = ms;
+    k = p + 1;
+  }
+  *n = k;
   return MPT_OK;
 }
 

@@ -17,6 +17,7 @@
 // does not hide queueing delay.
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
 #include <chrono>
 #include <condition_variable>
 #include <deque>
@@ -198,7 +199,11 @@ mpt_status mpt_serve_start(mpt_ctx_t ctx, const mpt_serve_config* cfg, mpt_serve
   mpt_server_s* s = new mpt_server_s;
   s->ctx = ctx;
   mpt_serve_config c = cfg ? *cfg : mpt_serve_config{};
-  if (c.staging_budget_bytes == 0) c.staging_budget_bytes = 8ull << 30;
+  if (c.staging_budget_bytes == 0) {
+    const char* v = std::getenv("MPT_STAGING_BUDGET");
+    c.staging_budget_bytes = (v && *v) ? std::strtoull(v, nullptr, 0) : 0;
+    if (c.staging_budget_bytes == 0) c.staging_budget_bytes = 8ull << 30;
+  }
   if (c.max_batch == 0 || c.max_batch > ctx->slots[0].max_xfers) c.max_batch = ctx->slots[0].max_xfers;
   if (c.max_inflight_batches == 0 || c.max_inflight_batches > ctx->slots.size())
     c.max_inflight_batches = (uint32_t)ctx->slots.size();

@@ -367,3 +367,26 @@ def test_pageable_host_memory_through_zero_copy(ctx):
     assert np.array_equal(o[:MiB], host_src[16:16 + MiB]) and np.array_equal(o[MiB:MiB + 1000], host_src[5:1005])
     for p in (zc, back, ce):
         mpt.mpt_plan_destroy(p)
+
+
+def test_lane_timers():
+    """Lane timers report one duration per path of a traced multi-path eager launch, and a
+    large share on a slow path (the staged route over the host link) shows up as the
+    longest lane."""
+    import torch
+    ctx = mpt.mpt_ctx_create(0)
+    n = 32 * MiB
+    src, dst = Buf(n, "dev"), Buf(n, "dev")
+    src.fill(seeded("u8", 5, n))
+    plan = mpt.mpt_plan(ctx, n, P.D2D, [(P.CE, 21845, 4 * MiB), (P.SM, 21845, 4 * MiB), (P.HS, 21846, 4 * MiB)])
+    mpt.mpt_launch_eager(ctx, plan, dst.ptr, src.ptr, torch.cuda.current_stream())
+    assert mpt.mpt_lane_times(ctx) == []  # not traced yet
+    mpt.mpt_trace_lanes(ctx, True)
+    mpt.mpt_launch_eager(ctx, plan, dst.ptr, src.ptr, torch.cuda.current_stream())
+    t = mpt.mpt_lane_times(ctx)
+    assert len(t) == 3 and all(x > 0 for x in t)
+    assert t[2] == max(t)  # ~11 MB through host memory twice, far slower than HBM paths
+    assert np.array_equal(dst.numpy(), seeded("u8", 5, n))
+    mpt.mpt_trace_lanes(ctx, False)
+    mpt.mpt_plan_destroy(plan)
+    mpt.mpt_ctx_destroy(ctx)
