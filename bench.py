@@ -61,18 +61,28 @@ def load_peaks():
 def roofline_traffic(variant: str, ctas: int):
     """DRAM bytes per 1 GiB launch from the committed ncu summary, or None when the kernel
     source changed since the capture (or no capture exists for this variant/launch)."""
-    import hashlib
     import re
     prof = os.path.join(ROOT, "profiles", f"k_sm_copy_{variant}_1GiB.md")
     if not os.path.exists(prof) or ctas not in (0,):
         return None
     text = open(prof).read()
     m = re.search(r"traffic_bytes_per_launch \| (\d+)", text)
-    h = re.search(r"copy_kernels.cu\): ([0-9a-f]{64})", text)
-    src = os.path.join(ROOT, "paper_2604_22228_gb300", "csrc", "copy_kernels.cu")
-    if not m or not h or hashlib.sha256(open(src, "rb").read()).hexdigest() != h.group(1):
+    h = re.search(r"kernel source sha256 \([^)]*\): ([0-9a-f]{64})", text)
+    if not m or not h or kernel_source_sha() != h.group(1):
         return None
     return int(m.group(1))
+
+
+KERNEL_SOURCES = ("copy_kernels.cu", "copy_device.cuh", "kernels.cuh")
+
+
+def kernel_source_sha() -> str:
+    """sha256 over the files the copy kernels are compiled from, in KERNEL_SOURCES order."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_2604_22228_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()
 
 
 # ---- clocks sampled during the timed region ---------------------------------------------

@@ -73,8 +73,10 @@ typedef enum { MPT_LAYOUT_CONTIG = 0, MPT_LAYOUT_INTERLEAVE = 1 } mpt_layout;
 typedef enum { MPT_MODE_GRAPH = 0, MPT_MODE_EAGER = 1 } mpt_mode;
 
 /* mpt_path_spec.flags for SM-kernel paths: which copy kernel variant to run. */
-#define MPT_SM_VEC128 0u   /* 128-bit vector loads/stores, grid-stride over tiles */
+#define MPT_SM_VEC128 0u   /* 128-bit vector loads/stores, grid-stride over 64 KiB tiles */
 #define MPT_SM_BULK 1u     /* cp.async.bulk global->shared->global ring per CTA */
+#define MPT_SM_TILE8K 2u   /* VEC128 over 8 KiB tiles: a message of a few MiB reaches every SM
+                              (BULK takes precedence when both are set) */
 
 /* One path of a plan.
  *   kind         one mpt_path_kind; allowed kinds per direction:
@@ -285,16 +287,21 @@ MPT_API mpt_status mpt_graph_evict(mpt_ctx_t ctx, const void* ptr, uint32_t* n);
 /* Issue the same multi-path workflow without a graph (Sec. 4.3's static runtime
  * pipelining engine): fork from `stream` onto per-path lane streams, enqueue every chunk,
  * join back onto `stream`.  Asynchronous.  Eager transfers that use the same staged path
- * serialise on that path's lane (Sec. 4.5 "Contention Avoidance"). */
+ * serialise on that path's lane (Sec. 4.5 "Contention Avoidance").  A plan with a single
+ * copy-engine or kernel path is issued on `stream` itself, without fork or join; outside a
+ * stream capture its copy kernels are launched with programmatic dependent launch, so that
+ * their launch overlaps the end of a copy kernel before them on `stream` (they wait for its
+ * completion before touching memory).  MPT_PDL=0 at context creation turns that off. */
 MPT_API mpt_status mpt_launch_eager(mpt_ctx_t ctx, mpt_plan_t plan, void* dst, const void* src, void* stream);
 
 /* ---- single kernels (the SM and zero-copy paths on their own) -------------------- */
 
 /* Copy `nbytes` from src to dst with one launch of the SM copy kernel on `stream`.
  * Both pointers must be device-accessible (device memory, or mapped page-locked host
- * memory for the zero-copy direction).  variant: MPT_SM_VEC128 or MPT_SM_BULK (the bulk
+ * memory for the zero-copy direction).  variant: MPT_SM_VEC128, MPT_SM_BULK (the bulk
  * variant handles the 16-byte-aligned body with cp.async.bulk and the rest with plain
- * loads; it falls back to VEC128 when src and dst differ modulo 16).  ctas: grid size,
+ * loads; it falls back to VEC128 when src and dst differ modulo 16) or MPT_SM_TILE8K
+ * (device memory only; ignored for the zero-copy direction).  ctas: grid size,
  * 0 = default.  ctx supplies the status word for bounded waits.  Errors: EINVAL. */
 MPT_API mpt_status mpt_sm_copy(mpt_ctx_t ctx, void* dst, const void* src, uint64_t nbytes, uint32_t variant,
                        uint32_t ctas, void* stream);
@@ -337,7 +344,9 @@ MPT_API mpt_status mpt_model_optimize(const mpt_model* m, uint64_t nbytes, uint3
  * zero-copy kernel, copy engine + kernel splits at several shares and chunk counts, the
  * staged path -- each the median of `reps` timed runs (0 = default), every run starting
  * with a cold L2 full of dirty lines (a 256 MiB write first, as after the kernel that
- * produced the data), and store the fastest for the message's log2 size bucket.  Blocking;
+ * produced the data; a message of at most 2 MiB is timed as the mean of 8 back-to-back
+ * launches after it, the regime of a stream of short messages where launch costs overlap),
+ * and store the fastest for the message's log2 size bucket.  Blocking;
  * allocates scratch buffers of `nbytes` (kept by the context).  MPT_TUNE_VERBOSE=1 prints
  * every candidate's timing to stderr.  out (capacity 4, nullable),
  * out_n and out_us (nullable) receive the winner.  Errors: EINVAL, ECUDA, ENOMEM. */

@@ -6,6 +6,16 @@
 
 namespace mpt {
 
+// Programmatic dependent launch.  A copy kernel launched with programmatic stream
+// serialization may start while the kernel before it on the stream is finishing; it waits
+// here, before touching memory, until that kernel has completed and its writes are visible,
+// then lets the next such kernel begin its own launch.  Launched without the attribute
+// (graph nodes, plain launches) both instructions are no-ops.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
   uint4 v;
   asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"

@@ -4,6 +4,8 @@
 //                  the ranges it is given, every thread keeping eight 16-byte vectors in
 //                  flight.  The device-to-device path the SMs add next to the copy
 //                  engines (Sec. 4.3's horizontal split over paths).
+//  k_sm_copy_vec8k the same loop with one vector per thread (8 KiB tiles), so that a
+//                  message of a few MiB spreads over every SM instead of a few dozen.
 //  k_sm_copy_bulk  same contract, body moved by cp.async.bulk global->shared->global
 //                  (non-multicast) through a four-stage shared-memory ring driven by one
 //                  thread per CTA and tracked by mbarriers.
@@ -55,8 +57,12 @@ __device__ __forceinline__ void copy_edges(const uint8_t* s, uint8_t* o, const R
   if (tid >= 32 && tid < 32 + tail) o[tail_start + (tid - 32)] = s[tail_start + (tid - 32)];
 }
 
-template <bool kHostLink, bool kAny>
+// kU 16-byte vectors per thread per tile: tiles of kVecThreads * kU * 16 bytes (64 KiB for
+// kU = 8, 8 KiB for kU = 1).
+template <bool kHostLink, bool kAny, int kU>
 __device__ __forceinline__ void copy_tiles_vec(const CopyArgs& a) {
+  constexpr uint64_t kTileVecs = (uint64_t)kVecThreads * kU;
+  constexpr int kHalf = kU >= 2 ? kU / 2 : 1;  // shifted path: vector pairs per round
   const uint32_t tid = threadIdx.x;
   for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
     const int r = find_range(a, t);
@@ -67,17 +73,17 @@ __device__ __forceinline__ void copy_tiles_vec(const CopyArgs& a) {
     const uint64_t nvec = (d.bytes - d.head) >> 4;
     if (lt == 0) copy_edges(s, o, d, nvec << 4);
     uint4* ov = reinterpret_cast<uint4*>(o + d.head);
-    const uint64_t v0 = (uint64_t)lt * kVecTileVecs + tid;
+    const uint64_t v0 = (uint64_t)lt * kTileVecs + tid;
     if (!kAny || d.shift == 0) {
       const uint4* sv = reinterpret_cast<const uint4*>(s + d.head);
-      uint4 buf[kVecUnroll];
+      uint4 buf[kU];
 #pragma unroll
-      for (int u = 0; u < kVecUnroll; ++u) {
+      for (int u = 0; u < kU; ++u) {
         const uint64_t i = v0 + (uint64_t)u * kVecThreads;
         if (i < nvec) buf[u] = kHostLink ? ld_plain(sv + i) : ld_stream(sv + i);
       }
 #pragma unroll
-      for (int u = 0; u < kVecUnroll; ++u) {
+      for (int u = 0; u < kU; ++u) {
         const uint64_t i = v0 + (uint64_t)u * kVecThreads;
         if (i < nvec) st_plain(ov + i, buf[u]);
       }
@@ -86,10 +92,10 @@ __device__ __forceinline__ void copy_tiles_vec(const CopyArgs& a) {
       const uint4* sw = reinterpret_cast<const uint4*>(s + d.head - d.shift);
       const uint32_t k = d.shift >> 2, r = (d.shift & 3u) * 8u;
 #pragma unroll
-      for (int half = 0; half < kVecUnroll; half += kVecUnroll / 2) {
-        uint4 w0[kVecUnroll / 2], w1[kVecUnroll / 2];
+      for (int half = 0; half < kU; half += kHalf) {
+        uint4 w0[kHalf], w1[kHalf];
 #pragma unroll
-        for (int u = 0; u < kVecUnroll / 2; ++u) {
+        for (int u = 0; u < kHalf; ++u) {
           const uint64_t i = v0 + (uint64_t)(half + u) * kVecThreads;
           if (i < nvec) {
             w0[u] = kHostLink ? ld_plain(sw + i) : ld_stream(sw + i);
@@ -97,7 +103,7 @@ __device__ __forceinline__ void copy_tiles_vec(const CopyArgs& a) {
           }
         }
 #pragma unroll
-        for (int u = 0; u < kVecUnroll / 2; ++u) {
+        for (int u = 0; u < kHalf; ++u) {
           const uint64_t i = v0 + (uint64_t)(half + u) * kVecThreads;
           if (i < nvec) st_plain(ov + i, shift16(w0[u], w1[u], k, r));
         }
@@ -184,15 +190,36 @@ __device__ __forceinline__ uint32_t bulk_piece(const CopyArgs& a, uint32_t t, co
 
 }  // namespace
 
-__global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec(CopyArgs a) { copy_tiles_vec<false, false>(a); }
-__global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec_any(CopyArgs a) { copy_tiles_vec<false, true>(a); }
-__global__ void __launch_bounds__(kVecThreads) k_zc_copy(CopyArgs a) { copy_tiles_vec<true, false>(a); }
-__global__ void __launch_bounds__(kVecThreads) k_zc_copy_any(CopyArgs a) { copy_tiles_vec<true, true>(a); }
+__global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec(CopyArgs a) {
+  pdl_enter();
+  copy_tiles_vec<false, false, kVecUnroll>(a);
+}
+__global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec_any(CopyArgs a) {
+  pdl_enter();
+  copy_tiles_vec<false, true, kVecUnroll>(a);
+}
+__global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec8k(CopyArgs a) {
+  pdl_enter();
+  copy_tiles_vec<false, false, 1>(a);
+}
+__global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec8k_any(CopyArgs a) {
+  pdl_enter();
+  copy_tiles_vec<false, true, 1>(a);
+}
+__global__ void __launch_bounds__(kVecThreads) k_zc_copy(CopyArgs a) {
+  pdl_enter();
+  copy_tiles_vec<true, false, kVecUnroll>(a);
+}
+__global__ void __launch_bounds__(kVecThreads) k_zc_copy_any(CopyArgs a) {
+  pdl_enter();
+  copy_tiles_vec<true, true, kVecUnroll>(a);
+}
 
 __global__ void __launch_bounds__(kBulkThreads, 1) k_sm_copy_bulk(CopyArgs a) {
   extern __shared__ __align__(128) uint8_t smem[];
   __shared__ __align__(8) uint64_t bar[kBulkStages];
   const uint32_t tid = threadIdx.x;
+  pdl_enter();
 
   // Bytes outside the 16-byte body go with plain loads by the CTA owning tile 0.
   for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
@@ -364,8 +391,9 @@ int make_copy_args(CopyArgs& a, const void* src, void* dst, const RangeDesc* ran
     if (variant == 1 && d.shift) return kArgsNeedVec;
     if (d.shift) a.any_shift = 1;
     const uint64_t body = ((d.bytes - d.head) >> 4) << 4;
+    const uint64_t tile_vecs = variant == 3 ? (uint64_t)kVecThreads : kVecTileVecs;
     uint64_t t = variant == 1 ? (body + kBulkStageBytes - 1) / kBulkStageBytes
-                              : ((body >> 4) + kVecTileVecs - 1) / kVecTileVecs;
+                              : ((body >> 4) + tile_vecs - 1) / tile_vecs;
     if (t == 0) t = 1;  // a range too short for a body still needs its edge bytes copied
     a.r[a.nranges] = d;
     tiles += t;

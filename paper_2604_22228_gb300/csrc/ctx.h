@@ -110,6 +110,7 @@ struct mpt_ctx_s {
   bool rebind_enabled = true;  // MPT_GRAPH_REBIND=0 turns the capture fast path off
   bool trace_lanes = false;    // time every lane of multi-path eager launches
   uint32_t traced = 0;         // lanes timed by the last such launch
+  bool pdl = true;             // direct kernel issue overlaps the previous copy kernel's end
   std::map<uint32_t, mpt::TuneEntry> tuned;  // tune_key -> choice
   // tuner scratch (grown on demand)
   void* tune_a = nullptr;

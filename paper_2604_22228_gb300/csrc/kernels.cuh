@@ -40,7 +40,7 @@ struct CopyArgs {
 };
 
 // Fill `a` for up to kInlineRanges ranges with the tiling of `variant` (0 vec128,
-// 1 bulk, 2 zero-copy).  Returns kArgsOk, kArgsNeedVec when a bulk launch must fall
+// 1 bulk, 2 zero-copy, 3 vec128 with 8 KiB tiles).  Returns kArgsOk, kArgsNeedVec when a bulk launch must fall
 // back to vec128 (source and destination differ modulo 16, which cp.async.bulk cannot
 // copy), or kArgsTooLarge.
 constexpr int kArgsOk = 0, kArgsNeedVec = 1, kArgsTooLarge = 2;
@@ -51,6 +51,8 @@ int make_copy_args(CopyArgs& a, const void* src, void* dst, const RangeDesc* ran
 // (RangeDesc.shift != 0); the plain ones are leaner and need every shift to be 0.
 __global__ void k_sm_copy_vec(CopyArgs a);
 __global__ void k_sm_copy_vec_any(CopyArgs a);
+__global__ void k_sm_copy_vec8k(CopyArgs a);
+__global__ void k_sm_copy_vec8k_any(CopyArgs a);
 __global__ void k_sm_copy_bulk(CopyArgs a);
 __global__ void k_zc_copy(CopyArgs a);
 __global__ void k_zc_copy_any(CopyArgs a);

@@ -121,6 +121,8 @@ std::vector<RangeDesc> path_ranges(const mpt_plan_s* plan, uint32_t p) {
 void* kernel_fn(int variant, bool any_shift) {
   if (variant == 1) return reinterpret_cast<void*>(&k_sm_copy_bulk);
   if (variant == 2) return any_shift ? reinterpret_cast<void*>(&k_zc_copy_any) : reinterpret_cast<void*>(&k_zc_copy);
+  if (variant == 3)
+    return any_shift ? reinterpret_cast<void*>(&k_sm_copy_vec8k_any) : reinterpret_cast<void*>(&k_sm_copy_vec8k);
   return any_shift ? reinterpret_cast<void*>(&k_sm_copy_vec_any) : reinterpret_cast<void*>(&k_sm_copy_vec);
 }
 
@@ -159,11 +161,28 @@ mpt_status add_copy_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndep
   return MPT_OK;
 }
 
-mpt_status launch_copy(cudaStream_t s, int variant, const CopyArgs& a, uint32_t ctas) {
+// `pdl`: launch with programmatic stream serialization, so that the kernel's launch overlaps
+// the end of a copy kernel before it on the stream (the kernels wait for that kernel's
+// completion before touching memory).  Not used inside a stream capture.
+mpt_status launch_copy(cudaStream_t s, int variant, const CopyArgs& a, uint32_t ctas, bool pdl = false) {
   void* kfn = kernel_fn(variant, a.any_shift != 0);
   CopyArgs args = a;
   void* params[] = {&args};
-  CUDA_TRY(cudaLaunchKernel(kfn, grid_for(a, ctas), dim3(block_for(variant)), params, smem_for(variant), s));
+  if (!pdl) {
+    CUDA_TRY(cudaLaunchKernel(kfn, grid_for(a, ctas), dim3(block_for(variant)), params, smem_for(variant), s));
+    return MPT_OK;
+  }
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid_for(a, ctas);
+  cfg.blockDim = dim3(block_for(variant));
+  cfg.dynamicSmemBytes = smem_for(variant);
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  CUDA_TRY(cudaLaunchKernelExC(&cfg, kfn, params));
   return MPT_OK;
 }
 
@@ -173,7 +192,7 @@ mpt_status for_each_copy(mpt_ctx_t c, const mpt_plan_s* plan, uint32_t p, const 
                          Emit emit) {
   const mpt_path_spec& spec = plan->paths[p];
   std::vector<RangeDesc> ranges = path_ranges(plan, p);
-  int base_variant = spec.kind == MPT_PATH_ZC ? 2 : (spec.flags & MPT_SM_BULK ? 1 : 0);
+  int base_variant = spec.kind == MPT_PATH_ZC ? 2 : (spec.flags & MPT_SM_BULK ? 1 : (spec.flags & MPT_SM_TILE8K ? 3 : 0));
   for (size_t i = 0; i < ranges.size(); i += kInlineRanges) {
     int n = (int)std::min<size_t>(kInlineRanges, ranges.size() - i);
     int variant = base_variant;
@@ -488,8 +507,18 @@ mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src
       }
       return MPT_OK;
     }
-    return for_each_copy(c, plan, only, src, dst,
-                         [&](int variant, const CopyArgs& a, uint32_t ctas) { return launch_copy(user, variant, a, ctas); });
+    bool pdl = c->pdl;
+    if (pdl) {
+      cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+      if (cudaStreamIsCapturing(user, &cap) != cudaSuccess) {
+        cudaGetLastError();
+        pdl = false;
+      }
+      if (cap != cudaStreamCaptureStatusNone) pdl = false;
+    }
+    return for_each_copy(c, plan, only, src, dst, [&](int variant, const CopyArgs& a, uint32_t ctas) {
+      return launch_copy(user, variant, a, ctas, pdl);
+    });
   }
   // A staged path allocates its staging on first use, which a stream capture forbids: refuse
   // before anything is issued, so the caller's capture stays intact.
@@ -676,6 +705,7 @@ mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out) {
   c->stage_max = std::max<uint64_t>(4096, env_u64("MPT_STAGE_BYTES", 8ull << 20));
   c->rebind_enabled = env_u64("MPT_GRAPH_REBIND", 1) != 0;
   c->trace_lanes = env_u64("MPT_TRACE_LANES", 0) != 0;
+  c->pdl = env_u64("MPT_PDL", 1) != 0;
   const char* tf = tune_file && *tune_file ? tune_file : std::getenv("MPT_TUNE_FILE");
   if (tf && *tf) {
     mpt_status st = mpt_tune_load(c, tf);
@@ -962,7 +992,7 @@ mpt_status mpt_launch_eager(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void*
 mpt_status mpt_sm_copy(mpt_ctx_t c, void* dst, const void* src, uint64_t nbytes, uint32_t variant, uint32_t ctas,
                        void* stream) {
   if (!c) return fail(MPT_EINVAL, "mpt_sm_copy: NULL context");
-  if (variant > MPT_SM_BULK) return fail(MPT_EINVAL, "mpt_sm_copy: unknown variant %u", variant);
+  if (variant > MPT_SM_TILE8K) return fail(MPT_EINVAL, "mpt_sm_copy: unknown variant %u", variant);
   if (nbytes == 0) return MPT_OK;
   if (!dst || !src) return fail(MPT_EINVAL, "mpt_sm_copy: NULL pointer");
   CUDA_TRY(cudaSetDevice(c->device));
@@ -971,7 +1001,7 @@ mpt_status mpt_sm_copy(mpt_ctx_t c, void* dst, const void* src, uint64_t nbytes,
     return fail(MPT_EINVAL, "mpt_sm_copy: pointers must be device or host memory the GPU can reach");
   const bool host = ks != kMemDevice || kd != kMemDevice;
   RangeDesc r{0, 0, nbytes, 0, 0};
-  int v = host ? 2 : (int)variant;
+  int v = host ? 2 : (variant == MPT_SM_TILE8K ? 3 : (int)variant);
   CopyArgs a;
   mpt_status st = prepare_copy(a, v, src, dst, &r, 1, c->d_status);
   if (st != MPT_OK) return st;

@@ -67,7 +67,7 @@ SIZES = [1, 15, 16, 17, 255, 4096, 65536 + 3, MiB + 5, 3 * 48 * 1024 + 7, 5 * Mi
 OFFSETS = [(0, 0), (1, 1), (3, 3), (8, 8), (15, 15), (0, 1), (5, 9), (16, 0)]
 
 
-@pytest.mark.parametrize("variant", [mpt.MPT_SM_VEC128, mpt.MPT_SM_BULK])
+@pytest.mark.parametrize("variant", [mpt.MPT_SM_VEC128, mpt.MPT_SM_BULK, mpt.MPT_SM_TILE8K])
 def test_sm_copy_kernel_sizes_and_alignment(ctx, variant):
     import torch
     for n in SIZES:
@@ -86,7 +86,7 @@ def test_sm_copy_kernel_sizes_and_alignment(ctx, variant):
 def test_sm_copy_kernel_grid_sizes(ctx, ctas):
     import torch
     n = 7 * MiB + 333
-    for variant in (mpt.MPT_SM_VEC128, mpt.MPT_SM_BULK):
+    for variant in (mpt.MPT_SM_VEC128, mpt.MPT_SM_BULK, mpt.MPT_SM_TILE8K):
         src, dst = Buf(n, "dev"), Buf(n, "dev")
         data = seeded("f32", 9, n)
         src.fill(data)
@@ -103,13 +103,15 @@ def test_copy64_graph_two_paths(ctx):
 
 
 @pytest.mark.parametrize("mode", ["graph", "eager"])
-@pytest.mark.parametrize("pathset", ["ce", "sm", "sm_bulk", "ce+sm", "hs", "ce+sm+hs"])
+@pytest.mark.parametrize("pathset", ["ce", "sm", "sm_bulk", "sm_8k", "ce+sm", "ce+sm_8k", "hs", "ce+sm+hs"])
 def test_d2d_paths(ctx, mode, pathset):
     sets = {
         "ce": [(P.CE, 65536, MiB)],
         "sm": [(P.SM, 65536, MiB)],
         "sm_bulk": [(P.SM, 65536, MiB, 0, mpt.MPT_SM_BULK)],
+        "sm_8k": [(P.SM, 65536, MiB, 0, mpt.MPT_SM_TILE8K)],
         "ce+sm": [(P.CE, 20000, MiB), (P.SM, 45536, 256 * 1024)],
+        "ce+sm_8k": [(P.CE, 20000, MiB), (P.SM, 45536, 256 * 1024, 7, mpt.MPT_SM_TILE8K)],
         "hs": [(P.HS, 65536, MiB)],
         "ce+sm+hs": [(P.CE, 30000, MiB), (P.SM, 30000, MiB, 0, mpt.MPT_SM_BULK), (P.HS, 5536, 512 * 1024)],
     }
