@@ -218,6 +218,47 @@ def cpu_oracle_sample(plans, budget_s=10.0, max_bytes=256 * MiB):
     return moved / el / 1e9, el, moved, desc
 
 
+def _cpu_oracle_part(job):
+    """One worker of the all-cores oracle sample: the oracle (planner + memcpy) on part w of P
+    contiguous parts of every sweep message up to max_bytes, repeated for budget_s."""
+    w, nparts, budget_s, max_bytes = job
+    import payload
+    from oracle import planner as OP
+    from oracle import transfer as OT
+    sizes = [n for n in SIZES if n <= max_bytes]
+    parts = [(n * w // nparts, n * (w + 1) // nparts) for n in sizes]
+    top = max(b - a for a, b in parts)
+    src = payload.fill_window("f32", SEED, max_bytes * w // nparts, max(16, top))
+    moved, reps = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        for n, (a, b) in zip(sizes, parts):
+            OP.plan(n, OP.D2D, [(OP.SM, 65536, max(16, n))], 16, OP.CONTIG)
+            if b > a:
+                out = OT.copy(src[:b - a])
+                moved += out.size
+        reps += 1
+        if time.perf_counter() - t0 >= budget_s:
+            break
+    return moved, time.perf_counter() - t0, reps
+
+
+def cpu_oracle_all_cores(budget_s=5.0, max_bytes=256 * MiB):
+    """The same oracle sample on every host core: one spawned worker process per core, each on
+    its contiguous part of every message.  Returns (GB/s, cores, description)."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        res = pool.map(_cpu_oracle_part, [(w, cores, budget_s, max_bytes) for w in range(cores)])
+    moved = sum(r[0] for r in res)
+    el = max(r[1] for r in res)
+    reps = min(r[2] for r in res)
+    desc = (f"{cores} worker processes, each the oracle (plan + numpy memcpy) on its 1/{cores} "
+            f"contiguous part of every sweep size 8 B..{max_bytes >> 20} MiB, >= {reps} passes")
+    return moved / el / 1e9, cores, desc
+
+
 def run_reference(args):
     world, rank, _ = dist_setup()
     if rank != 0:
@@ -418,6 +459,21 @@ def run_ours(args):
                 mpt.mpt_plan_destroy(p)
         eager_plans = [mpt.mpt_plan(ctx, n, mpt.MPT_D2D, None, 16, mpt.MPT_PLAN_EAGER) for n in SIZES]
         base["tuned_eager"] = time_eager(eager_plans, reps)
+        # back to back, K launches per size (per-transfer time), each set as graph and direct issue
+        b2b_sets = {"tuned": (tuned_plans, eager_plans)}
+        for kind in ("ce", "sm"):
+            b2b_sets[kind] = ([make_plan(n, kind) for n in SIZES], None)
+        for name, (gplans, eplans) in b2b_sets.items():
+            eplans = eplans or gplans
+            for mode, plans in (("graph", gplans), ("eager", eplans)):
+                pm = mpt.MPT_PREPARE_GRAPH if mode == "graph" else mpt.MPT_PREPARE_EAGER
+                hs = [mpt.mpt_prepare(ctx, p, base_d + o, base_s + o, pm) for p, o in zip(plans, offs)]
+                base[f"b2b_{name}_{mode}"] = time_back_to_back(mpt, torch, stream, hs, args.b2b_max_launches)
+                for h in hs:
+                    mpt.mpt_graph_release(h)
+            if name != "tuned":
+                for p in gplans:
+                    mpt.mpt_plan_destroy(p)
         for p in eager_plans:
             mpt.mpt_plan_destroy(p)
 
@@ -519,6 +575,10 @@ def run_ours(args):
             mpt.mpt_plan_destroy(p)
         del src2, dst2
 
+    config1 = None
+    if not args.no_baselines:
+        config1 = run_config1(mpt, torch, ctx, stream)
+        ok = ok and config1["parity_ok"]
     lifecycle = run_graph_lifecycle(mpt, torch, ctx, stream)
     windows = None if args.no_windows else run_windows(mpt, torch, ctx)
     jacobi = None if args.no_jacobi else run_jacobi(mpt, torch, ctx)
@@ -542,6 +602,9 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_cpu:
         gbs, el, moved, desc = cpu_oracle_sample({}, budget_s=args.cpu_seconds)
         cpu = {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc}
+        if args.cpu_all_cores_seconds > 0:
+            g_all, n_all, d_all = cpu_oracle_all_cores(args.cpu_all_cores_seconds)
+            cpu["all_cores"] = {"value": round(g_all, 3), "unit": "GB/s", "cores": n_all, "sample": d_all}
 
     sweep = []
     for i, n in enumerate(SIZES):
@@ -559,6 +622,11 @@ def run_ours(args):
                 "tuned_eager_gbs": gb(base["tuned_eager"][i]), "best_single_gbs": gb(best_single),
                 "tuned_vs_best_single": round(best_single / base["tuned"][i], 3),
                 "tuned_graph_vs_tuned_eager": round(base["tuned_eager"][i] / base["tuned"][i], 3)})
+            b2b = {f"{k}_{m}": base[f"b2b_{k}_{m}"][i] for k in ("tuned", "ce", "sm") for m in ("graph", "eager")}
+            row["b2b_gbs"] = {k: gb(v) for k, v in b2b.items()}
+            best_b2b_single = min(v for k, v in b2b.items() if not k.startswith("tuned"))
+            best_b2b_tuned = min(b2b["tuned_graph"], b2b["tuned_eager"])
+            row["b2b_tuned_vs_best_single"] = round(best_b2b_single / best_b2b_tuned, 3)
         sweep.append(row)
 
     traffic = roofline_traffic("vec" if variant == 0 else "bulk", ctas)
@@ -584,11 +652,78 @@ def run_ours(args):
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": kernels_per_step * args.steps,
             "clocks": clk, "parity_ok": ok, "host_elapsed_s": round(host_elapsed, 4), "tune_s": round(tune_s, 2),
             "batched": batched, "serving": serving, "host_sweep": host_sweep, "graph_lifecycle": lifecycle,
-            "windows": windows, "jacobi": jacobi,
+            "windows": windows, "jacobi": jacobi, "config1_64MiB": config1,
             "sweep": sweep, "wall_s": round(time.perf_counter() - t_wall0, 2),
         }
         print(json.dumps(line), flush=True)
     return 0 if ok else 1
+
+
+def run_config1(mpt, torch, ctx, stream, replays=100, warm=10):
+    """The 64 MiB worked configuration: one uint8 message (seed 0x5EED0001) over copy engine +
+    SM kernel at 50/50 with 4 MiB chunks in one graph, against each path alone.  10 warm-up
+    replays, then `replays` replays each bracketed by CUDA events, a 256 MiB write before each
+    so that every replay starts with a cold L2.  Median and mean per replay."""
+    import statistics
+    import payload
+    n = 64 * MiB
+    src = torch.from_numpy(payload.fill("u8", payload.SEED_COPY64, n)).to("cuda")
+    dst = torch.zeros_like(src)
+    flush = torch.empty(256 * MiB, dtype=torch.uint8, device="cuda")
+    sets = {"ce+sm_50_50": [(mpt.MPT_PATH_CE, 32768, 4 * MiB), (mpt.MPT_PATH_SM, 32768, 4 * MiB)],
+            "ce": [(mpt.MPT_PATH_CE, 65536, 4 * MiB)], "sm": [(mpt.MPT_PATH_SM, 65536, 4 * MiB)]}
+    out = {"bytes": n, "replays": replays, "warmup": warm, "l2": "256 MiB write before every replay"}
+    ok = True
+    for name, specs in sets.items():
+        plan = mpt.mpt_plan(ctx, n, mpt.MPT_D2D, specs)
+        g = mpt.mpt_capture(ctx, plan, dst.data_ptr(), src.data_ptr())
+        info = mpt.mpt_graph_get_info(g)
+        for _ in range(warm):
+            mpt.mpt_launch(g, stream)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(replays)]
+        with torch.cuda.stream(stream):
+            for r, (a, b) in enumerate(ev):
+                flush.fill_(r & 0xFF)
+                a.record(stream)
+                mpt.mpt_launch(g, stream)
+                b.record(stream)
+        stream.synchronize()
+        us = [a.elapsed_time(b) * 1e3 for a, b in ev]
+        med, mean = statistics.median(us), statistics.fmean(us)
+        out[name] = {"median_us": round(med, 2), "mean_us": round(mean, 2),
+                     "median_gbs": round(n / med / 1e3, 1), "mean_gbs": round(n / mean / 1e3, 1),
+                     "memcpy_nodes": info["memcpy_nodes"], "kernel_nodes": info["kernel_nodes"]}
+        ok = ok and mpt.mpt_hash_device(ctx, dst.data_ptr(), n) == mpt.mpt_hash_device(ctx, src.data_ptr(), n)
+        dst.zero_()
+        mpt.mpt_graph_release(g)
+        mpt.mpt_plan_destroy(plan)
+    best = min(out["ce"]["median_us"], out["sm"]["median_us"])
+    out["split_vs_best_single"] = round(best / out["ce+sm_50_50"]["median_us"], 3)
+    out["parity_ok"] = bool(ok)
+    del flush
+    return out
+
+
+def time_back_to_back(mpt, torch, stream, handles, max_k=10000):
+    """Per-transfer time of K launches of one handle back to back, K = max(1, 2^26 / N) capped
+    at max_k (median of 3 runs when K = 1): the regime of a stream of messages of one size
+    over the same buffers (L2-warm below about 64 MiB)."""
+    import statistics
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = []
+    for n, h in zip(SIZES, handles):
+        k = max(1, min(max_k, (1 << 26) // n))
+        ts = []
+        for _ in range(3 if k == 1 else 1):
+            mpt.mpt_launch(h, stream)
+            e0.record(stream)
+            for _ in range(k):
+                mpt.mpt_launch(h, stream)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) / k)
+        out.append(statistics.median(ts))
+    return out
 
 
 def _percentile(xs, q):
@@ -1079,7 +1214,7 @@ def run_kernel_only(args):
         a = torch.empty(n, dtype=torch.uint8, device="cuda")
     b = torch.empty(n, dtype=torch.uint8, device="cuda")
     a.fill_(7)
-    variant = mpt.MPT_SM_BULK if args.kernel_only == "bulk" else mpt.MPT_SM_VEC128
+    variant = {"bulk": mpt.MPT_SM_BULK, "vec8k": mpt.MPT_SM_TILE8K}.get(args.kernel_only, mpt.MPT_SM_VEC128)
     s = torch.cuda.Stream()
     for _ in range(args.warmup):
         mpt.mpt_sm_copy(ctx, b.data_ptr(), a.data_ptr(), n, variant, args.kernel_ctas, s)
@@ -1111,6 +1246,10 @@ def main(argv=None):
     ap.add_argument("--kernel-launches", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--b2b-max-launches", type=int, default=10000,
+                    help="cap on K back-to-back launches per size in the per-transfer sweep")
+    ap.add_argument("--cpu-all-cores-seconds", type=float, default=5.0,
+                    help="oracle sample on every host core (0 skips it)")
     ap.add_argument("--e2e-plan", choices=["tuned", "ce"], default="ce",
                     help="plans of the end-to-end link legs: tuned, or copy engines only")
     ap.add_argument("--no-cpu", action="store_true")
@@ -1124,7 +1263,7 @@ def main(argv=None):
     ap.add_argument("--tune", choices=["online", "model"], default="online",
                     help="online: measure every size bucket with mpt_tune before capturing; model: cost model only")
     ap.add_argument("--tune-out", default=None, help="write the tuned table (JSON lines) here")
-    ap.add_argument("--kernel-only", choices=["vec", "bulk", "zc"], default=None,
+    ap.add_argument("--kernel-only", choices=["vec", "vec8k", "bulk", "zc"], default=None,
                     help="time one copy kernel alone on --kernel-bytes (profiling)")
     ap.add_argument("--kernel-bytes", type=int, default=256 * MiB)
     ap.add_argument("--kernel-ctas", type=int, default=0)
