@@ -583,9 +583,12 @@ def run_ours(args):
     windows = None if args.no_windows else run_windows(mpt, torch, ctx)
     jacobi = None if args.no_jacobi else run_jacobi(mpt, torch, ctx)
     host_sweep = None
+    pageable = None
     if not args.no_host_sweep:
         host_sweep = run_host_sweep(mpt, torch, ctx, stream)
         ok = ok and host_sweep["parity_ok"]
+        pageable = run_pageable_sweep(mpt, torch, ctx, stream)
+        ok = ok and pageable["parity_ok"]
     batched = None
     if not args.no_batched:
         batched = run_batched(mpt, torch, ctx, stream)
@@ -652,11 +655,79 @@ def run_ours(args):
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": kernels_per_step * args.steps,
             "clocks": clk, "parity_ok": ok, "host_elapsed_s": round(host_elapsed, 4), "tune_s": round(tune_s, 2),
             "batched": batched, "serving": serving, "host_sweep": host_sweep, "graph_lifecycle": lifecycle,
-            "windows": windows, "jacobi": jacobi, "config1_64MiB": config1,
+            "windows": windows, "jacobi": jacobi, "config1_64MiB": config1, "pageable_host": pageable,
             "sweep": sweep, "wall_s": round(time.perf_counter() - t_wall0, 2),
         }
         print(json.dumps(line), flush=True)
     return 0 if ok else 1
+
+
+def run_pageable_sweep(mpt, torch, ctx, stream, sizes=(4 * MiB, 16 * MiB, 64 * MiB, 256 * MiB, 1024 * MiB),
+                       reps=3, stage_chunk=8 * MiB):
+    """Host<->device transfers of ordinary (pageable, not page-locked) host memory, the case
+    NEXT-4 names: each single route -- torch's own copy (the driver's pageable path), the
+    zero-copy kernel reading/writing the pageable buffer directly, host-thread staging
+    (CPU hop into page-locked slots + copy-engine hop) -- against zero-copy + host-thread
+    splits, all as graphs, median of `reps` runs with CUDA events around each."""
+    import statistics
+    import payload
+    top = max(sizes)
+    host = torch.empty(top, dtype=torch.uint8)             # pageable
+    base = torch.from_numpy(payload.fill("u32", payload.SEED_HOST_SWEEP, 64 * MiB))
+    for o in range(0, top, 64 * MiB):
+        host[o:o + 64 * MiB].copy_(base[:min(64 * MiB, top - o)])
+    back = torch.zeros(top, dtype=torch.uint8)              # pageable, pages touched
+    dev = torch.empty(top, dtype=torch.uint8, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        fn()
+        ts = []
+        for _ in range(reps):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    HT = mpt.MPT_HS_HOST_THREADS
+    rows = []
+    zc_ok = bool(mpt.mpt_ctx_info(ctx)["pageable_access"])
+    for n in sizes:
+        row = {"bytes": n}
+        for direction, name in ((mpt.MPT_H2D, "h2d"), (mpt.MPT_D2H, "d2h")):
+            src = host if direction == mpt.MPT_H2D else dev
+            dst = dev if direction == mpt.MPT_H2D else back
+
+            def driver():
+                with torch.cuda.stream(stream):
+                    dst[:n].copy_(src[:n], non_blocking=False)
+            row[f"{name}_driver_gbs"] = round(n / (timed(driver) / 1e3) / 1e9, 2)
+            sets = {"ht": [(mpt.MPT_PATH_HS, 65536, stage_chunk, 0, HT)]}
+            if zc_ok:
+                sets["zc"] = [(mpt.MPT_PATH_ZC, 65536, 64 * MiB)]
+                for w in (16384, 32768, 49152):
+                    sets[f"zc{w * 100 // 65536}+ht"] = [(mpt.MPT_PATH_ZC, w, 64 * MiB),
+                                                       (mpt.MPT_PATH_HS, 65536 - w, stage_chunk, 0, HT)]
+            for label, specs in sets.items():
+                plan = mpt.mpt_plan(ctx, n, direction, specs)
+                g = mpt.mpt_capture(ctx, plan, dst.data_ptr(), src.data_ptr())
+                ms = timed(lambda: mpt.mpt_launch(g, stream))
+                row[f"{name}_{label}_gbs"] = round(n / (ms / 1e3) / 1e9, 2)
+                mpt.mpt_graph_release(g)
+                mpt.mpt_plan_destroy(plan)
+            single = [row[f"{name}_{k}_gbs"] for k in ("driver", "zc", "ht") if f"{name}_{k}_gbs" in row]
+            multi = [v for k, v in row.items() if k.startswith(name) and "+ht" in k]
+            row[f"{name}_best_single_gbs"] = max(single)
+            if multi:
+                row[f"{name}_best_multi_vs_best_single"] = round(max(multi) / max(single), 3)
+        rows.append(row)
+    stream.synchronize()
+    ok = bool(torch.equal(back[:n], host[:n]))
+    return {"rows": rows, "parity_ok": ok, "stage_chunk": stage_chunk,
+            "host_threads": "MPT_HOST_THREADS workers + the host-function thread",
+            "note": "GB/s of message bytes; host buffers pageable (torch CPU tensors, not pinned)"}
 
 
 def run_config1(mpt, torch, ctx, stream, replays=100, warm=10):

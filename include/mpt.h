@@ -77,6 +77,12 @@ typedef enum { MPT_MODE_GRAPH = 0, MPT_MODE_EAGER = 1 } mpt_mode;
 #define MPT_SM_BULK 1u     /* cp.async.bulk global->shared->global ring per CTA */
 #define MPT_SM_TILE8K 2u   /* VEC128 over 8 KiB tiles: a message of a few MiB reaches every SM
                               (BULK takes precedence when both are set) */
+/* mpt_path_spec.flags for MPT_PATH_HS in H2D/D2H: host-thread staging.  The host side of each
+ * chunk is a CPU copy, by the context's pool of host threads, between the caller's host buffer
+ * and a page-locked slot; the device side is a copy-engine hop between the slot and device
+ * memory (two slots, hop two of a chunk after its hop one, a slot refilled after its previous
+ * hop two; Algorithm 2 StageHostCopy with a CPU hop).  The host buffer may be pageable. */
+#define MPT_HS_HOST_THREADS 1u
 
 /* One path of a plan.
  *   kind         one mpt_path_kind; allowed kinds per direction:
@@ -126,6 +132,7 @@ typedef struct {
   double update_us;        /* last in-place retarget (mpt_graph_rebind or a capture that reused it) */
   uint32_t rebinds;        /* in-place retargets so far */
   uint32_t mode;           /* 0: a CUDA graph; 1: prepared for direct issue (mpt_prepare) */
+  uint32_t host_nodes;     /* CPU hops of host-thread staging */
 } mpt_graph_info;
 
 /* Cost model of one path kind: per-chunk issue latency and bandwidth (the staged path's

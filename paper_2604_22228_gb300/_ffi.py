@@ -21,6 +21,7 @@ MPT_D2D, MPT_H2D, MPT_D2H = 0, 1, 2
 MPT_PATH_CE, MPT_PATH_SM, MPT_PATH_HS, MPT_PATH_ZC = 1, 2, 4, 8
 MPT_LAYOUT_CONTIG, MPT_LAYOUT_INTERLEAVE = 0, 1
 MPT_SM_VEC128, MPT_SM_BULK, MPT_SM_TILE8K = 0, 1, 2
+MPT_HS_HOST_THREADS = 1
 MPT_PLAN_EAGER = 0x100
 MPT_MODE_GRAPH, MPT_MODE_EAGER = 0, 1
 MPT_PREPARE_GRAPH, MPT_PREPARE_EAGER, MPT_PREPARE_AUTO = 0, 1, 2
@@ -49,7 +50,7 @@ class mpt_graph_info(C.Structure):
     _fields_ = [("nodes", C.c_uint32), ("memcpy_nodes", C.c_uint32), ("kernel_nodes", C.c_uint32),
                 ("memset_nodes", C.c_uint32), ("create_us", C.c_double), ("construct_us", C.c_double),
                 ("instantiate_us", C.c_double), ("staging_bytes", C.c_uint64), ("update_us", C.c_double),
-                ("rebinds", C.c_uint32), ("mode", C.c_uint32)]
+                ("rebinds", C.c_uint32), ("mode", C.c_uint32), ("host_nodes", C.c_uint32)]
 
 
 class mpt_path_model(C.Structure):

@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "libmpt.so")
 OBJDIR = os.path.join(PKG, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["copy_kernels.cu", "runtime.cu", "planner.cpp", "api_plan.cpp", "model.cpp", "tuner.cu", "batch.cu", "serve.cu", "jacobi.cu", "noalloc.cu"]
+SOURCES = ["copy_kernels.cu", "runtime.cu", "planner.cpp", "api_plan.cpp", "model.cpp", "tuner.cu", "batch.cu", "serve.cu", "jacobi.cu", "noalloc.cu", "host_pool.cpp"]
 
 
 def _nvcc() -> str:
@@ -40,7 +40,7 @@ def _compile(nvcc: str, src: str) -> str:
 def build(force: bool = False) -> str:
     """Compile every source and link libmpt.so; returns its path."""
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, h) for h in ("kernels.cuh", "copy_device.cuh", "internal.h", "ctx.h")] + [os.path.join(INCLUDE, "mpt.h")]
+    deps = srcs + [os.path.join(CSRC, h) for h in ("kernels.cuh", "copy_device.cuh", "internal.h", "ctx.h", "host_pool.h")] + [os.path.join(INCLUDE, "mpt.h")]
     if not force and os.path.exists(OUT):
         newest = max(os.path.getmtime(d) for d in deps)
         if os.path.getmtime(OUT) >= newest:

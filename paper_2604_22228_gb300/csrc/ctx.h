@@ -2,10 +2,12 @@
 #pragma once
 #include <list>
 #include <map>
+#include <memory>
 #include <unordered_map>
 #include <unordered_set>
 #include <vector>
 
+#include "host_pool.h"
 #include "internal.h"
 #include "kernels.cuh"
 
@@ -91,6 +93,7 @@ struct mpt_graph_s {
   bool cached = false;
   std::list<mpt_graph_s*>::iterator lru_it;
   mpt_plan_s* eager_plan = nullptr;  // set when prepared for direct issue instead of a graph
+  std::vector<std::unique_ptr<mpt::HostCopyJob>> host_jobs;  // userData of this graph's host nodes
 };
 
 struct mpt_ctx_s {
@@ -111,6 +114,8 @@ struct mpt_ctx_s {
   bool trace_lanes = false;    // time every lane of multi-path eager launches
   uint32_t traced = 0;         // lanes timed by the last such launch
   bool pdl = true;             // direct kernel issue overlaps the previous copy kernel's end
+  std::unique_ptr<mpt::HostCopyPool> host_pool;  // CPU hops of host-thread staging (made on first use)
+  unsigned host_threads = 0;   // pool workers (MPT_HOST_THREADS; 0 = min(16, cores) - 1)
   std::map<uint32_t, mpt::TuneEntry> tuned;  // tune_key -> choice
   // tuner scratch (grown on demand)
   void* tune_a = nullptr;

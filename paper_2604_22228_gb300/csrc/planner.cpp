@@ -74,6 +74,8 @@ mpt_status build_chunks(uint64_t nbytes, uint32_t dir, const mpt_path_spec* path
     if (!kind_allowed(dir, s.kind))
       return fail(MPT_EINVAL, "mpt_plan: path %u kind %u cannot carry direction %u", p, s.kind, dir);
     if (s.share == 0) return fail(MPT_EINVAL, "mpt_plan: path %u has a zero share", p);
+    if (s.kind == MPT_PATH_HS && (s.flags & MPT_HS_HOST_THREADS) && dir == MPT_D2D)
+      return fail(MPT_EINVAL, "mpt_plan: path %u: host-thread staging carries host<->device transfers only", p);
     if (s.chunk_bytes == 0 || s.chunk_bytes % align != 0)
       return fail(MPT_EINVAL, "mpt_plan: path %u chunk %llu is not a positive multiple of %u", p,
                   (unsigned long long)s.chunk_bytes, align);

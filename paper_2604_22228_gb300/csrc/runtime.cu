@@ -11,6 +11,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <list>
+#include <thread>
 #include <unordered_map>
 #include <unordered_set>
 
@@ -71,6 +72,9 @@ namespace {
 void graph_destroy_exec(mpt_graph_s* g) {
   delete g->eager_plan;
   g->eager_plan = nullptr;
+  // A launch still in flight may not have run its host nodes yet: their jobs must outlive it.
+  if (!g->host_jobs.empty()) cudaDeviceSynchronize();
+  g->host_jobs.clear();
   if (g->exec) cudaGraphExecDestroy(g->exec);
   if (g->graph) cudaGraphDestroy(g->graph);
   g->exec = nullptr;
@@ -207,6 +211,43 @@ mpt_status for_each_copy(mpt_ctx_t c, const mpt_plan_s* plan, uint32_t p, const 
   return MPT_OK;
 }
 
+// The context's host copy pool, made on first use: MPT_HOST_THREADS workers, or one fewer
+// than min(16, host cores) -- the thread running the host function copies a part too.
+HostCopyPool* host_pool(mpt_ctx_t c) {
+  if (!c->host_pool) {
+    unsigned w = c->host_threads;
+    if (w == 0) {
+      const unsigned hw = std::max(1u, std::thread::hardware_concurrency());
+      w = std::min(16u, hw) - 1;
+    }
+    try {
+      c->host_pool.reset(new HostCopyPool(w));
+    } catch (...) {
+      return nullptr;
+    }
+  }
+  return c->host_pool.get();
+}
+
+bool host_threads_path(const mpt_path_spec& s) { return s.kind == MPT_PATH_HS && (s.flags & MPT_HS_HOST_THREADS); }
+
+bool has_host_threads(const mpt_plan_s* plan) {
+  for (uint32_t p = 0; p < plan->npaths; ++p)
+    if (plan->first_chunk[p + 1] > plan->first_chunk[p] && host_threads_path(plan->paths[p])) return true;
+  return false;
+}
+
+mpt_status add_host_copy_node(mpt_graph_s* g, HostCopyPool* pool, const cudaGraphNode_t* dep, void* dst,
+                              const void* src, size_t bytes, cudaGraphNode_t* node) {
+  g->host_jobs.emplace_back(new HostCopyJob{pool, dst, src, bytes, false});
+  cudaHostNodeParams hp{};
+  hp.fn = host_copy_fn;
+  hp.userData = g->host_jobs.back().get();
+  CUDA_TRY(cudaGraphAddHostNode(node, g->graph, dep, dep ? 1 : 0, &hp));
+  g->info.host_nodes++;
+  return MPT_OK;
+}
+
 // ---- graph construction (Algorithm 1 CreateGraph, Algorithm 2 node helpers) ---------------
 
 // Build the graph of `plan` for (dst, src) into g->graph and instantiate it (unless
@@ -271,7 +312,41 @@ mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const voi
         if (cb > c->stage_max)
           return fail(MPT_EINVAL, "mpt_capture: staged chunk %llu exceeds the stage size %llu (MPT_STAGE_BYTES)",
                       (unsigned long long)cb, (unsigned long long)c->stage_max);
-        if (plan->dir == MPT_D2D) {
+        if (host_threads_path(spec)) {
+          // Algorithm 2 StageHostCopy with a CPU hop: host buffer <-> pinned slot by the host
+          // thread pool, slot <-> device by a copy engine; two slots, hop two of chunk k after
+          // its hop one, hop one of chunk k+2 after hop two of chunk k.
+          if (reuse) return fail(MPT_ENOTSUP, "rebind: host-thread staging is not retargeted in place");
+          HostCopyPool* pool = host_pool(c);
+          if (!pool) return fail(MPT_ENOMEM, "mpt_capture: host copy threads");
+          void* stage = nullptr;
+          mpt_status sa = get_host(2 * cb, &stage);
+          if (sa != MPT_OK) return sa;
+          info.staging_bytes += 2 * cb;
+          uint8_t* st8 = static_cast<uint8_t*>(stage);
+          cudaGraphNode_t prev_hop2[2] = {nullptr, nullptr};
+          for (uint32_t i = lo; i < hi; ++i) {
+            const mpt_chunk& ch = plan->chunks[i];
+            const uint32_t slot = (i - lo) & 1u;
+            uint8_t* sl = st8 + slot * cb;
+            const cudaGraphNode_t* dep = prev_hop2[slot] ? &prev_hop2[slot] : nullptr;
+            cudaGraphNode_t h1, h2;
+            mpt_status st;
+            if (plan->dir == MPT_H2D) {
+              st = add_host_copy_node(g, pool, dep, sl, s8 + ch.offset, ch.bytes, &h1);
+              if (st != MPT_OK) return st;
+              CUDA_TRY(cudaGraphAddMemcpyNode1D(&h2, g->graph, &h1, 1, d8 + ch.offset, sl, ch.bytes,
+                                                cudaMemcpyHostToDevice));
+            } else {
+              CUDA_TRY(cudaGraphAddMemcpyNode1D(&h1, g->graph, dep, dep ? 1 : 0, sl, s8 + ch.offset, ch.bytes,
+                                                cudaMemcpyDeviceToHost));
+              st = add_host_copy_node(g, pool, &h1, d8 + ch.offset, sl, ch.bytes, &h2);
+              if (st != MPT_OK) return st;
+            }
+            info.memcpy_nodes++;
+            prev_hop2[slot] = h2;
+          }
+        } else if (plan->dir == MPT_D2D) {
           // Algorithm 2 StageHostCopy: device -> pinned host slot -> device, two slots;
           // hop two of chunk k after its hop one, hop one of chunk k+2 after hop two of k.
           void* stage = nullptr;
@@ -400,11 +475,10 @@ mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const voi
   return MPT_OK;
 }
 
-// Pointer kinds must fit the direction.  Host sides must be page-locked, except that plans
-// made only of zero-copy paths may use pageable host memory on devices that can reach it
-// (zero_copy_only: every non-empty path of the plan is MPT_PATH_ZC).
-mpt_status check_pointers(mpt_ctx_t c, uint32_t dir, const void* dst, const void* src, bool zero_copy_only = false) {
-  const bool pg = zero_copy_only && c->pageable;
+// Pointer kinds must fit the direction.  Host sides must be page-locked, except for plans
+// whose paths all reach host memory without a copy engine touching it (pageable_ok).
+mpt_status check_pointers(mpt_ctx_t c, uint32_t dir, const void* dst, const void* src, bool pageable_ok = false) {
+  const bool pg = pageable_ok;
   MemKind ks = classify(src, c->device, pg), kd = classify(dst, c->device, pg);
   if (ks == kMemPageable) ks = kMemHost;
   if (kd == kMemPageable) kd = kMemHost;
@@ -421,9 +495,17 @@ mpt_status check_pointers(mpt_ctx_t c, uint32_t dir, const void* dst, const void
   return MPT_OK;
 }
 
-bool zero_copy_only(const mpt_plan_s* plan) {
-  for (uint32_t p = 0; p < plan->npaths; ++p)
-    if (plan->first_chunk[p + 1] > plan->first_chunk[p] && plan->paths[p].kind != MPT_PATH_ZC) return false;
+// Pageable host memory is allowed when every non-empty path of the plan is the zero-copy
+// kernel (on devices that reach pageable memory: coherent hosts) or host-thread staging (CPU
+// threads touch the host buffer; copy engines only the page-locked slots).
+bool pageable_ok(mpt_ctx_t c, const mpt_plan_s* plan) {
+  for (uint32_t p = 0; p < plan->npaths; ++p) {
+    if (plan->first_chunk[p + 1] == plan->first_chunk[p]) continue;
+    const mpt_path_spec& s = plan->paths[p];
+    if (host_threads_path(s)) continue;
+    if (s.kind == MPT_PATH_ZC && c->pageable) continue;
+    return false;
+  }
   return true;
 }
 
@@ -433,6 +515,8 @@ bool zero_copy_only(const mpt_plan_s* plan) {
 // changes with the new alignment); g is then unchanged.
 mpt_status rebind(mpt_ctx_t c, mpt_graph_s* g, const mpt_plan_s* plan, void* dst, const void* src) {
   const double t0 = now_us();
+  // Host nodes carry their addresses in jobs that a launch in flight may still read.
+  if (has_host_threads(plan)) return fail(MPT_ENOTSUP, "rebind: host-thread staging is not retargeted in place");
   if (!g->exec) {  // empty message: nothing to retarget
     g->info.update_us = now_us() - t0;
     g->info.rebinds++;
@@ -468,9 +552,21 @@ void set_range(mpt_graph_s* g, uint64_t nbytes, const void* dst, const void* src
 
 // ---- eager engine (Sec. 4.3 static runtime pipelining; Sec. 4.5 contention avoidance) ------
 
+// Grow a lane's staging (never shrinks).  Earlier launches on the lane may still use the old
+// buffer: the lane's streams are drained before it is freed.
+mpt_status drain_lane(EagerLane& L) {
+  for (cudaStream_t s : L.s)
+    if (s) CUDA_TRY(cudaStreamSynchronize(s));
+  return MPT_OK;
+}
+
 mpt_status grow_host(EagerLane& L, uint64_t bytes) {
   if (L.host_stage_bytes >= bytes) return MPT_OK;
-  if (L.host_stage) CUDA_TRY(cudaFreeHost(L.host_stage));
+  if (L.host_stage) {
+    mpt_status st = drain_lane(L);
+    if (st != MPT_OK) return st;
+    CUDA_TRY(cudaFreeHost(L.host_stage));
+  }
   L.host_stage = nullptr;
   L.host_stage_bytes = 0;
   CUDA_TRY(cudaHostAlloc(&L.host_stage, bytes, cudaHostAllocPortable));
@@ -480,7 +576,11 @@ mpt_status grow_host(EagerLane& L, uint64_t bytes) {
 
 mpt_status grow_dev(EagerLane& L, uint64_t bytes) {
   if (L.dev_stage_bytes >= bytes) return MPT_OK;
-  if (L.dev_stage) CUDA_TRY(cudaFree(L.dev_stage));
+  if (L.dev_stage) {
+    mpt_status st = drain_lane(L);
+    if (st != MPT_OK) return st;
+    CUDA_TRY(cudaFree(L.dev_stage));
+  }
   L.dev_stage = nullptr;
   L.dev_stage_bytes = 0;
   CUDA_TRY(cudaMalloc(&L.dev_stage, bytes));
@@ -530,6 +630,9 @@ mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src
   }
   if (cap != cudaStreamCaptureStatusActive) capture_id = 0;
   if (cap != cudaStreamCaptureStatusNone) {
+    if (has_host_threads(plan))
+      return fail(MPT_EINVAL, "mpt_launch_eager: host-thread staging cannot be captured from the eager engine "
+                              "(each launch owns its CPU-hop jobs); build the graph with mpt_capture");
     for (uint32_t p = 0; p < plan->npaths; ++p) {
       if (plan->first_chunk[p + 1] == plan->first_chunk[p] || plan->paths[p].kind != MPT_PATH_HS) continue;
       const EagerLane& L = c->lane[p];
@@ -573,6 +676,46 @@ mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src
           return fail(MPT_EINVAL, "mpt_launch_eager: staged chunk %llu exceeds the stage size %llu",
                       (unsigned long long)cb, (unsigned long long)c->stage_max);
         CUDA_TRY(cudaStreamWaitEvent(L.s[1], c->fork, 0));
+        if (host_threads_path(spec)) {
+          HostCopyPool* pool = host_pool(c);
+          if (!pool) return fail(MPT_ENOMEM, "mpt_launch_eager: host copy threads");
+          mpt_status st = grow_host(L, 2 * cb);
+          if (st != MPT_OK) return st;
+          uint8_t* stage = static_cast<uint8_t*>(L.host_stage);
+          auto host_hop = [&](cudaStream_t s, void* to, const void* from, size_t n) -> mpt_status {
+            HostCopyJob* job = new HostCopyJob{pool, to, from, n, true};
+            const cudaError_t e = cudaLaunchHostFunc(s, host_copy_fn, job);
+            if (e != cudaSuccess) {
+              delete job;
+              return fail(MPT_ECUDA, "cudaLaunchHostFunc: %s", cudaGetErrorString(e));
+            }
+            return MPT_OK;
+          };
+          for (uint32_t i = lo; i < hi; ++i) {
+            const mpt_chunk& ch = plan->chunks[i];
+            const uint32_t slot = (i - lo) & 1u;
+            uint8_t* sl = stage + slot * cb;
+            if (L.hop2_capture[slot] == capture_id) CUDA_TRY(cudaStreamWaitEvent(L.s[0], L.hop2[slot], 0));
+            if (plan->dir == MPT_H2D) {
+              st = host_hop(L.s[0], sl, s8 + ch.offset, ch.bytes);
+              if (st != MPT_OK) return st;
+            } else {
+              CUDA_TRY(cudaMemcpyAsync(sl, s8 + ch.offset, ch.bytes, cudaMemcpyDeviceToHost, L.s[0]));
+            }
+            CUDA_TRY(cudaEventRecord(L.hop1[slot], L.s[0]));
+            CUDA_TRY(cudaStreamWaitEvent(L.s[1], L.hop1[slot], 0));
+            if (plan->dir == MPT_H2D) {
+              CUDA_TRY(cudaMemcpyAsync(d8 + ch.offset, sl, ch.bytes, cudaMemcpyHostToDevice, L.s[1]));
+            } else {
+              st = host_hop(L.s[1], d8 + ch.offset, sl, ch.bytes);
+              if (st != MPT_OK) return st;
+            }
+            CUDA_TRY(cudaEventRecord(L.hop2[slot], L.s[1]));
+            L.hop2_capture[slot] = capture_id;
+          }
+          last = L.s[1];
+          break;
+        }
         uint8_t* stage;
         if (plan->dir == MPT_D2D) {
           mpt_status st = grow_host(L, 2 * cb);
@@ -706,6 +849,7 @@ mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out) {
   c->rebind_enabled = env_u64("MPT_GRAPH_REBIND", 1) != 0;
   c->trace_lanes = env_u64("MPT_TRACE_LANES", 0) != 0;
   c->pdl = env_u64("MPT_PDL", 1) != 0;
+  c->host_threads = (unsigned)std::min<uint64_t>(256, env_u64("MPT_HOST_THREADS", 0));
   const char* tf = tune_file && *tune_file ? tune_file : std::getenv("MPT_TUNE_FILE");
   if (tf && *tf) {
     mpt_status st = mpt_tune_load(c, tf);
@@ -827,7 +971,7 @@ mpt_status mpt_capture(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void* src,
   *out = nullptr;
   CUDA_TRY(cudaSetDevice(c->device));
   if (plan->nbytes > 0) {
-    mpt_status st = check_pointers(c, plan->dir, dst, src, zero_copy_only(plan));
+    mpt_status st = check_pointers(c, plan->dir, dst, src, pageable_ok(c, plan));
     if (st != MPT_OK) return st;
   }
   GraphKey key{(uint64_t)(uintptr_t)src, (uint64_t)(uintptr_t)dst, plan->nbytes, plan->dir, plan->hash};
@@ -894,7 +1038,7 @@ mpt_status mpt_prepare(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void* src,
   if (mode == MPT_PREPARE_GRAPH) return mpt_capture(c, plan, dst, src, out);
   CUDA_TRY(cudaSetDevice(c->device));
   if (plan->nbytes > 0) {
-    mpt_status st = check_pointers(c, plan->dir, dst, src, zero_copy_only(plan));
+    mpt_status st = check_pointers(c, plan->dir, dst, src, pageable_ok(c, plan));
     if (st != MPT_OK) return st;
   }
   mpt_graph_s* g = new mpt_graph_s;
@@ -936,7 +1080,7 @@ mpt_status mpt_graph_rebind(mpt_graph_t g, mpt_plan_t plan, void* dst, const voi
     return fail(MPT_EINVAL, "mpt_graph_rebind: the plan is not the one the graph was captured from");
   CUDA_TRY(cudaSetDevice(c->device));
   if (plan->nbytes > 0) {
-    mpt_status st = check_pointers(c, plan->dir, dst, src, zero_copy_only(plan));
+    mpt_status st = check_pointers(c, plan->dir, dst, src, pageable_ok(c, plan));
     if (st != MPT_OK) return st;
   }
   GraphKey key{(uint64_t)(uintptr_t)src, (uint64_t)(uintptr_t)dst, plan->nbytes, plan->dir, plan->hash};
@@ -983,7 +1127,7 @@ mpt_status mpt_launch_eager(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void*
   if (!c || !plan) return fail(MPT_EINVAL, "mpt_launch_eager: NULL argument");
   CUDA_TRY(cudaSetDevice(c->device));
   if (plan->nbytes > 0) {
-    mpt_status st = check_pointers(c, plan->dir, dst, src, zero_copy_only(plan));
+    mpt_status st = check_pointers(c, plan->dir, dst, src, pageable_ok(c, plan));
     if (st != MPT_OK) return st;
   }
   return eager(c, plan, dst, src, static_cast<cudaStream_t>(stream));

@@ -17,6 +17,8 @@ class Buf:
         total = n + 2 * GUARD + 64
         if where == "dev":
             self.t = torch.full((total,), CANARY, dtype=torch.uint8, device="cuda")
+        elif where == "pageable":  # ordinary host memory, not page-locked
+            self.t = torch.full((total,), CANARY, dtype=torch.uint8)
         else:
             self.t = torch.full((total,), CANARY, dtype=torch.uint8).pin_memory()
         self.start = GUARD + offset

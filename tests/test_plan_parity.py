@@ -91,3 +91,16 @@ def test_chunk_count_limit():
     assert "limit" in str(e.value)
     got, _ = lib_plan(mpt.MPT_MAX_CHUNKS * 16, P.D2D, [(P.SM, 65536, 16)])
     assert len(got) == mpt.MPT_MAX_CHUNKS
+
+
+def test_host_thread_staging_is_host_link_only():
+    """MPT_HS_HOST_THREADS has a CPU hop between a host buffer and a page-locked slot: it
+    carries H2D and D2H transfers, and the plan's chunks are those of the oracle (flags do not
+    change the split)."""
+    for direction in (P.H2D, P.D2H):
+        specs = [(P.ZC, 40000, 4096), (P.HS, 25536, 1024, 0, mpt.MPT_HS_HOST_THREADS)]
+        got, _ = lib_plan(100_000 + 7, direction, specs)
+        assert got == P.plan(100_000 + 7, direction, [s[:3] for s in specs], 16, P.CONTIG)
+    with pytest.raises(mpt.MptError) as e:
+        lib_plan(4096, P.D2D, [(P.HS, 65536, 1024, 0, mpt.MPT_HS_HOST_THREADS)])
+    assert e.value.status == mpt.MPT_EINVAL
