@@ -668,7 +668,9 @@ def run_pageable_sweep(mpt, torch, ctx, stream, sizes=(4 * MiB, 16 * MiB, 64 * M
     NEXT-4 names: each single route -- torch's own copy (the driver's pageable path), the
     zero-copy kernel reading/writing the pageable buffer directly, host-thread staging
     (CPU hop into page-locked slots + copy-engine hop) -- against zero-copy + host-thread
-    splits, all as graphs, median of `reps` runs with CUDA events around each."""
+    splits, and the tuner's pageable choice (mpt_tune with MPT_MODE_PAGEABLE, then
+    mpt_plan with MPT_PLAN_PAGEABLE), all as graphs, median of `reps` runs with CUDA events
+    around each."""
     import statistics
     import payload
     top = max(sizes)
@@ -710,8 +712,15 @@ def run_pageable_sweep(mpt, torch, ctx, stream, sizes=(4 * MiB, 16 * MiB, 64 * M
                 for w in (16384, 32768, 49152):
                     sets[f"zc{w * 100 // 65536}+ht"] = [(mpt.MPT_PATH_ZC, w, 64 * MiB),
                                                        (mpt.MPT_PATH_HS, 65536 - w, stage_chunk, 0, HT)]
+            mpt.mpt_tune(ctx, direction, n, mpt.MPT_MODE_GRAPH | mpt.MPT_MODE_PAGEABLE)
+            sets["tuned"] = None
             for label, specs in sets.items():
-                plan = mpt.mpt_plan(ctx, n, direction, specs)
+                if specs is None:
+                    plan = mpt.mpt_plan(ctx, n, direction, None, 16, mpt.MPT_PLAN_PAGEABLE)
+                    row[f"{name}_tuned_plan"] = [(p["kind"], p["share"], p["chunk_bytes"], p["flags"])
+                                                 for p in mpt.mpt_plan_paths(plan)]
+                else:
+                    plan = mpt.mpt_plan(ctx, n, direction, specs)
                 g = mpt.mpt_capture(ctx, plan, dst.data_ptr(), src.data_ptr())
                 ms = timed(lambda: mpt.mpt_launch(g, stream))
                 row[f"{name}_{label}_gbs"] = round(n / (ms / 1e3) / 1e9, 2)
@@ -720,6 +729,7 @@ def run_pageable_sweep(mpt, torch, ctx, stream, sizes=(4 * MiB, 16 * MiB, 64 * M
             single = [row[f"{name}_{k}_gbs"] for k in ("driver", "zc", "ht") if f"{name}_{k}_gbs" in row]
             multi = [v for k, v in row.items() if k.startswith(name) and "+ht" in k]
             row[f"{name}_best_single_gbs"] = max(single)
+            row[f"{name}_tuned_vs_best_single"] = round(row[f"{name}_tuned_gbs"] / max(single), 3)
             if multi:
                 row[f"{name}_best_multi_vs_best_single"] = round(max(multi) / max(single), 3)
         rows.append(row)

@@ -70,7 +70,15 @@ typedef enum { MPT_PATH_CE = 1, MPT_PATH_SM = 2, MPT_PATH_HS = 4, MPT_PATH_ZC = 
 typedef enum { MPT_LAYOUT_CONTIG = 0, MPT_LAYOUT_INTERLEAVE = 1 } mpt_layout;
 /* OR into mpt_plan's layout to ask the tuner for its eager-mode (non-graph) choice. */
 #define MPT_PLAN_EAGER 0x100u
+/* OR into mpt_plan's layout (H2D/D2H) when the host buffer is ordinary pageable memory: the
+ * tuner then chooses among the paths that accept it -- the zero-copy kernel (devices that
+ * reach pageable memory) and host-thread staging -- from entries tuned with
+ * MPT_MODE_PAGEABLE, else zero-copy alone (host-thread staging where the device cannot reach
+ * pageable memory). */
+#define MPT_PLAN_PAGEABLE 0x200u
 typedef enum { MPT_MODE_GRAPH = 0, MPT_MODE_EAGER = 1 } mpt_mode;
+/* OR into mpt_tune's / mpt_tune_get's mode: tune (look up) the pageable-host-memory choice. */
+#define MPT_MODE_PAGEABLE 0x10u
 
 /* mpt_path_spec.flags for SM-kernel paths: which copy kernel variant to run. */
 #define MPT_SM_VEC128 0u   /* 128-bit vector loads/stores, grid-stride over 64 KiB tiles */
@@ -81,7 +89,11 @@ typedef enum { MPT_MODE_GRAPH = 0, MPT_MODE_EAGER = 1 } mpt_mode;
  * chunk is a CPU copy, by the context's pool of host threads, between the caller's host buffer
  * and a page-locked slot; the device side is a copy-engine hop between the slot and device
  * memory (two slots, hop two of a chunk after its hop one, a slot refilled after its previous
- * hop two; Algorithm 2 StageHostCopy with a CPU hop).  The host buffer may be pageable. */
+ * hop two; Algorithm 2 StageHostCopy with a CPU hop).  The host buffer may be pageable.
+ * MPT_HOST_THREADS at context creation sets the pool's worker count (default min(8, cores/2)
+ * - 1; the thread that runs the CUDA host function copies a part as well).  Graphs with
+ * this path are not retargeted in place (mpt_graph_rebind: ENOTSUP), and the eager engine
+ * refuses it inside a stream capture (each eager launch owns its CPU-hop jobs). */
 #define MPT_HS_HOST_THREADS 1u
 
 /* One path of a plan.
@@ -353,7 +365,10 @@ MPT_API mpt_status mpt_model_optimize(const mpt_model* m, uint64_t nbytes, uint3
  * with a cold L2 full of dirty lines (a 256 MiB write first, as after the kernel that
  * produced the data; a message of at most 2 MiB is timed as the mean of 8 back-to-back
  * launches after it, the regime of a stream of short messages where launch costs overlap),
- * and store the fastest for the message's log2 size bucket.  Blocking;
+ * and store the fastest for the message's log2 size bucket.  With mode | MPT_MODE_PAGEABLE
+ * (H2D/D2H) the host buffer is ordinary pageable memory and the candidates are the paths
+ * that accept it: the zero-copy kernel, host-thread staging (MPT_HS_HOST_THREADS) and their
+ * splits; the entry serves mpt_plan(..., MPT_PLAN_PAGEABLE).  Blocking;
  * allocates scratch buffers of `nbytes` (kept by the context).  MPT_TUNE_VERBOSE=1 prints
  * every candidate's timing to stderr.  out (capacity 4, nullable),
  * out_n and out_us (nullable) receive the winner.  Errors: EINVAL, ECUDA, ENOMEM. */

@@ -22,6 +22,7 @@ MPT_PATH_CE, MPT_PATH_SM, MPT_PATH_HS, MPT_PATH_ZC = 1, 2, 4, 8
 MPT_LAYOUT_CONTIG, MPT_LAYOUT_INTERLEAVE = 0, 1
 MPT_SM_VEC128, MPT_SM_BULK, MPT_SM_TILE8K = 0, 1, 2
 MPT_HS_HOST_THREADS = 1
+MPT_PLAN_PAGEABLE, MPT_MODE_PAGEABLE = 0x200, 0x10
 MPT_PLAN_EAGER = 0x100
 MPT_MODE_GRAPH, MPT_MODE_EAGER = 0, 1
 MPT_PREPARE_GRAPH, MPT_PREPARE_EAGER, MPT_PREPARE_AUTO = 0, 1, 2

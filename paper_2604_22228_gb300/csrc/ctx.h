@@ -115,7 +115,7 @@ struct mpt_ctx_s {
   uint32_t traced = 0;         // lanes timed by the last such launch
   bool pdl = true;             // direct kernel issue overlaps the previous copy kernel's end
   std::unique_ptr<mpt::HostCopyPool> host_pool;  // CPU hops of host-thread staging (made on first use)
-  unsigned host_threads = 0;   // pool workers (MPT_HOST_THREADS; 0 = min(16, cores) - 1)
+  unsigned host_threads = 0;   // pool workers (MPT_HOST_THREADS; 0 = min(8, cores / 2) - 1)
   std::map<uint32_t, mpt::TuneEntry> tuned;  // tune_key -> choice
   // tuner scratch (grown on demand)
   void* tune_a = nullptr;
@@ -123,6 +123,8 @@ struct mpt_ctx_s {
   uint64_t tune_dev_bytes = 0;
   void* tune_h = nullptr;
   uint64_t tune_host_bytes = 0;
+  void* tune_pg = nullptr;            // pageable host buffer (MPT_MODE_PAGEABLE)
+  uint64_t tune_pg_bytes = 0;
   void* flush = nullptr;              // L2 flush buffer
   uint64_t flush_bytes = 0;
   // batched transfers

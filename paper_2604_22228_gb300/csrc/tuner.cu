@@ -152,6 +152,22 @@ TuneEntry model_choice(uint64_t n, uint32_t dir, uint32_t mode, uint32_t align) 
   return best;
 }
 
+// Untuned choice for pageable host memory: the zero-copy kernel alone where the device
+// reaches pageable memory (it runs at the host link's speed on a coherent host), else
+// host-thread staging with the largest stage chunk.
+TuneEntry pageable_default(mpt_ctx_t c, uint64_t n, uint32_t align) {
+  TuneEntry e;
+  e.npaths = 1;
+  const uint64_t whole = std::max<uint64_t>(align, round_up(std::max<uint64_t>(n, 1), align));
+  if (c->pageable) {
+    e.paths[0] = mpt_path_spec{MPT_PATH_ZC, MPT_SHARE_ONE, whole, 0, 0};
+  } else {
+    e.paths[0] = mpt_path_spec{MPT_PATH_HS, MPT_SHARE_ONE, std::min<uint64_t>(whole, c->stage_max / align * align), 0,
+                               MPT_HS_HOST_THREADS};
+  }
+  return e;
+}
+
 // MPT_PATHS and friends; false when MPT_PATHS is unset.
 bool env_choice(uint64_t n, uint32_t dir, uint32_t align, TuneEntry& e, mpt_status& st) {
   const char* pv = std::getenv("MPT_PATHS");
@@ -222,7 +238,9 @@ mpt_status tuner_fill(mpt_ctx_t ctx, uint64_t nbytes, uint32_t dir, uint32_t mod
   if (!from_env) {
     if (!ctx) return fail(MPT_EINVAL, "mpt_plan: the tuner needs a context (or MPT_PATHS)");
     auto it = ctx->tuned.find(tune_key(dir, mode, size_bucket(nbytes)));
-    e = it != ctx->tuned.end() ? it->second : model_choice(nbytes, dir, mode, align);
+    if (it != ctx->tuned.end()) e = it->second;
+    else if (mode & MPT_MODE_PAGEABLE) e = pageable_default(ctx, nbytes, align);
+    else e = model_choice(nbytes, dir, mode, align);
   }
   for (uint32_t p = 0; p < e.npaths; ++p) e.paths[p].chunk_bytes = std::max<uint64_t>(align, round_up(e.paths[p].chunk_bytes, align));
   if (whole_set) {
@@ -271,6 +289,29 @@ std::vector<Candidate> candidates(mpt_ctx_t c, uint32_t dir, uint64_t n, uint32_
     out.push_back(k);
   };
   const uint64_t whole = chunk_for(n, 1);
+  if (mode & MPT_MODE_PAGEABLE) {
+    // paths that accept pageable host memory: zero-copy (where the device reaches it) and
+    // host-thread staging, alone and split
+    const uint64_t smax = c->stage_max / 16 * 16;
+    if (c->pageable)
+      for (uint32_t ctas : {sms / 2, sms, 2 * sms}) one(MPT_PATH_ZC, whole, ctas, 0);
+    for (uint64_t cb : {2ull << 20, 4ull << 20, 8ull << 20}) {
+      const uint64_t ch = std::min<uint64_t>(std::min(cb, smax), whole);
+      one(MPT_PATH_HS, ch, 0, MPT_HS_HOST_THREADS);
+      if (ch >= whole) break;
+    }
+    if (c->pageable && n >= (4u << 20)) {
+      for (uint32_t w : {32768u, 49152u, 57344u}) {
+        Candidate k{};
+        k.n = 2;
+        k.p[0] = mpt_path_spec{MPT_PATH_ZC, w, chunk_for((n * w) >> 16, 1), sms, 0};
+        k.p[1] = mpt_path_spec{MPT_PATH_HS, MPT_SHARE_ONE - w, std::min<uint64_t>(smax, whole), 0,
+                               MPT_HS_HOST_THREADS};
+        out.push_back(k);
+      }
+    }
+    return out;
+  }
   if (dir == MPT_D2D) {
     for (uint32_t ctas : {sms, 4 * sms, 16 * sms}) one(MPT_PATH_SM, whole, ctas, MPT_SM_VEC128);
     if (n <= (32ull << 20) && n > (64u << 10))
@@ -305,7 +346,6 @@ std::vector<Candidate> candidates(mpt_ctx_t c, uint32_t dir, uint64_t n, uint32_
       for (uint64_t cb : {1ull << 20, 4ull << 20, 8ull << 20})
         if (cb <= c->stage_max && cb <= n) one(MPT_PATH_HS, cb, 0, 0);
   }
-  (void)mode;
   return out;
 }
 
@@ -320,7 +360,10 @@ extern "C" {
 mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, uint32_t reps, mpt_path_spec* out,
                     uint32_t* out_n, double* out_us) {
   if (!c) return fail(MPT_EINVAL, "mpt_tune: NULL context");
-  if (dir > MPT_D2H || mode > 1) return fail(MPT_EINVAL, "mpt_tune: bad direction or mode");
+  const bool pageable = (mode & MPT_MODE_PAGEABLE) != 0;
+  const bool graph_mode = (mode & 1u) == 0;
+  if (dir > MPT_D2H || (mode & ~MPT_MODE_PAGEABLE) > 1 || (pageable && dir == MPT_D2D))
+    return fail(MPT_EINVAL, "mpt_tune: bad direction or mode");
   if (nbytes == 0) return fail(MPT_EINVAL, "mpt_tune: empty message");
   if (reps == 0) reps = nbytes >= (256ull << 20) ? 3 : (nbytes >= (16ull << 20) ? 5 : 11);
   CUDA_TRY(cudaSetDevice(c->device));
@@ -330,7 +373,17 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
   if (c->tune_b) cudaFree(c->tune_b);
   c->tune_b = nullptr;
   CUDA_TRY(cudaMalloc(&c->tune_b, c->tune_dev_bytes));
-  if (dir != MPT_D2D && c->tune_host_bytes < nbytes) {
+  if (pageable && c->tune_pg_bytes < nbytes) {
+    std::free(c->tune_pg);
+    c->tune_pg = std::malloc(nbytes);
+    if (!c->tune_pg) {
+      c->tune_pg_bytes = 0;
+      return fail(MPT_ENOMEM, "mpt_tune: pageable host buffer of %llu bytes", (unsigned long long)nbytes);
+    }
+    std::memset(c->tune_pg, 0x5a, nbytes);  // touch every page before timing
+    c->tune_pg_bytes = nbytes;
+  }
+  if (!pageable && dir != MPT_D2D && c->tune_host_bytes < nbytes) {
     if (c->tune_h) cudaFreeHost(c->tune_h);
     c->tune_h = nullptr;
     c->tune_host_bytes = 0;
@@ -339,8 +392,9 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
   }
   st = ensure_dev(c->flush, c->flush_bytes, 256ull << 20);
   if (st != MPT_OK) return st;
-  void* src = dir == MPT_H2D ? c->tune_h : c->tune_a;
-  void* dst = dir == MPT_D2H ? c->tune_h : c->tune_b;
+  void* host = pageable ? c->tune_pg : c->tune_h;
+  void* src = dir == MPT_H2D ? host : c->tune_a;
+  void* dst = dir == MPT_D2H ? host : c->tune_b;
   cudaStream_t s = c->lane[MPT_MAX_PATHS - 1].s[0];
   cudaEvent_t e0, e1;
   CUDA_TRY(cudaEventCreate(&e0));
@@ -359,7 +413,7 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
     if (mpt_plan(nullptr, nbytes, dir, k.p, k.n, 16, MPT_LAYOUT_CONTIG, &plan) != MPT_OK) continue;
     mpt_graph_s g;
     bool ok = true;
-    if (mode == 0) ok = build_private_graph(c, plan, dst, src, &g) == MPT_OK;
+    if (graph_mode) ok = build_private_graph(c, plan, dst, src, &g) == MPT_OK;
     std::vector<float> ts;
     for (uint32_t r = 0; ok && r < reps + 1; ++r) {
       // write 256 MiB (twice the L2) first, on the timing stream: each run starts with a cold
@@ -367,7 +421,7 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
       cudaMemsetAsync(c->flush, r & 0xff, c->flush_bytes, s);
       cudaEventRecord(e0, s);
       for (uint32_t k2 = 0; ok && k2 < chain; ++k2) {
-        if (mode == 0) ok = g.exec == nullptr || cudaGraphLaunch(g.exec, s) == cudaSuccess;
+        if (graph_mode) ok = g.exec == nullptr || cudaGraphLaunch(g.exec, s) == cudaSuccess;
         else ok = run_eager(c, plan, dst, src, s) == MPT_OK;
       }
       cudaEventRecord(e1, s);
@@ -376,7 +430,7 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
       cudaEventElapsedTime(&ms, e0, e1);
       if (r > 0) ts.push_back(ms / (float)chain);  // the first run warms up
     }
-    if (mode == 0) free_private_graph(&g);
+    if (graph_mode) free_private_graph(&g);
     mpt_plan_destroy(plan);
     if (!ok || ts.empty()) {
       cudaGetLastError();
@@ -451,7 +505,8 @@ mpt_status mpt_tune_load(mpt_ctx_t c, const char* path) {
       }
     }
     if (n == 0) continue;
-    if (n < 10 || (n - 5) % 5 != 0 || v[0] > 2 || v[1] > 1 || v[2] > 63) {
+    const uint32_t lmode = (uint32_t)v[1];
+    if (n < 10 || (n - 5) % 5 != 0 || v[0] > 2 || (lmode & ~MPT_MODE_PAGEABLE) > 1 || v[2] > 63) {
       std::fclose(f);
       return fail(MPT_EINVAL, "mpt_tune_load: %s line %u is not a tuner entry", path, lineno);
     }

@@ -170,3 +170,45 @@ def test_concurrent_transfers_share_the_pool(ctx):
             mpt.mpt_graph_release(g)
     finally:
         mpt.mpt_plan_destroy(plan)
+
+
+def _pageable_safe(paths):
+    return all(p["kind"] == P.ZC or (p["kind"] == P.HS and p["flags"] & HT) for p in paths)
+
+
+@pytest.mark.parametrize("direction", [P.H2D, P.D2H])
+def test_pageable_plans_from_the_tuner(monkeypatch, direction):
+    """mpt_plan(..., MPT_PLAN_PAGEABLE) gives a plan whose every path accepts pageable host
+    memory, untuned (default) and after mpt_tune(mode | MPT_MODE_PAGEABLE); both move a
+    pageable buffer bit-exactly."""
+    import torch
+    monkeypatch.setenv("MPT_TUNE_DEFAULTS", "0")
+    c = mpt.mpt_ctx_create(0)
+    try:
+        for n in (300_000 + 3, 16 * MiB + 5):
+            untuned = mpt.mpt_plan(c, n, direction, None, 16, mpt.MPT_PLAN_PAGEABLE)
+            assert _pageable_safe(mpt.mpt_plan_paths(untuned))
+            mpt.mpt_plan_destroy(untuned)
+            specs, us = mpt.mpt_tune(c, direction, n, mpt.MPT_MODE_GRAPH | mpt.MPT_MODE_PAGEABLE)
+            assert us > 0 and _pageable_safe(specs)
+            got, _ = mpt.mpt_tune_get(c, direction, n, mpt.MPT_MODE_GRAPH | mpt.MPT_MODE_PAGEABLE)
+            assert got == specs
+            with pytest.raises(mpt.MptError):  # the page-locked entry of this bucket is separate
+                mpt.mpt_tune_get(c, direction, n, mpt.MPT_MODE_GRAPH)
+            plan = mpt.mpt_plan(c, n, direction, None, 16, mpt.MPT_PLAN_PAGEABLE)
+            assert mpt.mpt_plan_paths(plan) == specs
+            host, dev = Buf(n, "pageable"), Buf(n, "dev")
+            data = seeded("u32", 300 + n, n)
+            (host if direction == P.H2D else dev).fill(data)
+            dst, src = (dev, host) if direction == P.H2D else (host, dev)
+            g = mpt.mpt_capture(c, plan, dst.ptr, src.ptr)
+            mpt.mpt_launch(g, torch.cuda.current_stream())
+            torch.cuda.synchronize()
+            assert np.array_equal(dst.numpy(), T.copy(data)) and dst.guards_intact()
+            mpt.mpt_graph_release(g)
+            mpt.mpt_plan_destroy(plan)
+        with pytest.raises(mpt.MptError) as e:
+            mpt.mpt_plan(c, 4096, P.D2D, None, 16, mpt.MPT_PLAN_PAGEABLE)
+        assert e.value.status == mpt.MPT_EINVAL
+    finally:
+        mpt.mpt_ctx_destroy(c)
