@@ -1234,6 +1234,19 @@ def run_jacobi(mpt, torch, ctx, iters=20):
         row = {"halo_bytes": hb, "subdomain_bytes": (rows + 2) * cols * 4,
                "plan_graph": [(q["kind"], q["share"]) for q in mpt.mpt_plan_paths(tuned_g)],
                "plan_direct": [(q["kind"], q["share"]) for q in mpt.mpt_plan_paths(tuned_e)]}
+        # the stencil alone: algorithmic bytes per sweep = (rows + 2) rows read + rows written
+        for warm in (True, False):
+            e0.record(s)
+            for it in range(2 if warm else iters):
+                sweep(it % 2)
+            e1.record(s)
+            e1.synchronize()
+        sweep_ms = e0.elapsed_time(e1) / iters
+        sweep_bytes = nsub * (2 * rows + 2) * cols * 4
+        peak, _ = load_peaks()
+        row["stencil_ms_per_iter"] = round(sweep_ms, 4)
+        row["stencil_gbs"] = round(sweep_bytes / (sweep_ms / 1e3) / 1e9, 1)
+        row["stencil_hbm_frac"] = round(sweep_bytes / (sweep_ms / 1e3) / 1e9 / peak, 3)
         for name, hs in variants.items():
             for warm in (True, False):
                 e0.record(s)
@@ -1288,12 +1301,15 @@ def run_kernel_only(args):
     build.build()
     n = args.kernel_bytes
     ctx = mpt.mpt_ctx_create(0)
-    host = args.kernel_only == "zc"
-    if host:
+    host = args.kernel_only in ("zc", "zc_d2h")
+    if args.kernel_only == "zc":  # host -> device
         a = torch.empty(n, dtype=torch.uint8).pin_memory()
     else:
         a = torch.empty(n, dtype=torch.uint8, device="cuda")
-    b = torch.empty(n, dtype=torch.uint8, device="cuda")
+    if args.kernel_only == "zc_d2h":  # device -> host
+        b = torch.empty(n, dtype=torch.uint8).pin_memory()
+    else:
+        b = torch.empty(n, dtype=torch.uint8, device="cuda")
     a.fill_(7)
     variant = {"bulk": mpt.MPT_SM_BULK, "vec8k": mpt.MPT_SM_TILE8K}.get(args.kernel_only, mpt.MPT_SM_VEC128)
     s = torch.cuda.Stream()
@@ -1306,7 +1322,7 @@ def run_kernel_only(args):
     e1.record(s)
     e1.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
-    ok = bool(torch.equal(a[:1 << 20].to(b.device), b[:1 << 20]))
+    ok = bool(torch.equal(a[:1 << 20].cpu(), b[:1 << 20].cpu()))
     st, _ = mpt.mpt_ctx_status(ctx)
     mpt.mpt_ctx_destroy(ctx)
     moved = n if host else 2 * n
@@ -1344,7 +1360,7 @@ def main(argv=None):
     ap.add_argument("--tune", choices=["online", "model"], default="online",
                     help="online: measure every size bucket with mpt_tune before capturing; model: cost model only")
     ap.add_argument("--tune-out", default=None, help="write the tuned table (JSON lines) here")
-    ap.add_argument("--kernel-only", choices=["vec", "vec8k", "bulk", "zc"], default=None,
+    ap.add_argument("--kernel-only", choices=["vec", "vec8k", "bulk", "zc", "zc_d2h"], default=None,
                     help="time one copy kernel alone on --kernel-bytes (profiling)")
     ap.add_argument("--kernel-bytes", type=int, default=256 * MiB)
     ap.add_argument("--kernel-ctas", type=int, default=0)

@@ -120,3 +120,29 @@ def test_staged_path_refuses_first_use_inside_capture():
     mpt.mpt_graph_release(h)
     mpt.mpt_plan_destroy(plan)
     mpt.mpt_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("rows,cols,offset", [
+    (1, 4, 0), (1, 8, 0), (2, 1024, 0), (8, 4096, 0), (3, 8192 + 4, 0), (33, 1028, 0), (5, 256 * 4 * 3 + 12, 0),
+    (8, 4099, 0), (5, 2, 0), (7, 3, 0), (4, 4096, 1),  # scalar kernel: ragged columns, misaligned rows
+])
+def test_single_sweep_matches_oracle(rows, cols, offset):
+    """One mpt_demo_jacobi_step on a (rows + 2) x cols subdomain against the oracle's sweep
+    of the same rows (bit-exact, fp32 in the stated order); halo rows of `out` untouched.
+    cols % 4 == 0 on 16-byte aligned rows takes the column-strip kernel, the rest the
+    one-thread-per-point kernel."""
+    import torch
+    grid = payload.fill("f32", 0x5EED0007 + rows * 131 + cols, (rows + 2) * cols * 4).view(np.float32)
+    grid = grid.reshape(rows + 2, cols)
+    n = (rows + 2) * cols
+    buf_in = torch.zeros(n + offset, dtype=torch.float32, device="cuda")
+    buf_out = torch.full((n + offset + 8,), 7.0, dtype=torch.float32, device="cuda")
+    buf_in[offset:offset + n].copy_(torch.from_numpy(grid.reshape(-1)))
+    assert mpt.mpt_demo_jacobi_step(buf_in[offset:], buf_out[offset:], rows, cols,
+                                    torch.cuda.current_stream()) is None
+    torch.cuda.synchronize()
+    got = buf_out[offset:offset + n].cpu().numpy().reshape(rows + 2, cols)
+    want = J.step(grid)[1:rows + 1]
+    assert np.array_equal(got[1:rows + 1], want), f"max diff {np.abs(got[1:rows + 1] - want).max()}"
+    assert (got[0] == 7.0).all() and (got[rows + 1] == 7.0).all()
+    assert (buf_out[offset + n:].cpu().numpy() == 7.0).all()
