@@ -844,20 +844,39 @@ def run_batched(mpt, torch, ctx, stream, reps=5):
                          for a, so, do, sz in items])
     total = sum(sizes)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    batch_ms, lat = [], []
-    for r in range(reps + 2):
-        e0.record(stream)
-        b = mpt.mpt_batch_submit(ctx, xf, stream)
-        e1.record(stream)
-        mpt.mpt_batch_wait(b, 60 * 10 ** 9)
-        t = mpt.mpt_batch_times(b, len(items))
-        mpt.mpt_batch_release(b)
-        e1.synchronize()
-        if r >= 2:
-            batch_ms.append(e0.elapsed_time(e1))
-            lat += [x / 1e3 for x in t]
-    ok = all(mpt.mpt_hash_device(ctx, dst.data_ptr() + do, sz) == mpt.mpt_hash_device(ctx, src[a].data_ptr() + so, sz)
-             for a, so, do, sz in items[::64])
+
+    def timed_batches():
+        ms_, lat_ = [], []
+        for r in range(reps + 2):
+            e0.record(stream)
+            b = mpt.mpt_batch_submit(ctx, xf, stream)
+            e1.record(stream)
+            mpt.mpt_batch_wait(b, 60 * 10 ** 9)
+            t = mpt.mpt_batch_times(b, len(items))
+            mpt.mpt_batch_release(b)
+            e1.synchronize()
+            if r >= 2:
+                ms_.append(e0.elapsed_time(e1))
+                lat_ += [x / 1e3 for x in t]
+        ok_ = all(mpt.mpt_hash_device(ctx, dst.data_ptr() + do, sz) ==
+                  mpt.mpt_hash_device(ctx, src[a].data_ptr() + so, sz) for a, so, do, sz in items[::64])
+        return ms_, lat_, ok_
+
+    # the persistent kernel plus copy-engine lanes for the large entries, at a few settings
+    dma = []
+    for lanes, min_mb in ((1, 8), (2, 4), (3, 2)):
+        mpt.mpt_batch_configure_dma(ctx, lanes, 8, min_mb * MiB)
+        dst.zero_()
+        ms_, lat_, ok_ = timed_batches()
+        m_ = statistics.median(ms_)
+        dma.append({"lanes_per_direction": lanes, "items_per_lane": 8, "min_bytes": min_mb * MiB,
+                    "batch_ms": round(m_, 3), "transfers_per_s": round(4096 / (m_ / 1e3), 1),
+                    "p50_us": round(_percentile(lat_, 50), 1), "p99_us": round(_percentile(lat_, 99), 1),
+                    "parity_ok": bool(ok_)})
+    mpt.mpt_batch_configure_dma(ctx, 0, 0, 0)  # the kernel alone (the default)
+    dst.zero_()
+    batch_ms, lat, ok = timed_batches()
+    ok = ok and all(d["parity_ok"] for d in dma)
     # per-transfer eager copies, one event per transfer for its completion time
     views = [(dst[do:do + sz], src[a][so:so + sz]) for a, so, do, sz in items]
     evs = [torch.cuda.Event(enable_timing=True) for _ in items]
@@ -885,7 +904,7 @@ def run_batched(mpt, torch, ctx, stream, reps=5):
         "eager_ms": round(emed, 3), "eager_transfers_per_s": round(4096 / (emed / 1e3), 1),
         "eager_p50_us": round(_percentile(eager_lat, 50), 1), "eager_p99_us": round(_percentile(eager_lat, 99), 1),
         "latency": "per-transfer completion after the batch kernel started (batched) / after the first "
-                   "copy was enqueued (eager), device clocks", "parity_ok": bool(ok)}
+                   "copy was enqueued (eager), device clocks", "dma_lanes": dma, "parity_ok": bool(ok)}
 
 
 def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30):

@@ -397,6 +397,18 @@ MPT_API mpt_status mpt_tune_get(mpt_ctx_t ctx, uint32_t dir, uint64_t nbytes, ui
 MPT_API mpt_status mpt_batch_configure(mpt_ctx_t ctx, uint32_t slots, uint32_t max_xfers, uint32_t ctas,
                                        uint32_t tile_bytes);
 
+/* DMA lanes of the batch (config 4's "kernel plus DMA lanes"): per direction (D2D, H2D,
+ * D2H) `lanes` copy-engine lanes, each taking up to `items_per_lane` entries of at least
+ * `min_bytes` per batch, largest first to the least-loaded lane of the entry's direction;
+ * the kernel moves everything else.  Entries with a pageable host side stay with the
+ * kernel.  Each lane entry completes individually (time stamp and host flag, as for kernel
+ * entries).  lanes = 0 turns the lanes off (the default unless MPT_BATCH_DMA_LANES,
+ * MPT_BATCH_DMA_ITEMS and MPT_BATCH_DMA_MIN set them).  Rebuilds the batch ring like
+ * mpt_batch_configure.  Errors: EINVAL (lanes > 8, items outside 1..64, min_bytes < 16),
+ * EAGAIN (a batch is held), ECUDA. */
+MPT_API mpt_status mpt_batch_configure_dma(mpt_ctx_t ctx, uint32_t lanes, uint32_t items_per_lane,
+                                           uint64_t min_bytes);
+
 /* Register an arena (this GPU's memory or page-locked host memory) so that batch
  * descriptors inside it are classified without per-pointer runtime queries.  The caller
  * keeps ownership; the arena must stay allocated while registered. */

@@ -255,6 +255,10 @@ def mpt_batch_configure(ctx: int, slots: int = 0, max_xfers: int = 0, ctas: int 
     _check(lib().mpt_batch_configure(ctx, slots, max_xfers, ctas, tile_bytes), "mpt_batch_configure")
 
 
+def mpt_batch_configure_dma(ctx: int, lanes: int, items_per_lane: int = 8, min_bytes: int = 4 << 20) -> None:
+    _check(lib().mpt_batch_configure_dma(ctx, lanes, items_per_lane, min_bytes), "mpt_batch_configure_dma")
+
+
 def mpt_batch_register(ctx: int, base, nbytes: int) -> None:
     _check(lib().mpt_batch_register(ctx, _ptr(base), nbytes), "mpt_batch_register")
 

@@ -124,6 +124,7 @@ SIGNATURES = {
     "mpt_tune_get": (C.c_int, [H, C.c_uint32, C.c_uint64, C.c_uint32, P(mpt_path_spec), P(C.c_uint32),
                                P(C.c_double)]),
     "mpt_batch_configure": (C.c_int, [H, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]),
+    "mpt_batch_configure_dma": (C.c_int, [H, C.c_uint32, C.c_uint32, C.c_uint64]),
     "mpt_batch_register": (C.c_int, [H, C.c_void_p, C.c_uint64]),
     "mpt_batch_submit": (C.c_int, [H, P(mpt_xfer), C.c_size_t, C.c_void_p, P(H)]),
     "mpt_batch_poll": (C.c_int, [H, P(C.c_size_t), P(C.c_uint8)]),

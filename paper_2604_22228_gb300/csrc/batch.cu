@@ -17,6 +17,7 @@
 // batch up to the slot capacity replays the same graph.
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <thread>
 
@@ -84,6 +85,15 @@ __device__ __forceinline__ void batch_body(const BatchArgs& a) {
   }
 }
 
+__global__ void k_batch_dma_done(BatchArgs a, const uint32_t* dma_map, uint32_t item) {
+  if (threadIdx.x != 0) return;
+  const uint32_t idx = dma_map[item];
+  if (idx == ~0u) return;
+  a.times[idx] = now_ns();
+  __threadfence_system();
+  asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(a.host_flags + idx), "r"(a.hdr->epoch) : "memory");
+}
+
 __global__ void __launch_bounds__(kVecThreads, 3) k_batch(BatchArgs a) { batch_body<false>(a); }
 __global__ void __launch_bounds__(kVecThreads) k_batch_any(BatchArgs a) { batch_body<true>(a); }
 
@@ -92,6 +102,7 @@ namespace {
 constexpr uint32_t kDefaultSlots = 4;
 constexpr uint32_t kDefaultMaxXfers = 4096;
 constexpr uint32_t kDefaultTile = 256 * 1024;
+constexpr uint32_t kDmaDirs = 3;  // lanes per direction: D2D, H2D, D2H
 
 uint64_t host_ns() {
   return (uint64_t)std::chrono::duration_cast<std::chrono::nanoseconds>(
@@ -105,6 +116,7 @@ void slot_free(BatchSlot& s) {
     if (s.graph[i]) cudaGraphDestroy(s.graph[i]);
   }
   if (s.done_ev) cudaEventDestroy(s.done_ev);
+  if (s.h_scratch) cudaFreeHost(s.h_scratch);
   if (s.h_table) cudaFreeHost(s.h_table);
   if (s.h_flags) cudaFreeHost(s.h_flags);
   if (s.d_mem) cudaFree(s.d_mem);
@@ -113,7 +125,11 @@ void slot_free(BatchSlot& s) {
 
 mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t ctas) {
   s.max_xfers = max_xfers;
-  s.table_bytes = sizeof(BatchHeader) + (size_t)max_xfers * sizeof(BatchDesc);
+  s.dma_lanes = c->batch_dma_lanes;
+  s.dma_items = c->batch_dma_lanes ? c->batch_dma_items : 0;
+  const uint32_t ndma = kDmaDirs * s.dma_lanes * s.dma_items;
+  const size_t map_off = sizeof(BatchHeader) + (size_t)max_xfers * sizeof(BatchDesc);
+  s.table_bytes = map_off + (size_t)ndma * sizeof(uint32_t);
   CUDA_TRY(cudaHostAlloc(&s.h_table, s.table_bytes, cudaHostAllocPortable));
   CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&s.h_flags), (size_t)max_xfers * sizeof(uint32_t),
                          cudaHostAllocMapped | cudaHostAllocPortable));
@@ -122,12 +138,18 @@ mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t cta
   const size_t ctrl_off = (s.table_bytes + 255) & ~(size_t)255;
   s.ctrl_bytes = 256 + (size_t)max_xfers * sizeof(uint32_t);
   const size_t times_off = (ctrl_off + s.ctrl_bytes + 255) & ~(size_t)255;
-  CUDA_TRY(cudaMalloc(&s.d_mem, times_off + (size_t)max_xfers * sizeof(uint64_t)));
+  const size_t scratch_off = (times_off + (size_t)max_xfers * sizeof(uint64_t) + 255) & ~(size_t)255;
+  CUDA_TRY(cudaMalloc(&s.d_mem, scratch_off + 256));
   uint8_t* base = static_cast<uint8_t*>(s.d_mem);
   s.d_table = base;
   s.d_ctrl = base + ctrl_off;
   s.d_times = reinterpret_cast<unsigned long long*>(base + times_off);
-  CUDA_TRY(cudaMemset(s.d_mem, 0, times_off + (size_t)max_xfers * sizeof(uint64_t)));
+  CUDA_TRY(cudaMemset(s.d_mem, 0, scratch_off + 256));
+  s.h_dma_map = reinterpret_cast<uint32_t*>(s.h_table + map_off);
+  for (uint32_t k = 0; k < ndma; ++k) s.h_dma_map[k] = ~0u;
+  if (ndma) CUDA_TRY(cudaHostAlloc(&s.h_scratch, 64, cudaHostAllocPortable));
+  uint8_t* d_scratch = base + scratch_off;
+  const uint32_t* d_map = reinterpret_cast<const uint32_t*>(s.d_table + map_off);
   CUDA_TRY(cudaEventCreateWithFlags(&s.done_ev, cudaEventDisableTiming));
   s.args.hdr = reinterpret_cast<const BatchHeader*>(s.d_table);
   s.args.desc = reinterpret_cast<const BatchDesc*>(s.d_table + sizeof(BatchHeader));
@@ -160,7 +182,44 @@ mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t cta
     kp.blockDim = dim3(kVecThreads);
     kp.kernelParams = params;
     CUDA_TRY(cudaGraphAddKernelNode(&kn, s.graph[gi], deps, 2, &kp));
+    // DMA lanes beside the kernel: per direction, chains of memcpy -> completion kernel.
+    // Instantiation-time operands are scratch buffers of the lane's memory kinds (a
+    // retargeted memcpy node keeps the kinds it was built with).
+    s.dma_cp[gi].assign(ndma, nullptr);
+    s.dma_fin[gi].assign(ndma, nullptr);
+    for (uint32_t dir = 0; dir < kDmaDirs; ++dir) {
+      void* to = dir == MPT_D2H ? s.h_scratch : static_cast<void*>(d_scratch);
+      const void* from = dir == MPT_H2D ? s.h_scratch : static_cast<const void*>(d_scratch + 128);
+      for (uint32_t l = 0; l < s.dma_lanes; ++l) {
+        cudaGraphNode_t prev = nullptr;
+        for (uint32_t j = 0; j < s.dma_items; ++j) {
+          const uint32_t item = (dir * s.dma_lanes + l) * s.dma_items + j;
+          cudaGraphNode_t cn, fn;
+          if (prev) {
+            CUDA_TRY(cudaGraphAddMemcpyNode1D(&cn, s.graph[gi], &prev, 1, to, from, 16, cudaMemcpyDefault));
+          } else {
+            CUDA_TRY(cudaGraphAddMemcpyNode1D(&cn, s.graph[gi], deps, 2, to, from, 16, cudaMemcpyDefault));
+          }
+          uint32_t it = item;
+          void* fparams[] = {&s.args, const_cast<uint32_t**>(&d_map), &it};
+          cudaKernelNodeParams fp{};
+          fp.func = reinterpret_cast<void*>(&k_batch_dma_done);
+          fp.gridDim = dim3(1);
+          fp.blockDim = dim3(32);
+          fp.kernelParams = fparams;
+          CUDA_TRY(cudaGraphAddKernelNode(&fn, s.graph[gi], &cn, 1, &fp));
+          s.dma_cp[gi][item] = cn;
+          s.dma_fin[gi][item] = fn;
+          prev = fn;
+        }
+      }
+    }
     CUDA_TRY(cudaGraphInstantiate(&s.exec[gi], s.graph[gi], 0));
+    for (uint32_t k = 0; k < ndma; ++k) {  // every lane item starts disabled
+      CUDA_TRY(cudaGraphNodeSetEnabled(s.exec[gi], s.dma_cp[gi][k], 0));
+      CUDA_TRY(cudaGraphNodeSetEnabled(s.exec[gi], s.dma_fin[gi][k], 0));
+    }
+    s.dma_on[gi].assign(ndma, 0);
   }
   return MPT_OK;
 }
@@ -178,8 +237,17 @@ int range_kind(mpt_ctx_t c, const void* p, uint64_t n) {
   if ((at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) && at.device == c->device) return 0;
   if (at.type == cudaMemoryTypeHost) return 1;
   // pageable host memory: the batch kernel reads and writes it directly when the GPU can
-  if (at.type == cudaMemoryTypeUnregistered && c->pageable) return 1;
+  // (a copy-engine graph node cannot: such entries stay with the kernel)
+  if (at.type == cudaMemoryTypeUnregistered && c->pageable) return 2;
   return -1;
+}
+
+uint64_t env_or(const char* name, uint64_t dflt) {
+  const char* v = std::getenv(name);
+  if (!v || !*v) return dflt;
+  char* end = nullptr;
+  const unsigned long long x = std::strtoull(v, &end, 0);
+  return (end && *end == 0) ? (uint64_t)x : dflt;
 }
 
 }  // namespace
@@ -192,6 +260,11 @@ mpt_status batch_setup(mpt_ctx_t c) {
   // which the latency of host-link reads needs; all CTAs resident at once
   const uint32_t ctas = c->batch_ctas ? c->batch_ctas : 3u * (uint32_t)c->sms;
   if (!c->batch_tile) c->batch_tile = kDefaultTile;
+  if (!c->batch_dma_set) {
+    c->batch_dma_lanes = (uint32_t)std::min<uint64_t>(8, env_or("MPT_BATCH_DMA_LANES", 0));
+    c->batch_dma_items = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(64, env_or("MPT_BATCH_DMA_ITEMS", 8)));
+    c->batch_dma_min = std::max<uint64_t>(16, env_or("MPT_BATCH_DMA_MIN", 4ull << 20));
+  }
   c->slots.resize(nslots);
   for (auto& s : c->slots) {
     mpt_status st = slot_init(c, s, maxx, ctas);
@@ -239,6 +312,22 @@ mpt_status mpt_batch_configure(mpt_ctx_t c, uint32_t slots, uint32_t max_xfers, 
   return batch_setup(c);
 }
 
+mpt_status mpt_batch_configure_dma(mpt_ctx_t c, uint32_t lanes, uint32_t items_per_lane, uint64_t min_bytes) {
+  if (!c) return fail(MPT_EINVAL, "mpt_batch_configure_dma: NULL context");
+  for (auto& s : c->slots)
+    if (s.held) return fail(MPT_EAGAIN, "mpt_batch_configure_dma: a batch is still held");
+  if (lanes > 8 || items_per_lane > 64 || (lanes && (items_per_lane == 0 || min_bytes < 16)))
+    return fail(MPT_EINVAL, "mpt_batch_configure_dma: lanes <= 8, 1 <= items <= 64, min_bytes >= 16");
+  CUDA_TRY(cudaSetDevice(c->device));
+  CUDA_TRY(cudaDeviceSynchronize());
+  batch_teardown(c);
+  c->batch_dma_lanes = lanes;
+  c->batch_dma_items = lanes ? items_per_lane : 0;
+  c->batch_dma_min = lanes ? min_bytes : 0;
+  c->batch_dma_set = true;
+  return batch_setup(c);
+}
+
 mpt_status mpt_batch_register(mpt_ctx_t c, const void* base, uint64_t bytes) {
   if (!c || !base || bytes == 0) return fail(MPT_EINVAL, "mpt_batch_register: bad argument");
   CUDA_TRY(cudaSetDevice(c->device));
@@ -271,6 +360,7 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
   // transfer owns its destination region)
   std::vector<std::pair<uint64_t, uint64_t>> spans;
   spans.reserve(n);
+  std::vector<uint32_t> dma_cand;  // entries large enough for a copy-engine lane
   for (size_t i = 0; i < n; ++i) {
     const mpt_xfer& x = xfers[i];
     if (x.dir > MPT_D2H) return fail(MPT_EINVAL, "mpt_batch_submit: transfer %zu has direction %u", i, x.dir);
@@ -278,9 +368,10 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
     if (!x.src || !x.dst) return fail(MPT_EINVAL, "mpt_batch_submit: transfer %zu has a NULL pointer", i);
     const int ks = range_kind(c, x.src, x.bytes), kd = range_kind(c, x.dst, x.bytes);
     const int want_s = x.dir == MPT_H2D ? 1 : 0, want_d = x.dir == MPT_D2H ? 1 : 0;
-    if (ks != want_s || kd != want_d)
+    if ((ks == 2 ? 1 : ks) != want_s || (kd == 2 ? 1 : kd) != want_d)
       return fail(MPT_EINVAL, "mpt_batch_submit: transfer %zu: pointers do not match direction %u", i, x.dir);
     spans.emplace_back((uint64_t)(uintptr_t)x.dst, (uint64_t)(uintptr_t)x.dst + x.bytes);
+    if (s.dma_lanes && x.bytes >= c->batch_dma_min && ks != 2 && kd != 2) dma_cand.push_back((uint32_t)i);
   }
   std::sort(spans.begin(), spans.end());
   for (size_t i = 1; i < spans.size(); ++i)
@@ -292,21 +383,59 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
   if (s.epoch == 0) s.epoch = 1;
   BatchHeader* h = reinterpret_cast<BatchHeader*>(s.h_table);
   BatchDesc* d = reinterpret_cast<BatchDesc*>(s.h_table + sizeof(BatchHeader));
+  // DMA lanes: largest eligible entries first, each to the least-loaded lane of its
+  // direction with a free item (longest-processing-time order); the rest stay with the kernel
+  const uint32_t ndma = kDmaDirs * s.dma_lanes * s.dma_items;
+  std::vector<uint8_t> to_dma(n, 0);
+  for (uint32_t k = 0; k < ndma; ++k) s.h_dma_map[k] = ~0u;
+  if (!dma_cand.empty()) {
+    std::sort(dma_cand.begin(), dma_cand.end(),
+              [&](uint32_t a, uint32_t b) { return xfers[a].bytes > xfers[b].bytes || (xfers[a].bytes == xfers[b].bytes && a < b); });
+    std::vector<uint64_t> load(kDmaDirs * s.dma_lanes, 0);
+    std::vector<uint32_t> used(kDmaDirs * s.dma_lanes, 0);
+    for (uint32_t i : dma_cand) {
+      const uint32_t dir = xfers[i].dir;
+      int best = -1;
+      for (uint32_t l = 0; l < s.dma_lanes; ++l) {
+        const uint32_t li = dir * s.dma_lanes + l;
+        if (used[li] < s.dma_items && (best < 0 || load[li] < load[(uint32_t)best])) best = (int)li;
+      }
+      if (best < 0) continue;
+      s.h_dma_map[(uint32_t)best * s.dma_items + used[(uint32_t)best]] = i;
+      used[(uint32_t)best]++;
+      load[(uint32_t)best] += xfers[i].bytes;
+      to_dma[i] = 1;
+    }
+  }
   uint64_t tiles = 0;
   const uint64_t tile = c->batch_tile;
   bool any_shift = false;
   for (size_t i = 0; i < n; ++i) {
     const mpt_xfer& x = xfers[i];
-    any_shift |= (((uintptr_t)x.src ^ (uintptr_t)x.dst) & 15) != 0 && x.bytes >= 16;
-    const uint64_t t = std::max<uint64_t>(1, (x.bytes + tile - 1) / tile);
-    const uint32_t fl = (x.dir == MPT_D2H ? kDescHostDst : 0u) | (x.dir != MPT_D2D ? kDescHostSide : 0u);
+    const uint32_t fl = (x.dir == MPT_D2H ? kDescHostDst : 0u) | (x.dir != MPT_D2D ? kDescHostSide : 0u) |
+                        (to_dma[i] ? kDescDma : 0u);
+    const uint64_t t = to_dma[i] ? 0 : std::max<uint64_t>(1, (x.bytes + tile - 1) / tile);
+    if (!to_dma[i]) any_shift |= (((uintptr_t)x.src ^ (uintptr_t)x.dst) & 15) != 0 && x.bytes >= 16;
     d[i] = BatchDesc{(uint64_t)(uintptr_t)x.src, (uint64_t)(uintptr_t)x.dst, x.bytes, (uint32_t)tiles, (uint32_t)t, fl, 0u};
     tiles += t;
   }
   if (tiles >= (1ull << 32)) return fail(MPT_EINVAL, "mpt_batch_submit: batch too large for 32-bit tile indices");
   *h = BatchHeader{(uint32_t)n, (uint32_t)tiles, (uint32_t)tile, s.epoch};
+  const int gi = any_shift ? 1 : 0;
+  for (uint32_t k = 0; k < ndma; ++k) {  // retarget used lane items, switch the rest off
+    const uint32_t i = s.h_dma_map[k];
+    const uint8_t want = i != ~0u;
+    if (want)
+      CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(s.exec[gi], s.dma_cp[gi][k], xfers[i].dst, xfers[i].src,
+                                                  xfers[i].bytes, cudaMemcpyDefault));
+    if (want != s.dma_on[gi][k]) {
+      CUDA_TRY(cudaGraphNodeSetEnabled(s.exec[gi], s.dma_cp[gi][k], want));
+      CUDA_TRY(cudaGraphNodeSetEnabled(s.exec[gi], s.dma_fin[gi][k], want));
+      s.dma_on[gi][k] = want;
+    }
+  }
   const cudaStream_t cs = static_cast<cudaStream_t>(stream);
-  CUDA_TRY(cudaGraphLaunch(s.exec[any_shift ? 1 : 0], cs));
+  CUDA_TRY(cudaGraphLaunch(s.exec[gi], cs));
   CUDA_TRY(cudaEventRecord(s.done_ev, cs));
   s.held = true;
   s.n = n;

@@ -69,6 +69,15 @@ struct BatchSlot {
   uint32_t epoch = 0;
   bool held = false;
   size_t n = 0;
+  // DMA lanes: for each direction (D2D, H2D, D2H) `lanes` chains of `items` copy-engine
+  // memcpy nodes, each followed by a completion kernel; item k = (dir * lanes + lane) *
+  // items + position.  Per batch the used memcpy nodes are retargeted and enabled, the
+  // others disabled (no cost when no entry is large).
+  uint32_t dma_lanes = 0, dma_items = 0;
+  uint32_t* h_dma_map = nullptr;  // in the page-locked table: item -> descriptor (~0 unused)
+  std::vector<cudaGraphNode_t> dma_cp[2], dma_fin[2];
+  std::vector<uint8_t> dma_on[2];
+  void* h_scratch = nullptr;      // page-locked 64 bytes: instantiation-time operand of host lanes
 };
 
 mpt_status batch_setup(mpt_ctx_t c);
@@ -131,4 +140,7 @@ struct mpt_ctx_s {
   std::vector<mpt::BatchSlot> slots;
   std::vector<mpt::Arena> arenas;
   uint32_t batch_slots = 0, batch_max_xfers = 0, batch_ctas = 0, batch_tile = 0;
+  uint32_t batch_dma_lanes = 0, batch_dma_items = 0;  // per direction; items per lane
+  uint64_t batch_dma_min = 0;                         // smallest entry a DMA lane takes
+  bool batch_dma_set = false;                         // configured (else environment defaults)
 };
