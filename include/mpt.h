@@ -409,6 +409,32 @@ MPT_API mpt_status mpt_batch_configure(mpt_ctx_t ctx, uint32_t slots, uint32_t m
 MPT_API mpt_status mpt_batch_configure_dma(mpt_ctx_t ctx, uint32_t lanes, uint32_t items_per_lane,
                                            uint64_t min_bytes);
 
+/* Batch autotuner (config 4: autotuned CTA count and tile size).  Runs the representative
+ * batch `xfers` (n entries; their destinations are written) `reps` times (0 = 3) under each
+ * candidate setting -- kernel CTAs in {1, 2, 3} x SMs, tile bytes in {64, 128, 256, 512,
+ * 1024} KiB, DMA lanes off or 2 per direction for entries of at least 4 MiB -- and keeps the
+ * best: objective MPT_BATCH_TUNE_TIME the shortest median batch, MPT_BATCH_TUNE_P99 the
+ * lowest median p99 entry completion time (device clock, from the kernel's start).  The
+ * chosen setting is applied to the context (as mpt_batch_configure and
+ * mpt_batch_configure_dma would) and written to *out (nullable).  Blocking.  Errors: EINVAL,
+ * EAGAIN (a batch is held), ECUDA. */
+#define MPT_BATCH_TUNE_TIME 0u
+#define MPT_BATCH_TUNE_P99 1u
+typedef struct {
+  uint32_t ctas;           /* kernel CTAs */
+  uint32_t tile_bytes;
+  uint32_t dma_lanes;      /* per direction, 0 = kernel alone */
+  uint32_t dma_items;
+  uint64_t dma_min_bytes;
+  double batch_us;         /* median batch time of the chosen setting */
+  double p99_us;           /* median p99 entry completion of the chosen setting */
+  uint32_t candidates;     /* settings measured */
+  uint32_t reserved;
+} mpt_batch_tuning;
+
+MPT_API mpt_status mpt_batch_tune(mpt_ctx_t ctx, const mpt_xfer* xfers, size_t n, uint32_t objective, uint32_t reps,
+                                  void* stream, mpt_batch_tuning* out);
+
 /* Register an arena (this GPU's memory or page-locked host memory) so that batch
  * descriptors inside it are classified without per-pointer runtime queries.  The caller
  * keeps ownership; the arena must stay allocated while registered. */

@@ -17,7 +17,7 @@ import ctypes as C
 
 from . import _ffi
 from ._ffi import (MPT_D2D, MPT_D2H, MPT_H2D, MPT_LAYOUT_CONTIG, MPT_LAYOUT_INTERLEAVE, MPT_MAX_CHUNKS,  # noqa: F401
-                   MPT_NOALLOC_MAX_RANGES, MPT_MAX_PATHS, MPT_PATH_CE, MPT_PATH_HS, MPT_PATH_SM, MPT_PATH_ZC, MPT_SHARE_ONE, MPT_SM_BULK, MPT_SM_TILE8K, MPT_HS_HOST_THREADS, MPT_PLAN_PAGEABLE, MPT_MODE_PAGEABLE,
+                   MPT_NOALLOC_MAX_RANGES, MPT_MAX_PATHS, MPT_PATH_CE, MPT_PATH_HS, MPT_PATH_SM, MPT_PATH_ZC, MPT_SHARE_ONE, MPT_SM_BULK, MPT_SM_TILE8K, MPT_HS_HOST_THREADS, MPT_PLAN_PAGEABLE, MPT_MODE_PAGEABLE, MPT_BATCH_TUNE_TIME, MPT_BATCH_TUNE_P99,
                    MPT_SM_VEC128, MPT_PLAN_EAGER, MPT_MODE_GRAPH, MPT_MODE_EAGER, MPT_PREPARE_GRAPH,
                    MPT_PREPARE_EAGER, MPT_PREPARE_AUTO, STATUS_NAMES)
 from ._ffi import MPT_EAGAIN, MPT_ECUDA, MPT_EINVAL, MPT_ENOMEM, MPT_ENOTSUP, MPT_ETIMEDOUT, MPT_OK  # noqa: F401
@@ -278,6 +278,15 @@ def mpt_batch_submit(ctx: int, xfers, stream=None) -> int:
     h = C.c_void_p()
     _check(lib().mpt_batch_submit(ctx, arr, n, _stream(stream), C.byref(h)), "mpt_batch_submit")
     return h.value
+
+
+def mpt_batch_tune(ctx: int, xfers, objective: int = 0, reps: int = 0, stream=None) -> dict:
+    """Measure batch settings on a representative batch, apply the best; returns it."""
+    n = len(xfers)
+    arr = xfers if isinstance(xfers, C.Array) else make_xfers(xfers)
+    out = _ffi.mpt_batch_tuning()
+    _check(lib().mpt_batch_tune(ctx, arr, n, objective, reps, _stream(stream), C.byref(out)), "mpt_batch_tune")
+    return {name: getattr(out, name) for name, _ in _ffi.mpt_batch_tuning._fields_ if name != "reserved"}
 
 
 def mpt_batch_poll(batch: int, n: int | None = None):

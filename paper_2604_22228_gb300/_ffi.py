@@ -23,6 +23,7 @@ MPT_LAYOUT_CONTIG, MPT_LAYOUT_INTERLEAVE = 0, 1
 MPT_SM_VEC128, MPT_SM_BULK, MPT_SM_TILE8K = 0, 1, 2
 MPT_HS_HOST_THREADS = 1
 MPT_PLAN_PAGEABLE, MPT_MODE_PAGEABLE = 0x200, 0x10
+MPT_BATCH_TUNE_TIME, MPT_BATCH_TUNE_P99 = 0, 1
 MPT_PLAN_EAGER = 0x100
 MPT_MODE_GRAPH, MPT_MODE_EAGER = 0, 1
 MPT_PREPARE_GRAPH, MPT_PREPARE_EAGER, MPT_PREPARE_AUTO = 0, 1, 2
@@ -62,6 +63,12 @@ class mpt_model(C.Structure):
     _fields_ = [("launch_ps", C.c_uint64), ("hbm_Bps", C.c_uint64), ("link_h2d_Bps", C.c_uint64),
                 ("link_d2h_Bps", C.c_uint64), ("ce", mpt_path_model), ("sm", mpt_path_model),
                 ("hs", mpt_path_model), ("zc", mpt_path_model)]
+
+
+class mpt_batch_tuning(C.Structure):
+    _fields_ = [("ctas", C.c_uint32), ("tile_bytes", C.c_uint32), ("dma_lanes", C.c_uint32),
+                ("dma_items", C.c_uint32), ("dma_min_bytes", C.c_uint64), ("batch_us", C.c_double),
+                ("p99_us", C.c_double), ("candidates", C.c_uint32), ("reserved", C.c_uint32)]
 
 
 class mpt_serve_config(C.Structure):
@@ -125,6 +132,8 @@ SIGNATURES = {
                                P(C.c_double)]),
     "mpt_batch_configure": (C.c_int, [H, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32]),
     "mpt_batch_configure_dma": (C.c_int, [H, C.c_uint32, C.c_uint32, C.c_uint64]),
+    "mpt_batch_tune": (C.c_int, [H, C.c_void_p, C.c_size_t, C.c_uint32, C.c_uint32, C.c_void_p,
+                                 C.POINTER(mpt_batch_tuning)]),
     "mpt_batch_register": (C.c_int, [H, C.c_void_p, C.c_uint64]),
     "mpt_batch_submit": (C.c_int, [H, P(mpt_xfer), C.c_size_t, C.c_void_p, P(H)]),
     "mpt_batch_poll": (C.c_int, [H, P(C.c_size_t), P(C.c_uint8)]),

@@ -17,6 +17,7 @@
 // batch up to the slot capacity replays the same graph.
 #include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <cstdlib>
 #include <cstring>
 #include <thread>
@@ -326,6 +327,90 @@ mpt_status mpt_batch_configure_dma(mpt_ctx_t c, uint32_t lanes, uint32_t items_p
   c->batch_dma_min = lanes ? min_bytes : 0;
   c->batch_dma_set = true;
   return batch_setup(c);
+}
+
+mpt_status mpt_batch_tune(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, uint32_t objective, uint32_t reps, void* stream,
+                          mpt_batch_tuning* out) {
+  if (!c || !xfers || n == 0) return fail(MPT_EINVAL, "mpt_batch_tune: NULL or empty batch");
+  if (objective > MPT_BATCH_TUNE_P99) return fail(MPT_EINVAL, "mpt_batch_tune: unknown objective %u", objective);
+  for (auto& s : c->slots)
+    if (s.held) return fail(MPT_EAGAIN, "mpt_batch_tune: a batch is still held");
+  if (reps == 0) reps = 3;
+  const uint32_t sms = (uint32_t)c->sms;
+  struct Setting {
+    uint32_t ctas, tile, lanes, items;
+    uint64_t min;
+  };
+  std::vector<Setting> cand;
+  for (uint32_t k : {1u, 2u, 3u})
+    for (uint32_t tile : {64u << 10, 128u << 10, 256u << 10, 512u << 10, 1024u << 10})
+      for (uint32_t lanes : {0u, 2u}) cand.push_back(Setting{k * sms, tile, lanes, lanes ? 8u : 0u, lanes ? 4ull << 20 : 0});
+  const uint32_t keep_slots = c->batch_slots, keep_max = c->batch_max_xfers;
+  std::vector<uint64_t> t(n);
+  const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return fail(MPT_ECUDA, "mpt_batch_tune: events");
+  }
+  struct Events {
+    cudaEvent_t a, b;
+    ~Events() {
+      cudaEventDestroy(a);
+      cudaEventDestroy(b);
+    }
+  } ev{e0, e1};
+  mpt_batch_tuning best{};
+  double best_score = 1e300;
+  bool have = false;
+  for (const Setting& k : cand) {
+    c->batch_dma_lanes = k.lanes;
+    c->batch_dma_items = k.items;
+    c->batch_dma_min = k.min;
+    c->batch_dma_set = true;
+    mpt_status st = mpt_batch_configure(c, keep_slots, keep_max, k.ctas, k.tile);
+    if (st != MPT_OK) return st;
+    std::vector<double> times, p99s;
+    for (uint32_t r = 0; r < reps + 1; ++r) {
+      mpt_batch_t b = nullptr;
+      CUDA_TRY(cudaEventRecord(e0, cs));
+      st = mpt_batch_submit(c, xfers, n, stream, &b);
+      if (st != MPT_OK) return st;
+      if (cudaEventRecord(e1, cs) != cudaSuccess) st = fail(MPT_ECUDA, "mpt_batch_tune: event");
+      if (st == MPT_OK) st = mpt_batch_wait(b, 600ull * 1000000000ull);
+      if (st == MPT_OK) st = mpt_batch_times(b, t.data());
+      mpt_batch_release(b);
+      if (st != MPT_OK) return st;
+      float ms = 0;
+      CUDA_TRY(cudaEventSynchronize(e1));
+      CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+      if (r == 0) continue;  // the first run warms up
+      std::vector<uint64_t> sorted(t);
+      std::sort(sorted.begin(), sorted.end());
+      const size_t i99 = std::min(n - 1, (size_t)std::ceil(0.99 * (double)n) - (n > 0 ? 1 : 0));
+      p99s.push_back((double)sorted[i99] / 1e3);
+      times.push_back((double)ms * 1e3);
+    }
+    std::sort(times.begin(), times.end());
+    std::sort(p99s.begin(), p99s.end());
+    const double bt = times[times.size() / 2], p99 = p99s[p99s.size() / 2];
+    const double score = objective == MPT_BATCH_TUNE_P99 ? p99 : bt;
+    if (!have || score < best_score) {
+      have = true;
+      best_score = score;
+      best = mpt_batch_tuning{k.ctas, k.tile, k.lanes, k.items, k.min, bt, p99, 0, 0};
+    }
+  }
+  best.candidates = (uint32_t)cand.size();
+  c->batch_dma_lanes = best.dma_lanes;
+  c->batch_dma_items = best.dma_items;
+  c->batch_dma_min = best.dma_min_bytes;
+  c->batch_dma_set = true;
+  mpt_status st = mpt_batch_configure(c, keep_slots, keep_max, best.ctas, best.tile_bytes);
+  if (st != MPT_OK) return st;
+  if (out) *out = best;
+  return MPT_OK;
 }
 
 mpt_status mpt_batch_register(mpt_ctx_t c, const void* base, uint64_t bytes) {

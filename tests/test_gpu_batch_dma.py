@@ -90,3 +90,22 @@ def test_configure_dma_rejects_bad_values():
         mpt.mpt_batch_configure_dma(c, 0, 0, 0)  # lanes off
     finally:
         mpt.mpt_ctx_destroy(c)
+
+
+@pytest.mark.parametrize("objective", [mpt.MPT_BATCH_TUNE_TIME, mpt.MPT_BATCH_TUNE_P99])
+def test_batch_tune_applies_a_measured_setting(objective):
+    """mpt_batch_tune measures every candidate setting on the given batch, applies the best,
+    and later batches under it stay bit-exact."""
+    import torch
+    c = mpt.mpt_ctx_create(0)
+    try:
+        w = Workload(300, 4242, 4 * MiB, kind="u32")
+        r = mpt.mpt_batch_tune(c, w.xfers, objective, 1, torch.cuda.current_stream())
+        sms = mpt.mpt_ctx_info(c)["sms"]
+        assert r["candidates"] == 30 and r["ctas"] in (sms, 2 * sms, 3 * sms)
+        assert r["tile_bytes"] in [k << 10 for k in (64, 128, 256, 512, 1024)]
+        assert r["dma_lanes"] in (0, 2) and r["batch_us"] > 0 and r["p99_us"] > 0
+        w2 = Workload(300, 4243, 4 * MiB, kind="u32")
+        _run(c, w2, 300)
+    finally:
+        mpt.mpt_ctx_destroy(c)
