@@ -360,8 +360,9 @@ MPT_API mpt_status mpt_model_optimize(const mpt_model* m, uint64_t nbytes, uint3
 /* Measure candidate path sets for an `nbytes` message in direction `dir` and execution
  * mode `mode` (MPT_MODE_GRAPH or MPT_MODE_EAGER) on this context's GPU -- single copy
  * engine paths with 1..8 chunks, the SM kernel (vec128/bulk, several CTA counts), the
- * zero-copy kernel, copy engine + kernel splits at several shares and chunk counts, the
- * staged path -- each the median of `reps` timed runs (0 = default), every run starting
+ * zero-copy kernel, copy engine + kernel splits at several shares and chunk counts (a
+ * winning split is then refined in 1/64 steps of its share), the staged path -- each the
+ * median of `reps` timed runs (0 = default), every run starting
  * with a cold L2 full of dirty lines (a 256 MiB write first, as after the kernel that
  * produced the data; a message of at most 2 MiB is timed as the mean of 8 back-to-back
  * launches after it, the regime of a stream of short messages where launch costs overlap),

@@ -408,9 +408,9 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
   const uint32_t chain = nbytes <= kChainMaxBytes ? kChainLaunches : 1u;
   const char* vv = std::getenv("MPT_TUNE_VERBOSE");
   const bool verbose = vv && *vv && *vv != '0';
-  for (const Candidate& k : candidates(c, dir, nbytes, mode)) {
+  auto measure = [&](const Candidate& k) {
     mpt_plan_t plan = nullptr;
-    if (mpt_plan(nullptr, nbytes, dir, k.p, k.n, 16, MPT_LAYOUT_CONTIG, &plan) != MPT_OK) continue;
+    if (mpt_plan(nullptr, nbytes, dir, k.p, k.n, 16, MPT_LAYOUT_CONTIG, &plan) != MPT_OK) return;
     mpt_graph_s g;
     bool ok = true;
     if (graph_mode) ok = build_private_graph(c, plan, dst, src, &g) == MPT_OK;
@@ -434,7 +434,7 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
     mpt_plan_destroy(plan);
     if (!ok || ts.empty()) {
       cudaGetLastError();
-      continue;
+      return;
     }
     std::sort(ts.begin(), ts.end());
     const double us = 1e3 * ts[ts.size() / 2];
@@ -452,6 +452,23 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
       best.npaths = k.n;
       std::memcpy(best.paths, k.p, sizeof k.p);
       best.us = us;
+    }
+  };
+  for (const Candidate& k : candidates(c, dir, nbytes, mode)) measure(k);
+  // A two-path winner is refined in 1/64 steps of the message around its share (the coarse
+  // list steps by 1/16 .. 1/8); chunk sizes, CTAs and variants stay as they won.
+  if (best.npaths == 2) {
+    const TuneEntry coarse = best;
+    for (int step : {-2, -1, 1, 2}) {
+      const int64_t w = (int64_t)coarse.paths[0].share + step * (int64_t)(MPT_SHARE_ONE / 64);
+      if (w <= 0 || w >= (int64_t)MPT_SHARE_ONE) continue;
+      Candidate k{};
+      k.n = 2;
+      k.p[0] = coarse.paths[0];
+      k.p[1] = coarse.paths[1];
+      k.p[0].share = (uint32_t)w;
+      k.p[1].share = MPT_SHARE_ONE - (uint32_t)w;
+      measure(k);
     }
   }
   cudaEventDestroy(e0);
