@@ -595,7 +595,12 @@ def run_ours(args):
         ok = ok and batched["parity_ok"]
     serving = None
     if args.serve_seconds > 0:
-        serving = run_serving(mpt, torch, ctx, [float(r) for r in args.serve_rates.split(",")], args.serve_seconds)
+        rates = [float(r) for r in args.serve_rates.split(",")]
+        # the default: batches in flight on streams of their own, the batch kernel on one CTA
+        # per SM; then every batch in order on one stream with three CTAs per SM
+        serving = run_serving(mpt, torch, ctx, rates, args.serve_seconds)
+        serving += run_serving(mpt, torch, ctx, rates, args.serve_seconds, streams=1,
+                               batch_ctas=3 * ctx_sms(mpt, ctx))
         ok = ok and all(r["errors"] == 0 for r in serving)
 
     if args.tune_out:
@@ -807,6 +812,10 @@ def time_back_to_back(mpt, torch, stream, handles, max_k=10000):
     return out
 
 
+def ctx_sms(mpt, ctx) -> int:
+    return int(mpt.mpt_ctx_info(ctx)["sms"])
+
+
 def _percentile(xs, q):
     xs = sorted(xs)
     if not xs:
@@ -928,11 +937,12 @@ def run_batched(mpt, torch, ctx, stream, reps=5):
         "parity_ok": bool(ok)}
 
 
-def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30):
+def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30, streams=0, batch_ctas=0):
     """Open-loop Poisson arrivals (lognormal sizes, median 1 MiB, sigma 1.5, cap 256 MiB,
     50/25/25 directions) through the continuous-batching server; latency from the scheduled
-    arrival to the completion flag; 1% of requests and every request above 64 MiB verified
-    by digest right after completion."""
+    arrival to the completion flag (p50/p99), and from the client's actual submit call
+    (server_p50/p99: without the Python client's own lateness); 1% of requests and every
+    request above 64 MiB verified by digest right after completion."""
     import collections
 
     import payload
@@ -954,20 +964,21 @@ def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30):
         heads = {"dev": 0, "host": 0}
         outstanding = {"dev": collections.deque(), "host": collections.deque()}
         finished = set()
-        lat, late, verified, bad = [], [], 0, 0
+        lat, slat, late, verified, bad = [], [], [], 0, 0
         moved = 0
-        server = mpt.mpt_serve_start(ctx, staging_budget_bytes=budget)
+        server = mpt.mpt_serve_start(ctx, staging_budget_bytes=budget, streams=streams, batch_ctas=batch_ctas)
         meta = {}
 
         def harvest():
             nonlocal verified, bad, moved
             for tag, arr, adm, comp, nb, st in mpt.mpt_serve_poll(server):
-                kind, off, sp, dp = meta.pop(tag)
+                kind, off, sp, dp, t_sub = meta.pop(tag)
                 finished.add(tag)
                 if st != mpt.MPT_OK:
                     bad += 1
                     continue
                 lat.append((comp - arr) / 1e3)
+                slat.append((comp - t_sub) / 1e3)
                 moved += nb
                 if tag % 100 == 0 or nb > 64 * MiB:
                     h = mpt.mpt_hash_ranges_noalloc([(dp, nb), (sp, nb)], vstream)
@@ -1013,8 +1024,9 @@ def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30):
             s_t = src_host if d == mpt.MPT_H2D else src_dev
             soff = (payload.splitmix64_scalar(payload.SEED_SERVE, 1 << 40 | k) % (s_t.numel() - nb)) & ~255
             sp, dp = s_t.data_ptr() + soff, ring[kind].data_ptr() + start
-            meta[k] = (kind, start, sp, dp)
-            late.append((mpt.mpt_now_ns() - due) / 1e3)
+            t_sub = mpt.mpt_now_ns()
+            meta[k] = (kind, start, sp, dp, t_sub)
+            late.append((t_sub - due) / 1e3)
             mpt.mpt_serve_submit(server, sp, dp, nb, d, k, due)
         t_end_sched = t0 + int(seconds * 1e9)
         while meta:
@@ -1023,7 +1035,9 @@ def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30):
         stats = mpt.mpt_serve_stats(server)
         mpt.mpt_serve_stop(server)
         out.append({"rate_per_s": rate, "seconds": seconds, "requests": len(sched),
+                    "streams": streams or "one per batch in flight", "batch_ctas": batch_ctas or "one per SM",
                     "p50_us": round(_percentile(lat, 50), 1), "p99_us": round(_percentile(lat, 99), 1),
+                    "server_p50_us": round(_percentile(slat, 50), 1), "server_p99_us": round(_percentile(slat, 99), 1),
                     "gbs": round(moved / max(wall, 1e-9) / 1e9, 2), "offered_gbs": round(sum(x[1] for x in sched) / seconds / 1e9, 2),
                     "batches": stats["batches"], "max_inflight_bytes": stats["max_inflight_bytes"],
                     "submit_late_p99_us": round(_percentile(late, 99), 1), "verified": verified, "errors": bad,

@@ -476,6 +476,10 @@ typedef struct {
   uint64_t staging_budget_bytes;  /* admission limit on bytes in flight (0 = $MPT_STAGING_BUDGET, else 8 GiB) */
   uint32_t max_batch;             /* transfers per batch (0 = the slot capacity) */
   uint32_t max_inflight_batches;  /* batches on the GPU at once (0 = every slot) */
+  uint32_t streams;               /* streams batches are launched on (0 = one per batch in flight;
+                                     1 = every batch in submission order) */
+  uint32_t batch_ctas;            /* batch kernel CTAs (0 = one per SM, so that several batch
+                                     kernels share the SMs); the ring keeps it after the server stops */
 } mpt_serve_config;
 
 /* One finished request: its tag, the arrival time the caller gave, when it was admitted
@@ -504,7 +508,11 @@ MPT_API uint64_t mpt_now_ns(void);
  * request larger than the whole budget runs alone), packs them into the next batch, and
  * launches it as soon as a batch slot is free, so requests arriving while earlier batches
  * run overlap with them on the device.  Each request completes individually when the
- * batch kernel raises its flag. */
+ * batch kernel raises its flag.  By default each batch in flight gets a stream of its own
+ * and the batch kernel one CTA per SM, so a batch of short requests runs beside an earlier
+ * batch with a long one instead of behind it (on GB300 at 50k requests/s: p50 49 us against
+ * 152 us in order, p99 from submit 572 us against 1.19 ms); requests in flight are then
+ * unordered and must not share destination bytes. */
 MPT_API mpt_status mpt_serve_start(mpt_ctx_t ctx, const mpt_serve_config* cfg, mpt_server_t* out);
 
 /* Enqueue one request (thread-safe).  arrival_ns: the request's scheduled arrival on the

@@ -315,8 +315,9 @@ def mpt_now_ns() -> int:
     return lib().mpt_now_ns()
 
 
-def mpt_serve_start(ctx: int, staging_budget_bytes: int = 0, max_batch: int = 0, max_inflight_batches: int = 0) -> int:
-    cfg = _ffi.mpt_serve_config(staging_budget_bytes, max_batch, max_inflight_batches)
+def mpt_serve_start(ctx: int, staging_budget_bytes: int = 0, max_batch: int = 0, max_inflight_batches: int = 0,
+                    streams: int = 0, batch_ctas: int = 0) -> int:
+    cfg = _ffi.mpt_serve_config(staging_budget_bytes, max_batch, max_inflight_batches, streams, batch_ctas)
     h = C.c_void_p()
     _check(lib().mpt_serve_start(ctx, C.byref(cfg), C.byref(h)), "mpt_serve_start")
     return h.value

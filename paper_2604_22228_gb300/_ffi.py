@@ -73,7 +73,7 @@ class mpt_batch_tuning(C.Structure):
 
 class mpt_serve_config(C.Structure):
     _fields_ = [("staging_budget_bytes", C.c_uint64), ("max_batch", C.c_uint32),
-                ("max_inflight_batches", C.c_uint32)]
+                ("max_inflight_batches", C.c_uint32), ("streams", C.c_uint32), ("batch_ctas", C.c_uint32)]
 
 
 class mpt_completion(C.Structure):

@@ -13,6 +13,9 @@
 //      still on the GPU wait only for a slot, not for those batches to finish, so their
 //      work overlaps on the device -- the windowed, many-in-flight regime where the paper
 //      finds graphs pay off (Sec. 5.3).
+// Batches in flight run on streams of their own (by default) and the batch kernel takes one
+// CTA per SM, so several batch kernels share the SMs: a batch of short requests is not held
+// behind an earlier batch with a long one.
 // Latency is measured from the scheduled arrival time the caller passes, so a late caller
 // does not hide queueing delay.
 #include <algorithm>
@@ -43,6 +46,7 @@ struct Request {
 
 struct InFlight {
   mpt_batch_t batch;
+  uint32_t stream;                // index into the server's streams
   std::vector<Request> reqs;
   std::vector<uint8_t> flags;     // last poll: 1 = finished
   std::vector<uint8_t> reported;  // completion already handed out
@@ -55,7 +59,7 @@ struct InFlight {
 struct mpt_server_s {
   mpt_ctx_t ctx = nullptr;
   mpt_serve_config cfg{};
-  cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> streams;
   std::thread worker;
   std::mutex mu;  // guards incoming, completions, stop, error
   std::condition_variable cv;
@@ -87,6 +91,7 @@ void serve_loop(mpt_server_s* s) {
   uint64_t budget_used = 0;
   std::vector<mpt_xfer> xs;
   std::vector<mpt_completion> done_local;
+  std::vector<uint8_t> stream_busy(s->streams.size(), 0);  // a stream per batch in flight
   while (true) {
     bool stopping;
     {
@@ -121,6 +126,7 @@ void serve_loop(mpt_server_s* s) {
       }
       if (f.ndone == f.reqs.size() && mpt_batch_wait(f.batch, 0) == MPT_OK) {
         mpt_batch_release(f.batch);
+        stream_busy[f.stream] = 0;
         flight[i] = std::move(flight.back());
         flight.pop_back();
       } else {
@@ -142,14 +148,21 @@ void serve_loop(mpt_server_s* s) {
     s->inflight_bytes = budget_used;
     if (budget_used > s->max_inflight_bytes) s->max_inflight_bytes = budget_used;
     // 3. launch when a slot is free
-    if (!building.empty() && flight.size() < s->cfg.max_inflight_batches) {
+    // one stream: batches run in submission order; several: each batch in flight has its own
+    uint32_t si = 0;
+    if (s->streams.size() > 1) {
+      while (si < stream_busy.size() && stream_busy[si]) ++si;
+    }
+    if (!building.empty() && flight.size() < s->cfg.max_inflight_batches && si < s->streams.size()) {
       xs.resize(building.size());
       for (size_t k = 0; k < building.size(); ++k) xs[k] = building[k].x;
       mpt_batch_t b = nullptr;
-      const mpt_status st = mpt_batch_submit(s->ctx, xs.data(), xs.size(), s->stream, &b);
+      const mpt_status st = mpt_batch_submit(s->ctx, xs.data(), xs.size(), s->streams[si], &b);
       if (st == MPT_OK) {
+        if (s->streams.size() > 1) stream_busy[si] = 1;
         InFlight f;
         f.batch = b;
+        f.stream = si;
         f.reqs = std::move(building);
         f.flags.assign(f.reqs.size(), 0);
         f.reported.assign(f.reqs.size(), 0);
@@ -192,10 +205,15 @@ uint64_t mpt_now_ns(void) { return steady_ns(); }
 mpt_status mpt_serve_start(mpt_ctx_t ctx, const mpt_serve_config* cfg, mpt_server_t* out) {
   if (!ctx || !out) return fail(MPT_EINVAL, "mpt_serve_start: NULL argument");
   *out = nullptr;
-  mpt_status st = batch_setup(ctx);
-  if (st != MPT_OK) return st;
   for (auto& sl : ctx->slots)
     if (sl.held) return fail(MPT_EAGAIN, "mpt_serve_start: batches of this context are still held");
+  const uint32_t want_ctas = cfg && cfg->batch_ctas ? cfg->batch_ctas : (uint32_t)ctx->sms;
+  if (want_ctas != ctx->batch_ctas) {
+    mpt_status st = mpt_batch_configure(ctx, ctx->batch_slots, ctx->batch_max_xfers, want_ctas, ctx->batch_tile);
+    if (st != MPT_OK) return st;
+  }
+  mpt_status st = batch_setup(ctx);
+  if (st != MPT_OK) return st;
   mpt_server_s* s = new mpt_server_s;
   s->ctx = ctx;
   mpt_serve_config c = cfg ? *cfg : mpt_serve_config{};
@@ -207,12 +225,21 @@ mpt_status mpt_serve_start(mpt_ctx_t ctx, const mpt_serve_config* cfg, mpt_serve
   if (c.max_batch == 0 || c.max_batch > ctx->slots[0].max_xfers) c.max_batch = ctx->slots[0].max_xfers;
   if (c.max_inflight_batches == 0 || c.max_inflight_batches > ctx->slots.size())
     c.max_inflight_batches = (uint32_t)ctx->slots.size();
+  if (c.streams == 0 || c.streams > c.max_inflight_batches) c.streams = c.max_inflight_batches;
+  c.batch_ctas = want_ctas;
   s->cfg = c;
-  if (cudaSetDevice(ctx->device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaSetDevice(ctx->device) != cudaSuccess) {
     delete s;
-    return fail(MPT_ECUDA, "mpt_serve_start: stream");
+    return fail(MPT_ECUDA, "mpt_serve_start: device");
   }
+  s->streams.assign(c.streams, nullptr);
+  for (auto& cs : s->streams)
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+      for (auto& x : s->streams)
+        if (x) cudaStreamDestroy(x);
+      delete s;
+      return fail(MPT_ECUDA, "mpt_serve_start: stream");
+    }
   s->worker = std::thread(serve_loop, s);
   *out = s;
   return MPT_OK;
@@ -265,8 +292,10 @@ mpt_status mpt_serve_stop(mpt_server_t s) {
   mpt_status st = s->error;
   if (st != MPT_OK) fail(st, "mpt_serve_stop: server failed: %s", s->error_msg.c_str());
   // completions not yet polled are dropped with the server
-  cudaStreamSynchronize(s->stream);
-  cudaStreamDestroy(s->stream);
+  for (cudaStream_t cs : s->streams) {
+    cudaStreamSynchronize(cs);
+    cudaStreamDestroy(cs);
+  }
   delete s;
   return st;
 }

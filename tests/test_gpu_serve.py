@@ -80,9 +80,15 @@ def run(server, ar, order, one_at_a_time, timeout=60):
     return done
 
 
-def test_results_same_alone_and_in_the_mix(ctx):
+@pytest.mark.parametrize("streams,ctas", [(1, -3), (0, 0)], ids=["in_order", "concurrent"])
+def test_results_same_alone_and_in_the_mix(ctx, streams, ctas):
+    """Each request's result is the same alone and in the mix -- with batches in submission
+    order on one stream (three CTAs per SM), and with batches in flight on streams of their
+    own (the default: one CTA per SM, batch kernels sharing the SMs)."""
     ar = Arenas(400, payload.SEED_SERVE)
-    server = mpt.mpt_serve_start(ctx)
+    if ctas < 0:  # -k: k CTAs per SM
+        ctas = -ctas * mpt.mpt_ctx_info(ctx)["sms"]
+    server = mpt.mpt_serve_start(ctx, streams=streams, batch_ctas=ctas)
     alone = run(server, ar, range(len(ar.reqs)), one_at_a_time=True)
     assert len(alone) == len(ar.reqs) and all(c[5] == mpt.MPT_OK for c in alone.values())
     h_alone = ar.digests("dst")
