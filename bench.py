@@ -1346,6 +1346,31 @@ def run_jacobi(mpt, torch, ctx, iters=20):
     return out
 
 
+def run_kernel_only_jacobi(args, mpt, torch):
+    """The Jacobi sweep alone on one subdomain of 8 rows x (kernel_bytes / 4 / 8) fp32 columns
+    plus halos: K launches timed with CUDA events, algorithmic bytes (rows + 2) read + rows
+    written."""
+    rows = 8
+    cols = max(4, args.kernel_bytes // 4 // rows // 4 * 4)
+    a = torch.empty((rows + 2, cols), dtype=torch.float32, device="cuda").uniform_(-1, 1)
+    b = torch.zeros_like(a)
+    s = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        mpt.mpt_demo_jacobi_step(a, b, rows, cols, s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        mpt.mpt_demo_jacobi_step(a, b, rows, cols, s)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    moved = (2 * rows + 2) * cols * 4
+    print(json.dumps({"kernel": "jacobi", "rows": rows, "cols": cols, "launches": args.steps,
+                      "ms_per_launch": round(ms, 5), "gbs": round(moved / (ms / 1e3) / 1e9, 1),
+                      "algorithmic_bytes": moved, "ok": True}), flush=True)
+    return 0
+
+
 def run_kernel_only(args):
     """One kernel alone on one message (for profiling): K launches timed with CUDA events."""
     import torch
@@ -1354,6 +1379,8 @@ def run_kernel_only(args):
     from paper_2604_22228_gb300 import build
     build.build()
     n = args.kernel_bytes
+    if args.kernel_only == "jacobi":
+        return run_kernel_only_jacobi(args, mpt, torch)
     ctx = mpt.mpt_ctx_create(0)
     host = args.kernel_only in ("zc", "zc_d2h")
     if args.kernel_only == "zc":  # host -> device
@@ -1414,7 +1441,7 @@ def main(argv=None):
     ap.add_argument("--tune", choices=["online", "model"], default="online",
                     help="online: measure every size bucket with mpt_tune before capturing; model: cost model only")
     ap.add_argument("--tune-out", default=None, help="write the tuned table (JSON lines) here")
-    ap.add_argument("--kernel-only", choices=["vec", "vec8k", "bulk", "zc", "zc_d2h"], default=None,
+    ap.add_argument("--kernel-only", choices=["vec", "vec8k", "bulk", "zc", "zc_d2h", "jacobi"], default=None,
                     help="time one copy kernel alone on --kernel-bytes (profiling)")
     ap.add_argument("--kernel-bytes", type=int, default=256 * MiB)
     ap.add_argument("--kernel-ctas", type=int, default=0)
