@@ -12,8 +12,10 @@
  *   MPT_PATH_SM  a copy kernel driven by the SMs (device-to-device only);
  *   MPT_PATH_HS  a two-hop staged route, hop two of a chunk after its hop one
  *                (Algorithm 2 "StageHostCopy"): device-to-device goes through pinned
- *                host memory; host-to-device and device-to-host go through a device
- *                stage, chained by device-side chunk-ready flags;
+ *                host slots (three by default, MPT_STAGE_SLOTS = 2..4; the paper double
+ *                buffers); host-to-device and device-to-host go through a device stage,
+ *                chained by device-side chunk-ready flags, or with MPT_HS_HOST_THREADS
+ *                through pinned slots filled and drained by host threads;
  *   MPT_PATH_ZC  a zero-copy kernel that reads or writes mapped pinned host memory
  *                directly over the host link (host-to-device and device-to-host only).
  *
@@ -26,7 +28,8 @@
  *     and kernels can reach them -- except on devices that reach pageable memory directly
  *     (cudaDevAttrPageableMemoryAccess, e.g. GB300 with its coherent Grace host), where
  *     plans made only of zero-copy paths, batches and mpt_sm_copy also accept ordinary
- *     pageable host memory.
+ *     pageable host memory.  Plans made only of zero-copy and host-thread staging paths
+ *     (MPT_HS_HOST_THREADS) accept it on any device where those paths can run.
  *   - A context (mpt_ctx_t) owns its streams, events, staging buffers, device status
  *     word, graph cache and tuner cache.  One host thread per context.
  *   - Asynchronous calls only enqueue work; results are valid after the stream the work

@@ -13,6 +13,8 @@
 
 namespace mpt {
 
+constexpr uint32_t kMaxStageSlots = 4;
+
 struct GraphKey {
   uint64_t src, dst, nbytes, dir, plan_hash;
   bool operator==(const GraphKey& o) const {
@@ -27,9 +29,9 @@ struct GraphKeyHash {
 // two-slot staging ring, and the lane's staging buffers (grown on demand).
 struct EagerLane {
   cudaStream_t s[2] = {nullptr, nullptr};
-  cudaEvent_t hop1[2] = {nullptr, nullptr};
-  cudaEvent_t hop2[2] = {nullptr, nullptr};
-  unsigned long long hop2_capture[2] = {0, 0};  // capture id the hop2 event was recorded in (0 = none)
+  cudaEvent_t hop1[kMaxStageSlots] = {};
+  cudaEvent_t hop2[kMaxStageSlots] = {};
+  unsigned long long hop2_capture[kMaxStageSlots] = {};  // capture id the hop2 event was recorded in (0 = none)
   cudaEvent_t done = nullptr;
   cudaEvent_t t0 = nullptr, t1 = nullptr;      // lane timers (MPT_TRACE_LANES)
   void* host_stage = nullptr;
@@ -123,6 +125,7 @@ struct mpt_ctx_s {
   bool trace_lanes = false;    // time every lane of multi-path eager launches
   uint32_t traced = 0;         // lanes timed by the last such launch
   bool pdl = true;             // direct kernel issue overlaps the previous copy kernel's end
+  uint32_t stage_slots = 3;    // pinned slots of the device-to-device host-staged path (MPT_STAGE_SLOTS)
   std::unique_ptr<mpt::HostCopyPool> host_pool;  // CPU hops of host-thread staging (made on first use)
   unsigned host_threads = 0;   // pool workers (MPT_HOST_THREADS; 0 = min(8, cores / 2) - 1)
   std::map<uint32_t, mpt::TuneEntry> tuned;  // tune_key -> choice

@@ -349,17 +349,19 @@ mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const voi
             prev_hop2[slot] = h2;
           }
         } else if (plan->dir == MPT_D2D) {
-          // Algorithm 2 StageHostCopy: device -> pinned host slot -> device, two slots;
-          // hop two of chunk k after its hop one, hop one of chunk k+2 after hop two of k.
+          // Algorithm 2 StageHostCopy: device -> pinned host slot -> device; hop two of chunk k
+          // after its hop one, hop one of chunk k+S after hop two of chunk k.  The paper double
+          // buffers (S = 2); three slots keep both link directions busier (MPT_STAGE_SLOTS).
           void* stage = nullptr;
-          mpt_status sa = get_host(2 * cb, &stage);
+          const uint32_t S = c->stage_slots;
+          mpt_status sa = get_host(S * cb, &stage);
           if (sa != MPT_OK) return sa;
-          info.staging_bytes += 2 * cb;
+          info.staging_bytes += S * cb;
           uint8_t* st8 = static_cast<uint8_t*>(stage);
-          cudaGraphNode_t prev_hop2[2] = {nullptr, nullptr};
+          cudaGraphNode_t prev_hop2[kMaxStageSlots] = {};
           for (uint32_t i = lo; i < hi; ++i) {
             const mpt_chunk& ch = plan->chunks[i];
-            const uint32_t slot = (i - lo) & 1u;
+            const uint32_t slot = (i - lo) % S;
             cudaGraphNode_t h1, h2;
             CUDA_TRY(cudaGraphAddMemcpyNode1D(&h1, g->graph, prev_hop2[slot] ? &prev_hop2[slot] : nullptr,
                                               prev_hop2[slot] ? 1 : 0, st8 + slot * cb, s8 + ch.offset, ch.bytes,
@@ -639,7 +641,8 @@ mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src
       if (plan->first_chunk[p + 1] == plan->first_chunk[p] || plan->paths[p].kind != MPT_PATH_HS) continue;
       const EagerLane& L = c->lane[p];
       const uint64_t have = plan->dir == MPT_D2D ? L.host_stage_bytes : L.dev_stage_bytes;
-      if (have < 2 * plan->paths[p].chunk_bytes)
+      const uint64_t slots = plan->dir == MPT_D2D ? c->stage_slots : 2u;
+      if (have < slots * plan->paths[p].chunk_bytes)
         return fail(MPT_EINVAL, "mpt_launch_eager: the staged path allocates its staging on first use, which a "
                                 "stream capture forbids; run the transfer once before capturing it");
     }
@@ -719,18 +722,20 @@ mpt_status eager(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const void* src
           break;
         }
         uint8_t* stage;
+        // device-to-device: the context's pinned slot count; host<->device: two device slots
+        const uint32_t S = plan->dir == MPT_D2D ? c->stage_slots : 2u;
         if (plan->dir == MPT_D2D) {
-          mpt_status st = grow_host(L, 2 * cb);
+          mpt_status st = grow_host(L, S * cb);
           if (st != MPT_OK) return st;
           stage = static_cast<uint8_t*>(L.host_stage);
         } else {
-          mpt_status st = grow_dev(L, 2 * cb);
+          mpt_status st = grow_dev(L, S * cb);
           if (st != MPT_OK) return st;
           stage = static_cast<uint8_t*>(L.dev_stage);
         }
         for (uint32_t i = lo; i < hi; ++i) {
           const mpt_chunk& ch = plan->chunks[i];
-          const uint32_t slot = (i - lo) & 1u;
+          const uint32_t slot = (i - lo) % S;
           uint8_t* sl = stage + slot * cb;
           // hop one may refill this slot only after the slot's previous hop two -- when that
           // hop two belongs to the same capture (or neither is captured): a capture cannot
@@ -830,12 +835,13 @@ mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out) {
   if (cudaMemset(words, 0, 256) != cudaSuccess) return bail(fail(MPT_ECUDA, "mpt_ctx_create: memset"));
   for (uint32_t p = 0; p < MPT_MAX_PATHS; ++p) {
     EagerLane& L = c->lane[p];
-    for (int i = 0; i < 2; ++i) {
-      if (cudaStreamCreateWithFlags(&L.s[i], cudaStreamNonBlocking) != cudaSuccess ||
-          cudaEventCreateWithFlags(&L.hop1[i], cudaEventDisableTiming) != cudaSuccess ||
+    for (int i = 0; i < 2; ++i)
+      if (cudaStreamCreateWithFlags(&L.s[i], cudaStreamNonBlocking) != cudaSuccess)
+        return bail(fail(MPT_ECUDA, "mpt_ctx_create: streams"));
+    for (uint32_t i = 0; i < kMaxStageSlots; ++i)
+      if (cudaEventCreateWithFlags(&L.hop1[i], cudaEventDisableTiming) != cudaSuccess ||
           cudaEventCreateWithFlags(&L.hop2[i], cudaEventDisableTiming) != cudaSuccess)
-        return bail(fail(MPT_ECUDA, "mpt_ctx_create: streams/events"));
-    }
+        return bail(fail(MPT_ECUDA, "mpt_ctx_create: events"));
     if (cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreate(&L.t0) != cudaSuccess || cudaEventCreate(&L.t1) != cudaSuccess)
       return bail(fail(MPT_ECUDA, "mpt_ctx_create: events"));
@@ -851,6 +857,7 @@ mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out) {
   c->rebind_enabled = env_u64("MPT_GRAPH_REBIND", 1) != 0;
   c->trace_lanes = env_u64("MPT_TRACE_LANES", 0) != 0;
   c->pdl = env_u64("MPT_PDL", 1) != 0;
+  c->stage_slots = (uint32_t)std::min<uint64_t>(kMaxStageSlots, std::max<uint64_t>(2, env_u64("MPT_STAGE_SLOTS", 3)));
   c->host_threads = (unsigned)std::min<uint64_t>(256, env_u64("MPT_HOST_THREADS", 0));
   const char* tf = tune_file && *tune_file ? tune_file : std::getenv("MPT_TUNE_FILE");
   if (tf && *tf) {
@@ -894,8 +901,9 @@ mpt_status mpt_ctx_destroy(mpt_ctx_t c) {
   c->live.clear();
   for (uint32_t p = 0; p < MPT_MAX_PATHS; ++p) {
     EagerLane& L = c->lane[p];
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 2; ++i)
       if (L.s[i]) cudaStreamDestroy(L.s[i]);
+    for (uint32_t i = 0; i < kMaxStageSlots; ++i) {
       if (L.hop1[i]) cudaEventDestroy(L.hop1[i]);
       if (L.hop2[i]) cudaEventDestroy(L.hop2[i]);
     }

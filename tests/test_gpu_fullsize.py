@@ -94,3 +94,57 @@ def test_digest_of_full_message_matches_oracle(ctx):
     data = payload.fill("f32", payload.SEED_D2D_SWEEP, n)
     t = torch.from_numpy(data).cuda()
     assert mpt.mpt_hash_device(ctx, t.data_ptr(), n) == T.hash64(data)
+
+
+def _tiled_source(n, seed):
+    """n bytes on the device: the seeded u32 payload repeated with a period that does not
+    divide 2^32, so a 64-bit offset truncated to 32 bits reads different bytes."""
+    import torch
+    period = GiB - 28672
+    base_np = payload.fill("u32", seed, period)
+    base = torch.from_numpy(base_np).cuda()
+    src = torch.empty(n, dtype=torch.uint8, device="cuda")
+    for o in range(0, n, period):
+        m = min(period, n - o)
+        src[o:o + m].copy_(base[:m])
+    return src, base_np, period
+
+
+@pytest.mark.parametrize("case", ["sm_eager", "sm_graph", "sm8k_graph", "bulk_graph", "ce_sm_graph", "batch"])
+def test_d2d_beyond_4gib(ctx, case):
+    """A message above 4 GiB: 64-bit offsets in every path (kernel tile offsets, copy-engine
+    chunk offsets, batch descriptors).  Whole-buffer digest, untouched tail, and windows at
+    the 4 GiB boundary against the oracle's bytes."""
+    import torch
+    n = 4 * GiB + 4096 + 13
+    src, base_np, period = _tiled_source(n, payload.SEED_D2D_SWEEP + 5)
+    dst = torch.zeros(n + 4096, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream()
+    if case == "batch":
+        xf = [(src.data_ptr(), dst.data_ptr(), n, mpt.MPT_D2D)]
+        b = mpt.mpt_batch_submit(ctx, xf, s)
+        mpt.mpt_batch_wait(b)
+        done, _ = mpt.mpt_batch_poll(b, 1)
+        mpt.mpt_batch_release(b)
+        assert done == 1
+    else:
+        specs = {
+            "sm_eager": [(mpt.MPT_PATH_SM, 65536, n // 16 * 16 + 16)],
+            "sm_graph": [(mpt.MPT_PATH_SM, 65536, GiB)],
+            "sm8k_graph": [(mpt.MPT_PATH_SM, 65536, GiB, 0, mpt.MPT_SM_TILE8K)],
+            "bulk_graph": [(mpt.MPT_PATH_SM, 65536, GiB, 0, mpt.MPT_SM_BULK)],
+            "ce_sm_graph": [(mpt.MPT_PATH_CE, 32768, GiB), (mpt.MPT_PATH_SM, 32768, 512 * MiB)],
+        }[case]
+        plan = mpt.mpt_plan(ctx, n, mpt.MPT_D2D, specs)
+        mode = mpt.MPT_PREPARE_EAGER if case.endswith("eager") else mpt.MPT_PREPARE_GRAPH
+        h = mpt.mpt_prepare(ctx, plan, dst.data_ptr(), src.data_ptr(), mode)
+        mpt.mpt_launch(h, s)
+        mpt.mpt_graph_release(h)
+        mpt.mpt_plan_destroy(plan)
+    torch.cuda.synchronize()
+    assert mpt.mpt_hash_device(ctx, dst.data_ptr(), n) == mpt.mpt_hash_device(ctx, src.data_ptr(), n)
+    assert int(dst[n:].sum()) == 0
+    for off in (0, (1 << 32) - 2048, 1 << 32, n - 4096):
+        p = off % period
+        want = base_np[p:p + 4096] if p + 4096 <= period else np.concatenate([base_np[p:], base_np[:p + 4096 - period]])
+        assert np.array_equal(dst[off:off + 4096].cpu().numpy(), T.copy(want)), off
