@@ -399,17 +399,23 @@ def run_ours(args):
     dev_elapsed = t_start.elapsed_time(t_end) / 1e3
     value, slowest = aggregate(world, total_bytes * args.steps, dev_elapsed)
 
-    # ---- per-size breakdown: the same sweeps with an event after every message ----
-    bk = max(3, min(args.steps, 20))
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(nsz + 1)] for _ in range(bk)]
-    for k in range(bk):
-        ev[k][0].record(stream)
-        for i, g in enumerate(step_handles):
-            mpt.mpt_launch(g, stream)
-            ev[k][i + 1].record(stream)
-    stream.synchronize()
-    per_size_tuned = [statistics.median(ev[k][i].elapsed_time(ev[k][i + 1]) for k in range(bk))
-                      for i in range(nsz)]
+    # ---- per-size breakdown: each message's marginal cost inside the sweep, the time of the
+    # sweep minus the time of the same sweep without that message (events only around whole
+    # sweeps, so launches keep overlapping as in the timed region) ----
+    def sweep_ms(handles, reps=20, blocks=3):
+        out_ = []
+        for _ in range(blocks):
+            t_a.record(stream)
+            for _ in range(reps):
+                for h in handles:
+                    mpt.mpt_launch(h, stream)
+            t_b.record(stream)
+            t_b.synchronize()
+            out_.append(t_a.elapsed_time(t_b) / reps)
+        return statistics.median(out_)
+    t_a, t_b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    full_ms = sweep_ms(step_handles)
+    per_size_tuned = [max(1e-6, full_ms - sweep_ms(step_handles[:i] + step_handles[i + 1:])) for i in range(nsz)]
 
     # ---- per-size baselines (not part of value) ----
     def time_graphs(graphs, reps):
@@ -617,7 +623,8 @@ def run_ours(args):
     sweep = []
     for i, n in enumerate(SIZES):
         gb = lambda ms: round(n / (ms / 1e3) / 1e9, 3) if ms and ms > 0 else None
-        row = {"bytes": n, "in_sweep_gbs": gb(per_size_tuned[i]), "mode": step_modes[i],
+        row = {"bytes": n, "in_sweep_us": round(per_size_tuned[i] * 1e3, 2), "in_sweep_gbs": gb(per_size_tuned[i]),
+               "mode": step_modes[i],
                "plan": [(p["kind"], p["share"], p["chunk_bytes"], p["ctas"], p["flags"])
                         for p in mpt.mpt_plan_paths(step_plans[i])]}
         if base:

@@ -367,8 +367,9 @@ MPT_API mpt_status mpt_model_optimize(const mpt_model* m, uint64_t nbytes, uint3
  * winning split is then refined in 1/64 steps of its share), the staged path -- each the
  * median of `reps` timed runs (0 = default), every run starting
  * with a cold L2 full of dirty lines (a 256 MiB write first, as after the kernel that
- * produced the data; a message of at most 2 MiB is timed as the mean of 8 back-to-back
- * launches after it, the regime of a stream of short messages where launch costs overlap),
+ * produced the data; a message of at most 64 MiB is timed as the mean of 8 back-to-back
+ * launches after it, each on its own buffer region -- the regime of a stream of messages,
+ * where launch costs overlap),
  * and store the fastest for the message's log2 size bucket.  With mode | MPT_MODE_PAGEABLE
  * (H2D/D2H) the host buffer is ordinary pageable memory and the candidates are the paths
  * that accept it: the zero-copy kernel, host-thread staging (MPT_HS_HOST_THREADS) and their

@@ -261,8 +261,8 @@ mpt_status tuner_fill(mpt_ctx_t ctx, uint64_t nbytes, uint32_t dir, uint32_t mod
 
 namespace {
 
-constexpr uint64_t kChainMaxBytes = 2ull << 20;  // messages timed as launch chains
-constexpr uint32_t kChainLaunches = 8;
+constexpr uint64_t kChainMaxBytes = 64ull << 20;  // messages timed as launch chains
+constexpr uint32_t kChainLaunches = 8;             // launches per chain, one buffer region each
 
 struct Candidate {
   uint32_t n;
@@ -367,28 +367,36 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
   if (nbytes == 0) return fail(MPT_EINVAL, "mpt_tune: empty message");
   if (reps == 0) reps = nbytes >= (256ull << 20) ? 3 : (nbytes >= (16ull << 20) ? 5 : 11);
   CUDA_TRY(cudaSetDevice(c->device));
+  // A message of at most 64 MiB is timed as a chain of back-to-back launches, each on its own
+  // buffer region (no launch finds the previous one's data in L2): in a stream of messages
+  // the fixed cost of a launch overlaps the copy before it (programmatic dependent launch of
+  // the copy kernels; copy engines queue their work), which a single launch after the flush
+  // cannot show, and a graph launch does not overlap that way.
+  const uint32_t chain = nbytes <= kChainMaxBytes ? kChainLaunches : 1u;
+  const uint64_t stride = (nbytes + 4095) / 4096 * 4096;
+  const uint64_t span = chain == 1 ? nbytes : chain * stride;
   // buffers: device a/b, page-locked host h, and a 256 MiB L2 flush buffer
-  mpt_status st = ensure_dev(c->tune_a, c->tune_dev_bytes, nbytes);
+  mpt_status st = ensure_dev(c->tune_a, c->tune_dev_bytes, span);
   if (st != MPT_OK) return st;
   if (c->tune_b) cudaFree(c->tune_b);
   c->tune_b = nullptr;
   CUDA_TRY(cudaMalloc(&c->tune_b, c->tune_dev_bytes));
-  if (pageable && c->tune_pg_bytes < nbytes) {
+  if (pageable && c->tune_pg_bytes < span) {
     std::free(c->tune_pg);
-    c->tune_pg = std::malloc(nbytes);
+    c->tune_pg = std::malloc(span);
     if (!c->tune_pg) {
       c->tune_pg_bytes = 0;
-      return fail(MPT_ENOMEM, "mpt_tune: pageable host buffer of %llu bytes", (unsigned long long)nbytes);
+      return fail(MPT_ENOMEM, "mpt_tune: pageable host buffer of %llu bytes", (unsigned long long)span);
     }
-    std::memset(c->tune_pg, 0x5a, nbytes);  // touch every page before timing
-    c->tune_pg_bytes = nbytes;
+    std::memset(c->tune_pg, 0x5a, span);  // touch every page before timing
+    c->tune_pg_bytes = span;
   }
-  if (!pageable && dir != MPT_D2D && c->tune_host_bytes < nbytes) {
+  if (!pageable && dir != MPT_D2D && c->tune_host_bytes < span) {
     if (c->tune_h) cudaFreeHost(c->tune_h);
     c->tune_h = nullptr;
     c->tune_host_bytes = 0;
-    CUDA_TRY(cudaHostAlloc(&c->tune_h, nbytes, cudaHostAllocMapped | cudaHostAllocPortable));
-    c->tune_host_bytes = nbytes;
+    CUDA_TRY(cudaHostAlloc(&c->tune_h, span, cudaHostAllocMapped | cudaHostAllocPortable));
+    c->tune_host_bytes = span;
   }
   st = ensure_dev(c->flush, c->flush_bytes, 256ull << 20);
   if (st != MPT_OK) return st;
@@ -401,19 +409,16 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
   CUDA_TRY(cudaEventCreate(&e1));
   TuneEntry best;
   double best_us = 1e30;
-  // A message of at most 2 MiB is timed as a run of back-to-back launches: at that size the
-  // fixed cost of one launch, not the bytes, decides, and in a stream of messages that cost
-  // overlaps the copy before it (programmatic dependent launch of the copy kernels; copy
-  // engines queue their work) -- which a single launch after the flush cannot show.
-  const uint32_t chain = nbytes <= kChainMaxBytes ? kChainLaunches : 1u;
+  auto region = [&](void* base, uint32_t k) -> void* { return static_cast<uint8_t*>(base) + (uint64_t)k * stride; };
   const char* vv = std::getenv("MPT_TUNE_VERBOSE");
   const bool verbose = vv && *vv && *vv != '0';
   auto measure = [&](const Candidate& k) {
     mpt_plan_t plan = nullptr;
     if (mpt_plan(nullptr, nbytes, dir, k.p, k.n, 16, MPT_LAYOUT_CONTIG, &plan) != MPT_OK) return;
-    mpt_graph_s g;
+    std::vector<mpt_graph_s> g(graph_mode ? chain : 0);
     bool ok = true;
-    if (graph_mode) ok = build_private_graph(c, plan, dst, src, &g) == MPT_OK;
+    for (uint32_t k2 = 0; ok && k2 < g.size(); ++k2)
+      ok = build_private_graph(c, plan, region(dst, k2), region(src, k2), &g[k2]) == MPT_OK;
     std::vector<float> ts;
     for (uint32_t r = 0; ok && r < reps + 1; ++r) {
       // write 256 MiB (twice the L2) first, on the timing stream: each run starts with a cold
@@ -421,8 +426,8 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
       cudaMemsetAsync(c->flush, r & 0xff, c->flush_bytes, s);
       cudaEventRecord(e0, s);
       for (uint32_t k2 = 0; ok && k2 < chain; ++k2) {
-        if (graph_mode) ok = g.exec == nullptr || cudaGraphLaunch(g.exec, s) == cudaSuccess;
-        else ok = run_eager(c, plan, dst, src, s) == MPT_OK;
+        if (graph_mode) ok = g[k2].exec == nullptr || cudaGraphLaunch(g[k2].exec, s) == cudaSuccess;
+        else ok = run_eager(c, plan, region(dst, k2), region(src, k2), s) == MPT_OK;
       }
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
@@ -430,7 +435,7 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
       cudaEventElapsedTime(&ms, e0, e1);
       if (r > 0) ts.push_back(ms / (float)chain);  // the first run warms up
     }
-    if (graph_mode) free_private_graph(&g);
+    for (mpt_graph_s& gk : g) free_private_graph(&gk);
     mpt_plan_destroy(plan);
     if (!ok || ts.empty()) {
       cudaGetLastError();
