@@ -22,6 +22,7 @@ With --impl reference only the CPU oracle arm runs (the paper ships no code).
 from __future__ import annotations
 
 import argparse
+import ctypes
 import json
 import math
 import os
@@ -599,7 +600,7 @@ def run_ours(args):
     if not args.no_batched:
         batched = run_batched(mpt, torch, ctx, stream)
         ok = ok and batched["parity_ok"]
-    serving = None
+    serving = serving_replay = None
     if args.serve_seconds > 0:
         rates = [float(r) for r in args.serve_rates.split(",")]
         # the default: batches in flight on streams of their own, the batch kernel on one CTA
@@ -607,7 +608,10 @@ def run_ours(args):
         serving = run_serving(mpt, torch, ctx, rates, args.serve_seconds)
         serving += run_serving(mpt, torch, ctx, rates, args.serve_seconds, streams=1,
                                batch_ctas=3 * ctx_sms(mpt, ctx))
-        ok = ok and all(r["errors"] == 0 for r in serving)
+        mpt.mpt_batch_configure(ctx, 0, 0, 0, 0)
+        serving_replay = run_serving_replay(mpt, torch, ctx, rates, args.serve_seconds)
+        ok = ok and all(r["errors"] == 0 for r in serving + serving_replay)
+        ok = ok and all(r["destinations_disjoint_in_flight"] and r["completed"] == r["requests"] for r in serving_replay)
 
     if args.tune_out:
         mpt.mpt_tune_save(ctx, args.tune_out)
@@ -666,7 +670,8 @@ def run_ours(args):
                          "peak_source": f"{peak_kind} hbm_gbs (burst)"},
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": kernels_per_step * args.steps,
             "clocks": clk, "parity_ok": ok, "host_elapsed_s": round(host_elapsed, 4), "tune_s": round(tune_s, 2),
-            "batched": batched, "serving": serving, "host_sweep": host_sweep, "graph_lifecycle": lifecycle,
+            "batched": batched, "serving": serving, "serving_replay": serving_replay, "host_sweep": host_sweep,
+            "graph_lifecycle": lifecycle,
             "windows": windows, "jacobi": jacobi, "config1_64MiB": config1, "pageable_host": pageable,
             "sweep": sweep, "wall_s": round(time.perf_counter() - t_wall0, 2),
         }
@@ -1049,6 +1054,110 @@ def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30, streams=0, batc
                     "batches": stats["batches"], "max_inflight_bytes": stats["max_inflight_bytes"],
                     "submit_late_p99_us": round(_percentile(late, 99), 1), "verified": verified, "errors": bad,
                     "drain_s": round((mpt.mpt_now_ns() - t_end_sched) / 1e9, 3)})
+    return out
+
+
+def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30):
+    """The serving workload with a native load generator (mpt_serve_replay keeps the Poisson
+    schedule to about a microsecond), so latency from the scheduled arrival is the server's.
+    Destinations come from sequential rings (12 GiB device, 4 GiB host), each lap tens of
+    milliseconds long; after the run every request is checked against the previous lap: a
+    request overlapping an earlier one's destination must have been submitted after that one
+    completed.  1% of requests and every request above 64 MiB verified by digest on
+    completion."""
+    import bisect
+    import threading
+
+    import payload
+    src_dev = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
+    src_host = torch.empty(1 << 30, dtype=torch.uint8).pin_memory()
+    base_t = torch.from_numpy(payload.fill("u32", payload.SEED_SERVE, 64 * MiB))
+    for t in (src_dev, src_host):
+        for o in range(0, t.numel(), 64 * MiB):
+            t[o:o + 64 * MiB].copy_(base_t.to(t.device))
+    ring = {"dev": torch.empty(12 << 30, dtype=torch.uint8, device="cuda"),
+            "host": torch.empty(4 << 30, dtype=torch.uint8).pin_memory()}
+    for t in (src_dev, src_host, ring["dev"], ring["host"]):
+        mpt.mpt_batch_register(ctx, t.data_ptr(), t.numel())
+    vstream = torch.cuda.Stream()
+    out = []
+    for rate in rates:
+        sched = payload.serving_schedule(rate, seconds)
+        n = len(sched)
+        heads, laps = {"dev": 0, "host": 0}, {"dev": 0, "host": 0}
+        place = []      # (kind, lap, start, end)
+        rows = []
+        for k, (t_arr, nb, d) in enumerate(sched):
+            kind = "host" if d == mpt.MPT_D2H else "dev"
+            step = (nb + 255) // 256 * 256
+            if heads[kind] + step > ring[kind].numel():
+                heads[kind] = 0
+                laps[kind] += 1
+            start = heads[kind]
+            heads[kind] += step
+            s_t = src_host if d == mpt.MPT_H2D else src_dev
+            soff = (payload.splitmix64_scalar(payload.SEED_SERVE, 1 << 40 | k) % (s_t.numel() - nb)) & ~255
+            rows.append((s_t.data_ptr() + soff, ring[kind].data_ptr() + start, nb, d))
+            place.append((kind, laps[kind], start, start + nb))
+        xf = mpt.make_xfers(rows)
+        tags = (ctypes.c_uint64 * n)(*range(n))
+        t0 = mpt.mpt_now_ns() + 50_000_000
+        due = (ctypes.c_uint64 * n)(*[t0 + int(t * 1e9) for t, _, _ in sched])
+        late = (ctypes.c_uint64 * n)()
+        server = mpt.mpt_serve_start(ctx, staging_budget_bytes=budget)
+        err = []
+
+        def feed():
+            try:
+                mpt.mpt_serve_replay(server, xf, tags, due, late)
+            except Exception as e:  # reported after the run
+                err.append(e)
+        th = threading.Thread(target=feed)
+        th.start()
+        comp = [0] * n
+        verified, bad, moved, got = 0, 0, 0, 0
+        deadline = time.perf_counter() + seconds + 60
+        while got < n and time.perf_counter() < deadline and not err:
+            for tag, arr, adm, cns, nb, st in mpt.mpt_serve_poll(server):
+                got += 1
+                comp[tag] = cns
+                if st != mpt.MPT_OK:
+                    bad += 1
+                    continue
+                moved += nb
+                if tag % 100 == 0 or nb > 64 * MiB:
+                    sp, dp, _, _ = rows[tag]
+                    h = mpt.mpt_hash_ranges_noalloc([(dp, nb), (sp, nb)], vstream)
+                    verified += 1
+                    bad += h[0] != h[1]
+        th.join()
+        stats = mpt.mpt_serve_stats(server)
+        mpt.mpt_serve_stop(server)
+        # no two requests in flight shared destination bytes: check each against the previous lap
+        submit = [due[k] + late[k] for k in range(n)]
+        by_lap = {}
+        for k, (kind, lap, a, b) in enumerate(place):
+            by_lap.setdefault((kind, lap), []).append((a, b, k))
+        overlap_ok = True
+        for k, (kind, lap, a, b) in enumerate(place):
+            prev = by_lap.get((kind, lap - 1), [])
+            i = bisect.bisect_left(prev, (a, -1, -1))
+            for j in range(max(0, i - 1), len(prev)):
+                pa, pb, pk = prev[j]
+                if pa >= b:
+                    break
+                if pb > a and comp[pk] > submit[k]:
+                    overlap_ok = False
+        lat = [(comp[k] - due[k]) / 1e3 for k in range(n) if comp[k]]
+        slat = [(comp[k] - submit[k]) / 1e3 for k in range(n) if comp[k]]
+        out.append({"rate_per_s": rate, "seconds": seconds, "requests": n, "completed": got,
+                    "client": "native replay (mpt_serve_replay)",
+                    "p50_us": round(_percentile(lat, 50), 1), "p99_us": round(_percentile(lat, 99), 1),
+                    "server_p50_us": round(_percentile(slat, 50), 1), "server_p99_us": round(_percentile(slat, 99), 1),
+                    "submit_late_p99_us": round(_percentile([x / 1e3 for x in late], 99), 2),
+                    "gbs": round(moved / seconds / 1e9, 2), "offered_gbs": round(sum(x[1] for x in sched) / seconds / 1e9, 2),
+                    "batches": stats["batches"], "verified": verified, "errors": bad + len(err),
+                    "destinations_disjoint_in_flight": overlap_ok})
     return out
 
 

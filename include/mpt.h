@@ -529,6 +529,16 @@ MPT_API mpt_status mpt_serve_poll(mpt_server_t server, mpt_completion* out, size
 
 MPT_API mpt_status mpt_serve_stats(mpt_server_t server, mpt_serve_stats_t* out);
 
+/* Replay a request trace: submit xfers[i] (tag tags[i]) at its scheduled time due_ns[i]
+ * (mpt_now_ns clock, non-decreasing), spinning between arrivals, from the calling thread --
+ * a load generator that keeps the schedule to about a microsecond where a slower client
+ * would add its own lateness to every latency.  Returns once every request is submitted;
+ * completions arrive through mpt_serve_poll as usual (poll from another thread meanwhile).
+ * late_ns (nullable, n entries) receives each submission's delay past its scheduled time.
+ * Errors: EINVAL (NULL arrays, decreasing times), those of mpt_serve_submit. */
+MPT_API mpt_status mpt_serve_replay(mpt_server_t server, const mpt_xfer* xfers, const uint64_t* tags,
+                                    const uint64_t* due_ns, size_t n, uint64_t* late_ns);
+
 /* Finish every request already submitted, stop the worker and free the server.
  * Completions not yet polled are dropped. */
 MPT_API mpt_status mpt_serve_stop(mpt_server_t server);

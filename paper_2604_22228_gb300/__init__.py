@@ -331,6 +331,17 @@ def mpt_serve_submit(server: int, src, dst, nbytes: int, direction: int, tag: in
 _COMPLETION_BUF = None
 
 
+def mpt_serve_replay(server: int, xfers, tags, due_ns, late_out=None) -> None:
+    """Submit xfers[i] at due_ns[i] from a native loop (see the C API).  xfers: a ctypes
+    mpt_xfer array (make_xfers) or (src, dst, nbytes, dir) tuples; tags, due_ns: sequences
+    of ints or ctypes uint64 arrays; late_out: optional ctypes uint64 array for the delays."""
+    n = len(xfers)
+    arr = xfers if isinstance(xfers, C.Array) else make_xfers(xfers)
+    t = tags if isinstance(tags, C.Array) else (C.c_uint64 * max(1, n))(*tags)
+    d = due_ns if isinstance(due_ns, C.Array) else (C.c_uint64 * max(1, n))(*due_ns)
+    _check(lib().mpt_serve_replay(server, arr, t, d, n, late_out), "mpt_serve_replay")
+
+
 def mpt_serve_poll(server: int, cap: int = 4096) -> list[tuple]:
     """Finished requests as (tag, arrival_ns, admit_ns, complete_ns, bytes, status)."""
     global _COMPLETION_BUF

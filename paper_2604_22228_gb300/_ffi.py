@@ -143,6 +143,7 @@ SIGNATURES = {
     "mpt_now_ns": (C.c_uint64, []),
     "mpt_serve_start": (C.c_int, [H, P(mpt_serve_config), P(H)]),
     "mpt_serve_submit": (C.c_int, [H, P(mpt_xfer), C.c_uint64, C.c_uint64]),
+    "mpt_serve_replay": (C.c_int, [H, P(mpt_xfer), P(C.c_uint64), P(C.c_uint64), C.c_size_t, P(C.c_uint64)]),
     "mpt_serve_poll": (C.c_int, [H, P(mpt_completion), C.c_size_t, P(C.c_size_t)]),
     "mpt_serve_stats": (C.c_int, [H, P(mpt_serve_stats_t)]),
     "mpt_serve_stop": (C.c_int, [H]),

@@ -259,6 +259,25 @@ mpt_status mpt_serve_submit(mpt_server_t s, const mpt_xfer* x, uint64_t tag, uin
   return MPT_OK;
 }
 
+mpt_status mpt_serve_replay(mpt_server_t s, const mpt_xfer* xfers, const uint64_t* tags, const uint64_t* due_ns,
+                            size_t n, uint64_t* late_ns) {
+  if (!s || (n > 0 && (!xfers || !tags || !due_ns))) return fail(MPT_EINVAL, "mpt_serve_replay: NULL argument");
+  for (size_t i = 1; i < n; ++i)
+    if (due_ns[i] < due_ns[i - 1]) return fail(MPT_EINVAL, "mpt_serve_replay: times decrease at %zu", i);
+  for (size_t i = 0; i < n; ++i) {
+    uint64_t now = steady_ns();
+    while (now < due_ns[i]) {
+      // spin through the last 50 us, sleep-yield before that
+      if (due_ns[i] - now > 50000) std::this_thread::yield();
+      now = steady_ns();
+    }
+    mpt_status st = mpt_serve_submit(s, &xfers[i], tags[i], due_ns[i]);
+    if (late_ns) late_ns[i] = steady_ns() - due_ns[i];
+    if (st != MPT_OK) return st;
+  }
+  return MPT_OK;
+}
+
 mpt_status mpt_serve_poll(mpt_server_t s, mpt_completion* out, size_t cap, size_t* n) {
   if (!s || !n || (cap && !out)) return fail(MPT_EINVAL, "mpt_serve_poll: NULL argument");
   std::lock_guard<std::mutex> g(s->mu);

@@ -156,3 +156,34 @@ def test_refused_request_reported_and_server_continues(ctx):
     mpt.mpt_serve_stop(server)
     assert got[1][5] == mpt.MPT_EINVAL and got[2][5] == mpt.MPT_OK
     assert int(d[:4096].sum()) == 4096
+
+
+def test_replay_keeps_the_schedule_and_results(ctx):
+    """mpt_serve_replay submits a trace at its scheduled times from a native loop; every
+    request completes, after its scheduled arrival, with the same bytes as alone (digests),
+    and a trace with decreasing times is refused."""
+    import threading
+    ar = Arenas(300, payload.SEED_SERVE + 9)
+    server = mpt.mpt_serve_start(ctx)
+    n = len(ar.reqs)
+    xf = [(ar.ptr(s_ar, s_off), ar.ptr(d_ar, d_off), nb, d) for _, s_ar, s_off, d_ar, d_off, nb, d in ar.reqs]
+    t0 = mpt.mpt_now_ns() + 5_000_000
+    due = [t0 + 50_000 * k for k in range(n)]  # 20k requests/s
+    import ctypes
+    late = (ctypes.c_uint64 * n)()
+    th = threading.Thread(target=mpt.mpt_serve_replay, args=(server, xf, list(range(n)), due, late))
+    th.start()
+    done = {}
+    t_end = time.time() + 60
+    while len(done) < n and time.time() < t_end:
+        for c in mpt.mpt_serve_poll(server):
+            done[c[0]] = c
+    th.join()
+    with pytest.raises(mpt.MptError) as e:
+        mpt.mpt_serve_replay(server, xf[:2], [0, 1], [due[1], due[0]])
+    assert e.value.status == mpt.MPT_EINVAL
+    mpt.mpt_serve_stop(server)
+    assert len(done) == n and all(c[5] == mpt.MPT_OK for c in done.values())
+    assert all(done[k][1] == due[k] and done[k][3] >= due[k] for k in range(n))  # arrival = schedule
+    assert sorted(late)[n // 2] < 1_000_000  # the native loop keeps the schedule (median < 1 ms)
+    assert ar.digests("dst") == ar.digests("src")
