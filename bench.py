@@ -1487,6 +1487,45 @@ def run_kernel_only_jacobi(args, mpt, torch):
     return 0
 
 
+def run_kernel_only_stage_h2d(args, mpt, torch):
+    """One host-to-device message through the staged path alone (8 MiB chunks): copy-engine
+    hops into a device stage, each followed by a memset node that raises the chunk's ready
+    flag, and the consumer kernel moving chunks from the stage as their flags rise, all in
+    one graph.  K replays timed with CUDA events; the consumer's flag waits are bounded, and
+    the context status is checked after the run."""
+    import numpy as np
+
+    import payload
+    n = args.kernel_bytes
+    a = torch.from_numpy(payload.fill("u32", payload.SEED_HOST_SWEEP, n)).pin_memory()
+    b = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ctx = mpt.mpt_ctx_create(0)
+    plan = mpt.mpt_plan(ctx, n, mpt.MPT_H2D, [(mpt.MPT_PATH_HS, 65536, 8 * MiB)])
+    g = mpt.mpt_capture(ctx, plan, b.data_ptr(), a.data_ptr())
+    info = mpt.mpt_graph_get_info(g)
+    s = torch.cuda.Stream()
+    for _ in range(args.warmup):
+        mpt.mpt_launch(g, s)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        mpt.mpt_launch(g, s)
+    e1.record(s)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    ok = bool(np.array_equal(b.cpu().numpy(), a.numpy()))
+    st, _ = mpt.mpt_ctx_status(ctx)
+    mpt.mpt_graph_release(g)
+    mpt.mpt_plan_destroy(plan)
+    mpt.mpt_ctx_destroy(ctx)
+    print(json.dumps({"kernel": "stage_h2d", "bytes": n, "chunk_bytes": 8 * MiB, "launches": args.steps,
+                      "ms_per_launch": round(ms, 5), "link_gbs": round(n / (ms / 1e3) / 1e9, 1),
+                      "memcpy_nodes": info.get("memcpy_nodes"), "memset_nodes": info.get("memset_nodes"),
+                      "kernel_nodes": info.get("kernel_nodes"), "staging_bytes": info.get("staging_bytes"),
+                      "ok": ok and st == 0}), flush=True)
+    return 0 if ok and st == 0 else 1
+
+
 def run_kernel_only(args):
     """One kernel alone on one message (for profiling): K launches timed with CUDA events."""
     import torch
@@ -1497,6 +1536,8 @@ def run_kernel_only(args):
     n = args.kernel_bytes
     if args.kernel_only == "jacobi":
         return run_kernel_only_jacobi(args, mpt, torch)
+    if args.kernel_only == "stage_h2d":
+        return run_kernel_only_stage_h2d(args, mpt, torch)
     ctx = mpt.mpt_ctx_create(0)
     host = args.kernel_only in ("zc", "zc_d2h")
     if args.kernel_only == "zc":  # host -> device
@@ -1557,7 +1598,7 @@ def main(argv=None):
     ap.add_argument("--tune", choices=["online", "model"], default="online",
                     help="online: measure every size bucket with mpt_tune before capturing; model: cost model only")
     ap.add_argument("--tune-out", default=None, help="write the tuned table (JSON lines) here")
-    ap.add_argument("--kernel-only", choices=["vec", "vec8k", "bulk", "zc", "zc_d2h", "jacobi"], default=None,
+    ap.add_argument("--kernel-only", choices=["vec", "vec8k", "bulk", "zc", "zc_d2h", "jacobi", "stage_h2d"], default=None,
                     help="time one copy kernel alone on --kernel-bytes (profiling)")
     ap.add_argument("--kernel-bytes", type=int, default=256 * MiB)
     ap.add_argument("--kernel-ctas", type=int, default=0)

@@ -16,6 +16,21 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// Global timer in nanoseconds: the clock every bounded device-side wait measures against.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// A wait ran out: record (site << 8) | MPT_ETIMEDOUT in the context's status word, unless
+// an earlier failure is already recorded there.
+__device__ __forceinline__ void record_timeout(uint32_t* status, uint32_t site) {
+  constexpr uint32_t kTimedOut = 4;  // MPT_ETIMEDOUT
+  if (status) atomicCAS(status, 0u, (site << 8) | kTimedOut);
+}
+
+// Read-only path (ld.global.nc): only for data no agent writes while the kernel runs.
 __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
   uint4 v;
   asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0,%1,%2,%3}, [%4];"
@@ -66,7 +81,7 @@ __device__ __forceinline__ uint4 shift16(const uint4& w0, const uint4& w1, uint3
 // (straight when s is then aligned too, else -- only if kAny -- assembled from two aligned
 // source words), and the remaining tail bytes.  Reads never leave the 16-byte blocks that
 // hold source bytes.  Without kAny the caller guarantees s and o agree modulo 16.
-template <bool kHostLink, bool kAny>
+template <bool kCoherent, bool kAny>
 __device__ __forceinline__ void cta_copy(const uint8_t* s, uint8_t* o, uint64_t n) {
   const uint32_t tid = threadIdx.x, bd = blockDim.x;
   const uint64_t head = ((16u - (uint32_t)(reinterpret_cast<uintptr_t>(o) & 15)) & 15u) < n
@@ -84,7 +99,7 @@ __device__ __forceinline__ void cta_copy(const uint8_t* s, uint8_t* o, uint64_t 
     const uint4* sv = reinterpret_cast<const uint4*>(s1);
     for (; v + 3ull * bd < nv; v += 4ull * bd) {
       uint4 r0, r1, r2, r3;
-      if (kHostLink) {
+      if (kCoherent) {
         r0 = ld_plain(sv + v); r1 = ld_plain(sv + v + bd); r2 = ld_plain(sv + v + 2 * bd); r3 = ld_plain(sv + v + 3 * bd);
       } else {
         r0 = ld_stream(sv + v); r1 = ld_stream(sv + v + bd); r2 = ld_stream(sv + v + 2 * bd); r3 = ld_stream(sv + v + 3 * bd);
@@ -94,14 +109,14 @@ __device__ __forceinline__ void cta_copy(const uint8_t* s, uint8_t* o, uint64_t 
       st_plain(ov + v + 2 * bd, r2);
       st_plain(ov + v + 3 * bd, r3);
     }
-    for (; v < nv; v += bd) st_plain(ov + v, kHostLink ? ld_plain(sv + v) : ld_stream(sv + v));
+    for (; v < nv; v += bd) st_plain(ov + v, kCoherent ? ld_plain(sv + v) : ld_stream(sv + v));
   } else {
     const uint4* sw = reinterpret_cast<const uint4*>(s1 - m);
     const uint32_t k = m >> 2, r = (m & 3u) * 8u;
 #pragma unroll 2
     for (; v < nv; v += bd) {
-      const uint4 a0 = kHostLink ? ld_plain(sw + v) : ld_stream(sw + v);
-      const uint4 a1 = kHostLink ? ld_plain(sw + v + 1) : ld_stream(sw + v + 1);
+      const uint4 a0 = kCoherent ? ld_plain(sw + v) : ld_stream(sw + v);
+      const uint4 a1 = kCoherent ? ld_plain(sw + v + 1) : ld_stream(sw + v + 1);
       st_plain(ov + v, shift16(a0, a1, k, r));
     }
   }

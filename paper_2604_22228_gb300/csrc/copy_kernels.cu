@@ -11,10 +11,6 @@
 //                  thread per CTA and tracked by mbarriers.
 //  k_zc_copy       zero-copy kernel: the vec128 loop with plain (coherent) loads, used on
 //                  mapped page-locked host memory for host<->device transfers.
-//  k_stage_consume second hop of the host-to-device staged path: waits on per-chunk
-//                  ready flags set after each copy-engine hop one, then moves the chunk
-//                  from the device stage to its destination (Algorithm 2 StageHostCopy's
-//                  "hop two after hop one" edge, carried by device flags).
 //  k_hash          digest of a byte range (test utility).
 //
 // Every device-side wait is bounded by the global timer and records MPT_ETIMEDOUT in
@@ -27,18 +23,6 @@
 namespace mpt {
 
 namespace {
-
-constexpr uint32_t kTimedOut = 4;  // MPT_ETIMEDOUT
-
-__device__ __forceinline__ uint64_t global_ns() {
-  uint64_t t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-__device__ __forceinline__ void record_timeout(uint32_t* status, uint32_t site) {
-  if (status) atomicCAS(status, 0u, (site << 8) | kTimedOut);
-}
 
 __device__ __forceinline__ int find_range(const CopyArgs& a, uint32_t t) {
   int r = 0;
@@ -59,7 +43,7 @@ __device__ __forceinline__ void copy_edges(const uint8_t* s, uint8_t* o, const R
 
 // kU 16-byte vectors per thread per tile: tiles of kVecThreads * kU * 16 bytes (64 KiB for
 // kU = 8, 8 KiB for kU = 1).
-template <bool kHostLink, bool kAny, int kU>
+template <bool kCoherent, bool kAny, int kU>
 __device__ __forceinline__ void copy_tiles_vec(const CopyArgs& a) {
   constexpr uint64_t kTileVecs = (uint64_t)kVecThreads * kU;
   constexpr int kHalf = kU >= 2 ? kU / 2 : 1;  // shifted path: vector pairs per round
@@ -80,7 +64,7 @@ __device__ __forceinline__ void copy_tiles_vec(const CopyArgs& a) {
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
         const uint64_t i = v0 + (uint64_t)u * kVecThreads;
-        if (i < nvec) buf[u] = kHostLink ? ld_plain(sv + i) : ld_stream(sv + i);
+        if (i < nvec) buf[u] = kCoherent ? ld_plain(sv + i) : ld_stream(sv + i);
       }
 #pragma unroll
       for (int u = 0; u < kU; ++u) {
@@ -98,8 +82,8 @@ __device__ __forceinline__ void copy_tiles_vec(const CopyArgs& a) {
         for (int u = 0; u < kHalf; ++u) {
           const uint64_t i = v0 + (uint64_t)(half + u) * kVecThreads;
           if (i < nvec) {
-            w0[u] = kHostLink ? ld_plain(sw + i) : ld_stream(sw + i);
-            w1[u] = kHostLink ? ld_plain(sw + i + 1) : ld_stream(sw + i + 1);
+            w0[u] = kCoherent ? ld_plain(sw + i) : ld_stream(sw + i);
+            w1[u] = kCoherent ? ld_plain(sw + i + 1) : ld_stream(sw + i + 1);
           }
         }
 #pragma unroll
@@ -285,50 +269,6 @@ __global__ void __launch_bounds__(kBulkThreads, 1) k_sm_copy_bulk(CopyArgs a) {
     const uint64_t drain = global_ns() + kDefaultTimeoutNs;
     const uint32_t hi = (i + kBulkStages < n_my) ? i + kBulkStages : n_my;
     for (uint32_t j = i; j < hi; ++j) mbar_wait(smem_addr(&bar[j % kBulkStages]), (j / kBulkStages) & 1u, drain);
-  }
-}
-
-__global__ void __launch_bounds__(kVecThreads) k_stage_consume(StageArgs a) {
-  __shared__ int ok;
-  constexpr uint64_t kTile = kVecTileVecs * 16;
-  const uint32_t total = a.nchunks * a.tiles_per_chunk;
-  const uint32_t tid = threadIdx.x;
-  for (uint32_t t = blockIdx.x; t < total; t += gridDim.x) {
-    const uint32_t k = t / a.tiles_per_chunk;
-    const uint32_t lt = t - k * a.tiles_per_chunk;
-    if (tid == 0) {
-      const uint64_t deadline = global_ns() + a.timeout_ns;
-      int seen = 0;
-      while (true) {
-        uint32_t v;
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(a.ready + k) : "memory");
-        if (v != 0) {
-          seen = 1;
-          break;
-        }
-        if (global_ns() > deadline) break;
-        __nanosleep(128);
-      }
-      ok = seen;
-      if (!seen) record_timeout(a.status, kSiteStageFlag);
-    }
-    __syncthreads();
-    if (!ok) return;
-    const StageChunk c = a.chunks[k];
-    const uint64_t off = (uint64_t)lt * kTile;
-    if (off < c.bytes) {
-      const uint64_t n = c.bytes - off < kTile ? c.bytes - off : kTile;
-      cta_copy<false, true>(a.stage + c.stage_off + off, a.dst + c.dst_off + off, n);
-    }
-    __syncthreads();
-    if (tid == 0) {
-      __threadfence();
-      const uint32_t prev = atomicAdd(a.done + k, 1u);
-      if (prev == a.tiles_per_chunk - 1) {
-        a.done[k] = 0;
-        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(a.ready + k), "r"(0u) : "memory");
-      }
-    }
   }
 }
 
