@@ -30,6 +30,31 @@ __device__ __forceinline__ int find_range(const CopyArgs& a, uint32_t t) {
   return r;
 }
 
+// Before waiting on the kernel ahead (programmatic dependent launch), one thread asks L2 for
+// the source bytes of the CTA's first tile.  This is only a hint to L2, the GPU's point of
+// coherence: if the kernel ahead writes those bytes before the wait returns, its stores
+// update the lines in L2, and the loads after the wait, which miss L1, read the new bytes.
+// No data reaches registers before the wait.  The short messages of a stream of copies then
+// find their source in L2 instead of HBM once the kernel ahead completes.
+template <int kU>
+__device__ __forceinline__ void prefetch_first_tile(const CopyArgs& a) {
+  if (threadIdx.x != 0 || blockIdx.x >= a.ntiles) return;
+  constexpr uint64_t kTileBytes = (uint64_t)kVecThreads * kU * 16;
+  const int r = find_range(a, blockIdx.x);
+  const RangeDesc& d = a.r[r];
+  const uint64_t lt = blockIdx.x - a.tile_start[r];
+  // bytes of the range this tile reads: from the range start (tile 0 also copies the head)
+  // or one word before the tile (the shifted path reads a word pair), to one word past it
+  const uint64_t lo = lt == 0 ? 0 : d.head + lt * kTileBytes - 16;
+  const uint64_t end = d.head + (lt + 1) * kTileBytes + 16;
+  const uint64_t hi = end < d.bytes ? end : d.bytes;
+  if (hi <= lo) return;
+  // whole 16-byte blocks around [lo, hi): each holds a source byte, so it is mapped memory
+  const uintptr_t base = reinterpret_cast<uintptr_t>(a.src + d.src_off);
+  const uintptr_t p0 = (base + lo) & ~(uintptr_t)15, p1 = (base + hi + 15) & ~(uintptr_t)15;
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p0), "r"((uint32_t)(p1 - p0)) : "memory");
+}
+
 // Head (bytes before the destination-aligned body) and tail (bytes after it) of a range;
 // threads 0..15 copy the head, threads 32..47 the tail.
 __device__ __forceinline__ void copy_edges(const uint8_t* s, uint8_t* o, const RangeDesc& d,
@@ -175,18 +200,22 @@ __device__ __forceinline__ uint32_t bulk_piece(const CopyArgs& a, uint32_t t, co
 }  // namespace
 
 __global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec(CopyArgs a) {
+  prefetch_first_tile<kVecUnroll>(a);
   pdl_enter();
   copy_tiles_vec<false, false, kVecUnroll>(a);
 }
 __global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec_any(CopyArgs a) {
+  prefetch_first_tile<kVecUnroll>(a);
   pdl_enter();
   copy_tiles_vec<false, true, kVecUnroll>(a);
 }
 __global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec8k(CopyArgs a) {
+  prefetch_first_tile<1>(a);
   pdl_enter();
   copy_tiles_vec<false, false, 1>(a);
 }
 __global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec8k_any(CopyArgs a) {
+  prefetch_first_tile<1>(a);
   pdl_enter();
   copy_tiles_vec<false, true, 1>(a);
 }
