@@ -603,13 +603,31 @@ def run_ours(args):
     serving = serving_replay = None
     if args.serve_seconds > 0:
         rates = [float(r) for r in args.serve_rates.split(",")]
-        # the default: batches in flight on streams of their own, the batch kernel on one CTA
-        # per SM; then every batch in order on one stream with three CTAs per SM
-        serving = run_serving(mpt, torch, ctx, rates, args.serve_seconds)
-        serving += run_serving(mpt, torch, ctx, rates, args.serve_seconds, streams=1,
-                               batch_ctas=3 * ctx_sms(mpt, ctx))
-        mpt.mpt_batch_configure(ctx, 0, 0, 0, 0)
-        serving_replay = run_serving_replay(mpt, torch, ctx, rates, args.serve_seconds)
+        # Python's cyclic collector would walk the millions of trace and latency objects of a
+        # long run and stall the client for up to a second at a time: switch it off here
+        import gc
+        gc.collect()
+        gc.freeze()
+        gc.disable()
+        try:
+            # the default: batches in flight on streams of their own, the batch kernel on one
+            # CTA per SM; then every batch in order on one stream with three CTAs per SM
+            modes = args.serve_modes.split(",")
+            serving, serving_replay = [], []
+            if "python" in modes:
+                serving += run_serving(mpt, torch, ctx, rates, args.serve_seconds)
+            if "inorder" in modes:
+                serving += run_serving(mpt, torch, ctx, rates, args.serve_seconds, streams=1,
+                                       batch_ctas=3 * ctx_sms(mpt, ctx))
+            mpt.mpt_batch_configure(ctx, 0, 0, 0, 0)
+            if "replay" in modes:
+                serving_replay = run_serving_replay(mpt, torch, ctx, rates, args.serve_seconds,
+                                                    trace_dir=args.serve_trace_dir,
+                                                    max_inflight=args.serve_max_inflight,
+                                                    verify=not args.serve_no_verify)
+        finally:
+            gc.enable()
+            gc.unfreeze()
         ok = ok and all(r["errors"] == 0 for r in serving + serving_replay)
         ok = ok and all(r["destinations_disjoint_in_flight"] and r["completed"] == r["requests"] for r in serving_replay)
 
@@ -949,6 +967,24 @@ def run_batched(mpt, torch, ctx, stream, reps=5):
         "parity_ok": bool(ok)}
 
 
+def _serve_warmup(mpt, ctx, rows, **server_args):
+    """Untimed warm-up before a serving run's clock starts, on a server of its own (so the
+    timed server's counters start clean): submit `rows` (src, dst, bytes, dir) at once and
+    drain their completions.  Building a long trace leaves the GPU idle for seconds, and the
+    first batches after that ran far below the link rate."""
+    server = mpt.mpt_serve_start(ctx, **server_args)
+    try:
+        for k, (sp, dp, nb, d) in enumerate(rows):
+            mpt.mpt_serve_submit(server, sp, dp, nb, d, k)
+        got, t_end = 0, time.perf_counter() + 30
+        while got < len(rows) and time.perf_counter() < t_end:
+            got += len(mpt.mpt_serve_poll(server))
+    finally:
+        mpt.mpt_serve_stop(server)
+    if got < len(rows):
+        raise RuntimeError("serving warm-up did not complete")
+
+
 def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30, streams=0, batch_ctas=0):
     """Open-loop Poisson arrivals (lognormal sizes, median 1 MiB, sigma 1.5, cap 256 MiB,
     50/25/25 directions) through the continuous-batching server; latency from the scheduled
@@ -977,7 +1013,15 @@ def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30, streams=0, batc
         outstanding = {"dev": collections.deque(), "host": collections.deque()}
         finished = set()
         lat, slat, late, verified, bad = [], [], [], 0, 0
+        bad_status = {}
         moved = 0
+        warm, wh = [], {"dev": 0, "host": 0}
+        for k, (_, nb, d) in enumerate(sched[:2048]):
+            kind = "host" if d == mpt.MPT_D2H else "dev"
+            s_t = src_host if d == mpt.MPT_H2D else src_dev
+            warm.append((s_t.data_ptr(), ring[kind].data_ptr() + wh[kind], nb, d))
+            wh[kind] += (nb + 255) // 256 * 256
+        _serve_warmup(mpt, ctx, warm, staging_budget_bytes=budget, streams=streams, batch_ctas=batch_ctas)
         server = mpt.mpt_serve_start(ctx, staging_budget_bytes=budget, streams=streams, batch_ctas=batch_ctas)
         meta = {}
 
@@ -987,7 +1031,7 @@ def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30, streams=0, batc
                 kind, off, sp, dp, t_sub = meta.pop(tag)
                 finished.add(tag)
                 if st != mpt.MPT_OK:
-                    bad += 1
+                    bad_status[st] = bad_status.get(st, 0) + 1
                     continue
                 lat.append((comp - arr) / 1e3)
                 slat.append((comp - t_sub) / 1e3)
@@ -1052,12 +1096,20 @@ def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30, streams=0, batc
                     "server_p50_us": round(_percentile(slat, 50), 1), "server_p99_us": round(_percentile(slat, 99), 1),
                     "gbs": round(moved / max(wall, 1e-9) / 1e9, 2), "offered_gbs": round(sum(x[1] for x in sched) / seconds / 1e9, 2),
                     "batches": stats["batches"], "max_inflight_bytes": stats["max_inflight_bytes"],
-                    "submit_late_p99_us": round(_percentile(late, 99), 1), "verified": verified, "errors": bad,
+                    "max_pending_completions": stats["max_pending_completions"],
+                    "max_worker_turn_us": round(stats["max_turn_ns"] / 1e3, 1), "max_waiting": stats["max_waiting"],
+                    "max_phase_us": {k: round(stats[f"max_{k}_ns"] / 1e3, 1) for k in ("harvest", "admit", "launch")},
+                    "longest_batch": {"us": round(stats["max_batch_ns"] / 1e3, 1), "requests": stats["max_batch_reqs"],
+                                      "bytes": stats["max_batch_bytes"]},
+                    "submit_late_p99_us": round(_percentile(late, 99), 1), "verified": verified,
+                    "digest_errors": bad, "status_errors": {str(k): v for k, v in bad_status.items()},
+                    "errors": bad + sum(bad_status.values()),
                     "drain_s": round((mpt.mpt_now_ns() - t_end_sched) / 1e9, 3)})
     return out
 
 
-def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30):
+def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30, trace_dir=None, max_inflight=0,
+                       verify=True):
     """The serving workload with a native load generator (mpt_serve_replay keeps the Poisson
     schedule to about a microsecond), so latency from the scheduled arrival is the server's.
     Destinations come from sequential rings (12 GiB device, 4 GiB host), each lap tens of
@@ -1067,6 +1119,8 @@ def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30):
     completion."""
     import bisect
     import threading
+
+    import numpy as np
 
     import payload
     src_dev = torch.empty(1 << 30, dtype=torch.uint8, device="cuda")
@@ -1101,10 +1155,31 @@ def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30):
             place.append((kind, laps[kind], start, start + nb))
         xf = mpt.make_xfers(rows)
         tags = (ctypes.c_uint64 * n)(*range(n))
-        t0 = mpt.mpt_now_ns() + 50_000_000
-        due = (ctypes.c_uint64 * n)(*[t0 + int(t * 1e9) for t, _, _ in sched])
+        due_rel = np.array([int(t * 1e9) for t, _, _ in sched], dtype=np.uint64)
+        # the ring reuses a destination when the next lap reaches it: next_idx[k] is the first
+        # request of the next lap overlapping k's destination; a digest of k taken after that
+        # request is due may see its bytes and proves nothing
+        lap_rows = {}
+        for k, (kind, lap, a, b) in enumerate(place):
+            lap_rows.setdefault((kind, lap), []).append((b, a, k))   # ends increase with k
+        next_idx = [-1] * n
+        for k, (kind, lap, a, b) in enumerate(place):
+            nxt = lap_rows.get((kind, lap + 1))
+            if nxt:
+                i = bisect.bisect_right(nxt, (a, 1 << 64, 1 << 64))  # first whose end > a
+                if i < len(nxt) and nxt[i][1] < b:
+                    next_idx[k] = nxt[i][2]
         late = (ctypes.c_uint64 * n)()
-        server = mpt.mpt_serve_start(ctx, staging_budget_bytes=budget)
+        due = (ctypes.c_uint64 * n)()
+        # the first rows stay short of either ring's end
+        _serve_warmup(mpt, ctx, rows[:2048], staging_budget_bytes=budget, max_inflight_batches=max_inflight)
+        if trace_dir:  # the server writes one line per batch at stop
+            os.environ["MPT_SERVE_BATCH_LOG"] = os.path.join(trace_dir, f"replay_batches_{int(rate)}.csv")
+        server = mpt.mpt_serve_start(ctx, staging_budget_bytes=budget, max_inflight_batches=max_inflight)
+        os.environ.pop("MPT_SERVE_BATCH_LOG", None)
+        # the schedule starts 50 ms from now: every step above (seconds for a long trace) is done
+        t0 = mpt.mpt_now_ns() + 50_000_000
+        np.frombuffer(due, dtype=np.uint64)[:] = due_rel + np.uint64(t0)
         err = []
 
         def feed():
@@ -1115,21 +1190,26 @@ def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30):
         th = threading.Thread(target=feed)
         th.start()
         comp = [0] * n
-        verified, bad, moved, got = 0, 0, 0, 0
+        verified, skipped, bad_digest, moved, got = 0, 0, 0, 0, 0
+        bad_status = {}
         deadline = time.perf_counter() + seconds + 60
         while got < n and time.perf_counter() < deadline and not err:
             for tag, arr, adm, cns, nb, st in mpt.mpt_serve_poll(server):
                 got += 1
                 comp[tag] = cns
                 if st != mpt.MPT_OK:
-                    bad += 1
+                    bad_status[st] = bad_status.get(st, 0) + 1
                     continue
                 moved += nb
-                if tag % 100 == 0 or nb > 64 * MiB:
+                if verify and (tag % 100 == 0 or nb > 64 * MiB):
                     sp, dp, _, _ = rows[tag]
                     h = mpt.mpt_hash_ranges_noalloc([(dp, nb), (sp, nb)], vstream)
+                    j = next_idx[tag]
+                    if j >= 0 and mpt.mpt_now_ns() >= due[j]:
+                        skipped += 1   # the next lap may already be writing there
+                        continue
                     verified += 1
-                    bad += h[0] != h[1]
+                    bad_digest += h[0] != h[1]
         th.join()
         stats = mpt.mpt_serve_stats(server)
         mpt.mpt_serve_stop(server)
@@ -1150,13 +1230,26 @@ def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30):
                     overlap_ok = False
         lat = [(comp[k] - due[k]) / 1e3 for k in range(n) if comp[k]]
         slat = [(comp[k] - submit[k]) / 1e3 for k in range(n) if comp[k]]
+        if trace_dir:
+            np.savez_compressed(os.path.join(trace_dir, f"replay_requests_{int(rate)}.npz"), t0=t0,
+                                due=np.frombuffer(due, dtype=np.uint64), late=np.frombuffer(late, dtype=np.uint64),
+                                comp=np.array(comp, dtype=np.uint64), size=np.array([r[2] for r in rows], dtype=np.uint64),
+                                dir=np.array([r[3] for r in rows], dtype=np.uint8))
         out.append({"rate_per_s": rate, "seconds": seconds, "requests": n, "completed": got,
                     "client": "native replay (mpt_serve_replay)",
                     "p50_us": round(_percentile(lat, 50), 1), "p99_us": round(_percentile(lat, 99), 1),
                     "server_p50_us": round(_percentile(slat, 50), 1), "server_p99_us": round(_percentile(slat, 99), 1),
                     "submit_late_p99_us": round(_percentile([x / 1e3 for x in late], 99), 2),
                     "gbs": round(moved / seconds / 1e9, 2), "offered_gbs": round(sum(x[1] for x in sched) / seconds / 1e9, 2),
-                    "batches": stats["batches"], "verified": verified, "errors": bad + len(err),
+                    "batches": stats["batches"], "max_inflight_bytes": stats["max_inflight_bytes"],
+                    "max_pending_completions": stats["max_pending_completions"],
+                    "max_worker_turn_us": round(stats["max_turn_ns"] / 1e3, 1), "max_waiting": stats["max_waiting"],
+                    "max_phase_us": {k: round(stats[f"max_{k}_ns"] / 1e3, 1) for k in ("harvest", "admit", "launch")},
+                    "longest_batch": {"us": round(stats["max_batch_ns"] / 1e3, 1), "requests": stats["max_batch_reqs"],
+                                      "bytes": stats["max_batch_bytes"]},
+                    "verified": verified, "verify_skipped_reused": skipped, "digest_errors": bad_digest,
+                    "status_errors": {str(k): v for k, v in bad_status.items()},
+                    "errors": bad_digest + sum(bad_status.values()) + len(err),
                     "destinations_disjoint_in_flight": overlap_ok})
     return out
 
@@ -1595,6 +1688,12 @@ def main(argv=None):
     ap.add_argument("--no-jacobi", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=2.0, help="per arrival rate; 0 skips serving")
     ap.add_argument("--serve-rates", default="1000,10000,50000")
+    ap.add_argument("--serve-max-inflight", type=int, default=0, help="replay: batches in flight (0 = default)")
+    ap.add_argument("--serve-no-verify", action="store_true", help="replay: skip the digest checks")
+    ap.add_argument("--serve-trace-dir", default=None,
+                    help="write per-request arrays and the server's per-batch log of each replay here")
+    ap.add_argument("--serve-modes", default="python,inorder,replay",
+                    help="serving clients to run: python (default server), inorder (one stream), replay (native)")
     ap.add_argument("--tune", choices=["online", "model"], default="online",
                     help="online: measure every size bucket with mpt_tune before capturing; model: cost model only")
     ap.add_argument("--tune-out", default=None, help="write the tuned table (JSON lines) here")

@@ -499,8 +499,17 @@ typedef struct {
   uint32_t reserved;
 } mpt_completion;
 
+/* Counters of a running server.  max_pending_completions: the most finished requests
+ * that waited at once for mpt_serve_poll; max_turn_ns: the worker's longest single turn
+ * (harvest + admit + launch), which bounds how late it can notice a finished batch or a
+ * free slot, and the longest of each of those three phases; max_waiting: the longest
+ * admission queue seen; max_batch_ns: the longest batch, from its launch to the release of
+ * its slot, with its request count and bytes. */
 typedef struct {
   uint64_t submitted, completed, batches, inflight_bytes, max_inflight_bytes, rejected;
+  uint64_t max_pending_completions, max_turn_ns, max_waiting;
+  uint64_t max_batch_ns, max_batch_reqs, max_batch_bytes;
+  uint64_t max_harvest_ns, max_admit_ns, max_launch_ns;
 } mpt_serve_stats_t;
 
 /* The clock of mpt_serve_submit / mpt_completion (steady, nanoseconds). */
@@ -521,10 +530,16 @@ MPT_API mpt_status mpt_serve_start(mpt_ctx_t ctx, const mpt_serve_config* cfg, m
 
 /* Enqueue one request (thread-safe).  arrival_ns: the request's scheduled arrival on the
  * mpt_now_ns clock (0 = now); latency is measured from it.  The same rules as
- * mpt_batch_submit apply to the transfer; in-flight destinations must not overlap. */
+ * mpt_batch_submit apply to the transfer.  A request that breaks them on its own (direction,
+ * NULL pointer, memory kinds) is refused alone when it is admitted: its completion carries
+ * the error and the requests around it are unaffected.  The caller must keep destinations
+ * of requests in flight from overlapping one another or any source in flight; a batch
+ * that breaks this is refused as a whole. */
 MPT_API mpt_status mpt_serve_submit(mpt_server_t server, const mpt_xfer* xfer, uint64_t tag, uint64_t arrival_ns);
 
-/* Move up to `cap` finished requests into `out` (thread-safe); *n gets the count. */
+/* Move up to `cap` finished requests, oldest first, into `out` (thread-safe); *n gets the
+ * count.  Costs O(*n) under the server's lock whatever the backlog, so a client that falls
+ * behind does not slow the worker or the submitters. */
 MPT_API mpt_status mpt_serve_poll(mpt_server_t server, mpt_completion* out, size_t cap, size_t* n);
 
 MPT_API mpt_status mpt_serve_stats(mpt_server_t server, mpt_serve_stats_t* out);

@@ -84,7 +84,10 @@ class mpt_completion(C.Structure):
 
 class mpt_serve_stats_t(C.Structure):
     _fields_ = [(n, C.c_uint64) for n in ("submitted", "completed", "batches", "inflight_bytes",
-                                          "max_inflight_bytes", "rejected")]
+                                          "max_inflight_bytes", "rejected", "max_pending_completions",
+                                          "max_turn_ns", "max_waiting", "max_batch_ns", "max_batch_reqs",
+                                          "max_batch_bytes", "max_harvest_ns", "max_admit_ns",
+                                          "max_launch_ns")]
 
 
 class mpt_device_info(C.Structure):

@@ -16,6 +16,7 @@
 // whose parameters never change: the descriptor count lives in the table header, so any
 // batch up to the slot capacity replays the same graph.
 #include <algorithm>
+#include <iterator>
 #include <chrono>
 #include <cmath>
 #include <cstdlib>
@@ -117,6 +118,8 @@ void slot_free(BatchSlot& s) {
     if (s.graph[i]) cudaGraphDestroy(s.graph[i]);
   }
   if (s.done_ev) cudaEventDestroy(s.done_ev);
+  if (s.t0_ev) cudaEventDestroy(s.t0_ev);
+  if (s.t1_ev) cudaEventDestroy(s.t1_ev);
   if (s.h_scratch) cudaFreeHost(s.h_scratch);
   if (s.h_table) cudaFreeHost(s.h_table);
   if (s.h_flags) cudaFreeHost(s.h_flags);
@@ -283,6 +286,20 @@ void batch_teardown(mpt_ctx_t c) {
   c->slots.clear();
 }
 
+mpt_status batch_check_xfer(mpt_ctx_t c, const mpt_xfer& x, int* src_kind, int* dst_kind) {
+  *src_kind = *dst_kind = -1;
+  if (x.dir > MPT_D2H) return fail(MPT_EINVAL, "transfer has direction %u", x.dir);
+  if (x.bytes == 0) return MPT_OK;
+  if (!x.src || !x.dst) return fail(MPT_EINVAL, "transfer has a NULL pointer");
+  const int ks = range_kind(c, x.src, x.bytes), kd = range_kind(c, x.dst, x.bytes);
+  const int want_s = x.dir == MPT_H2D ? 1 : 0, want_d = x.dir == MPT_D2H ? 1 : 0;
+  if ((ks == 2 ? 1 : ks) != want_s || (kd == 2 ? 1 : kd) != want_d)
+    return fail(MPT_EINVAL, "transfer pointers do not match direction %u", x.dir);
+  *src_kind = ks;
+  *dst_kind = kd;
+  return MPT_OK;
+}
+
 }  // namespace mpt
 
 struct mpt_batch_s {
@@ -292,6 +309,13 @@ struct mpt_batch_s {
   size_t n;
   uint64_t submit_ns;
 };
+
+float mpt::batch_gpu_ms(mpt_batch_t b) {
+  const mpt::BatchSlot& s = b->ctx->slots[b->slot];
+  float ms = -1.0f;
+  if (!s.timed || cudaEventElapsedTime(&ms, s.t0_ev, s.t1_ev) != cudaSuccess) return -1.0f;
+  return ms;
+}
 
 using namespace mpt;
 
@@ -448,13 +472,10 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
   std::vector<uint32_t> dma_cand;  // entries large enough for a copy-engine lane
   for (size_t i = 0; i < n; ++i) {
     const mpt_xfer& x = xfers[i];
-    if (x.dir > MPT_D2H) return fail(MPT_EINVAL, "mpt_batch_submit: transfer %zu has direction %u", i, x.dir);
+    int ks, kd;
+    if (batch_check_xfer(c, x, &ks, &kd) != MPT_OK)
+      return fail(MPT_EINVAL, "mpt_batch_submit: transfer %zu: %s", i, mpt_last_error());
     if (x.bytes == 0) continue;
-    if (!x.src || !x.dst) return fail(MPT_EINVAL, "mpt_batch_submit: transfer %zu has a NULL pointer", i);
-    const int ks = range_kind(c, x.src, x.bytes), kd = range_kind(c, x.dst, x.bytes);
-    const int want_s = x.dir == MPT_H2D ? 1 : 0, want_d = x.dir == MPT_D2H ? 1 : 0;
-    if ((ks == 2 ? 1 : ks) != want_s || (kd == 2 ? 1 : kd) != want_d)
-      return fail(MPT_EINVAL, "mpt_batch_submit: transfer %zu: pointers do not match direction %u", i, x.dir);
     spans.emplace_back((uint64_t)(uintptr_t)x.dst, (uint64_t)(uintptr_t)x.dst + x.bytes);
     if (s.dma_lanes && x.bytes >= c->batch_dma_min && ks != 2 && kd != 2) dma_cand.push_back((uint32_t)i);
   }
@@ -462,6 +483,17 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
   for (size_t i = 1; i < spans.size(); ++i)
     if (spans[i].first < spans[i - 1].second)
       return fail(MPT_EINVAL, "mpt_batch_submit: destination regions overlap");
+  // no source may overlap a destination: the batch's transfers run at the same time
+  for (size_t i = 0; i < n; ++i) {
+    const mpt_xfer& x = xfers[i];
+    if (x.bytes == 0) continue;
+    const uint64_t a = (uint64_t)(uintptr_t)x.src, b = a + x.bytes;
+    // spans are sorted and disjoint: only the last one starting at or before a, and the
+    // first one starting after a, can reach into [a, b)
+    auto it = std::upper_bound(spans.begin(), spans.end(), std::pair<uint64_t, uint64_t>(a, UINT64_MAX));
+    if ((it != spans.begin() && std::prev(it)->second > a) || (it != spans.end() && it->first < b))
+      return fail(MPT_EINVAL, "mpt_batch_submit: the source of transfer %zu overlaps a destination of the batch", i);
+  }
   // the slot's previous batch must be done reading its table
   CUDA_TRY(cudaEventSynchronize(s.done_ev));
   s.epoch++;
@@ -520,8 +552,16 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
     }
   }
   const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  const bool timed = c->batch_timing;
+  if (timed && !s.t0_ev) {
+    CUDA_TRY(cudaEventCreate(&s.t0_ev));
+    CUDA_TRY(cudaEventCreate(&s.t1_ev));
+  }
+  if (timed) CUDA_TRY(cudaEventRecord(s.t0_ev, cs));
   CUDA_TRY(cudaGraphLaunch(s.exec[gi], cs));
+  if (timed) CUDA_TRY(cudaEventRecord(s.t1_ev, cs));
   CUDA_TRY(cudaEventRecord(s.done_ev, cs));
+  s.timed = timed;
   s.held = true;
   s.n = n;
   mpt_batch_s* b = new mpt_batch_s{c, si, s.epoch, n, host_ns()};

@@ -68,8 +68,10 @@ struct BatchSlot {
   cudaGraph_t graph[2] = {nullptr, nullptr};      // [0] k_batch, [1] k_batch_any
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
   cudaEvent_t done_ev = nullptr;
+  cudaEvent_t t0_ev = nullptr, t1_ev = nullptr;  // timing events around the replay (batch_timing)
   uint32_t epoch = 0;
   bool held = false;
+  bool timed = false;  // the last replay was bracketed by t0_ev / t1_ev
   size_t n = 0;
   // DMA lanes: for each direction (D2D, H2D, D2H) `lanes` chains of `items` copy-engine
   // memcpy nodes, each followed by a completion kernel; item k = (dir * lanes + lane) *
@@ -84,6 +86,16 @@ struct BatchSlot {
 
 mpt_status batch_setup(mpt_ctx_t c);
 void batch_teardown(mpt_ctx_t c);
+
+// The checks mpt_batch_submit applies to each transfer on its own (direction, NULL
+// pointers, memory kinds against the direction).  *src_kind / *dst_kind: 0 device, 1
+// page-locked host, 2 pageable host (-1 when not checked).  The cross-transfer checks
+// (overlaps) are the batch's.
+mpt_status batch_check_xfer(mpt_ctx_t c, const mpt_xfer& x, int* src_kind, int* dst_kind);
+
+// Device time in ms between the timing events around a finished batch's replay (from the
+// stream reaching the replay to its end), or -1 when the batch was not timed.
+float batch_gpu_ms(mpt_batch_t b);
 
 inline uint32_t tune_key(uint32_t dir, uint32_t mode, uint32_t bucket) { return (dir << 16) | (mode << 8) | bucket; }
 
@@ -146,4 +158,5 @@ struct mpt_ctx_s {
   uint32_t batch_dma_lanes = 0, batch_dma_items = 0;  // per direction; items per lane
   uint64_t batch_dma_min = 0;                         // smallest entry a DMA lane takes
   bool batch_dma_set = false;                         // configured (else environment defaults)
+  bool batch_timing = false;                          // bracket each batch replay with timing events
 };

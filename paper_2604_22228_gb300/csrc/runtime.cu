@@ -479,9 +479,21 @@ mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const voi
   return MPT_OK;
 }
 
+// True when [a, a+n) and [b, b+n) share a byte.
+bool ranges_overlap(const void* a, const void* b, uint64_t n) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return n > 0 && (x < y ? y - x < n : x - y < n);
+}
+
 // Pointer kinds must fit the direction.  Host sides must be page-locked, except for plans
-// whose paths all reach host memory without a copy engine touching it (pageable_ok).
-mpt_status check_pointers(mpt_ctx_t c, uint32_t dir, const void* dst, const void* src, bool pageable_ok = false) {
+// whose paths all reach host memory without a copy engine touching it (pageable_ok).  The
+// source and destination ranges must not overlap: the paths move disjoint chunks at the
+// same time, so an overlapping copy would read bytes another path is writing.
+mpt_status check_pointers(mpt_ctx_t c, uint32_t dir, const void* dst, const void* src, uint64_t nbytes,
+                          bool pageable_ok = false) {
+  if (ranges_overlap(dst, src, nbytes))
+    return fail(MPT_EINVAL, "source %p and destination %p overlap within %llu bytes", src, dst,
+                (unsigned long long)nbytes);
   const bool pg = pageable_ok;
   MemKind ks = classify(src, c->device, pg), kd = classify(dst, c->device, pg);
   if (ks == kMemPageable) ks = kMemHost;
@@ -982,7 +994,7 @@ mpt_status mpt_capture(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void* src,
   *out = nullptr;
   CUDA_TRY(cudaSetDevice(c->device));
   if (plan->nbytes > 0) {
-    mpt_status st = check_pointers(c, plan->dir, dst, src, pageable_ok(c, plan));
+    mpt_status st = check_pointers(c, plan->dir, dst, src, plan->nbytes, pageable_ok(c, plan));
     if (st != MPT_OK) return st;
   }
   GraphKey key{(uint64_t)(uintptr_t)src, (uint64_t)(uintptr_t)dst, plan->nbytes, plan->dir, plan->hash};
@@ -1049,7 +1061,7 @@ mpt_status mpt_prepare(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void* src,
   if (mode == MPT_PREPARE_GRAPH) return mpt_capture(c, plan, dst, src, out);
   CUDA_TRY(cudaSetDevice(c->device));
   if (plan->nbytes > 0) {
-    mpt_status st = check_pointers(c, plan->dir, dst, src, pageable_ok(c, plan));
+    mpt_status st = check_pointers(c, plan->dir, dst, src, plan->nbytes, pageable_ok(c, plan));
     if (st != MPT_OK) return st;
   }
   mpt_graph_s* g = new mpt_graph_s;
@@ -1091,7 +1103,7 @@ mpt_status mpt_graph_rebind(mpt_graph_t g, mpt_plan_t plan, void* dst, const voi
     return fail(MPT_EINVAL, "mpt_graph_rebind: the plan is not the one the graph was captured from");
   CUDA_TRY(cudaSetDevice(c->device));
   if (plan->nbytes > 0) {
-    mpt_status st = check_pointers(c, plan->dir, dst, src, pageable_ok(c, plan));
+    mpt_status st = check_pointers(c, plan->dir, dst, src, plan->nbytes, pageable_ok(c, plan));
     if (st != MPT_OK) return st;
   }
   GraphKey key{(uint64_t)(uintptr_t)src, (uint64_t)(uintptr_t)dst, plan->nbytes, plan->dir, plan->hash};
@@ -1138,7 +1150,7 @@ mpt_status mpt_launch_eager(mpt_ctx_t c, mpt_plan_t plan, void* dst, const void*
   if (!c || !plan) return fail(MPT_EINVAL, "mpt_launch_eager: NULL argument");
   CUDA_TRY(cudaSetDevice(c->device));
   if (plan->nbytes > 0) {
-    mpt_status st = check_pointers(c, plan->dir, dst, src, pageable_ok(c, plan));
+    mpt_status st = check_pointers(c, plan->dir, dst, src, plan->nbytes, pageable_ok(c, plan));
     if (st != MPT_OK) return st;
   }
   return eager(c, plan, dst, src, static_cast<cudaStream_t>(stream));
@@ -1150,6 +1162,7 @@ mpt_status mpt_sm_copy(mpt_ctx_t c, void* dst, const void* src, uint64_t nbytes,
   if (variant > MPT_SM_TILE8K) return fail(MPT_EINVAL, "mpt_sm_copy: unknown variant %u", variant);
   if (nbytes == 0) return MPT_OK;
   if (!dst || !src) return fail(MPT_EINVAL, "mpt_sm_copy: NULL pointer");
+  if (ranges_overlap(dst, src, nbytes)) return fail(MPT_EINVAL, "mpt_sm_copy: source and destination overlap");
   CUDA_TRY(cudaSetDevice(c->device));
   const MemKind ks = classify(src, c->device, c->pageable), kd = classify(dst, c->device, c->pageable);
   if (ks == kMemOther || kd == kMemOther)

@@ -187,3 +187,55 @@ def test_replay_keeps_the_schedule_and_results(ctx):
     assert all(done[k][1] == due[k] and done[k][3] >= due[k] for k in range(n))  # arrival = schedule
     assert sorted(late)[n // 2] < 1_000_000  # the native loop keeps the schedule (median < 1 ms)
     assert ar.digests("dst") == ar.digests("src")
+
+
+def test_bad_request_among_good_ones_refused_alone(ctx):
+    """Requests are checked one by one at admission: a request with the wrong memory kinds,
+    submitted amid valid ones that share its batch, is refused on its own and the others
+    complete with their sources' bytes."""
+    import torch
+    ar = Arenas(200, payload.SEED_SERVE + 3)
+    h = torch.ones(1 << 16, dtype=torch.uint8).pin_memory()
+    d = torch.zeros(1 << 16, dtype=torch.uint8, device="cuda")
+    server = mpt.mpt_serve_start(ctx)
+    bad_tag = 10 ** 6
+    for i, (k, s_ar, s_off, d_ar, d_off, nb, dr) in enumerate(ar.reqs):
+        if i == len(ar.reqs) // 2:  # device-to-device from page-locked host memory
+            mpt.mpt_serve_submit(server, h.data_ptr(), d.data_ptr(), 4096, mpt.MPT_D2D, bad_tag)
+        mpt.mpt_serve_submit(server, ar.ptr(s_ar, s_off), ar.ptr(d_ar, d_off), nb, dr, k)
+    done = {}
+    t0 = time.time()
+    while len(done) < len(ar.reqs) + 1 and time.time() - t0 < 60:
+        for c in mpt.mpt_serve_poll(server):
+            done[c[0]] = c
+    stats = mpt.mpt_serve_stats(server)
+    mpt.mpt_serve_stop(server)
+    assert done[bad_tag][5] == mpt.MPT_EINVAL and stats["rejected"] == 1
+    assert all(done[k][5] == mpt.MPT_OK for k in range(len(ar.reqs)))
+    assert ar.digests("dst") == ar.digests("src")
+    assert int(d.sum()) == 0
+
+
+def test_backlog_of_a_slow_client_drains_in_order(ctx):
+    """A client that stops polling leaves finished requests waiting in the server; polling
+    later hands each out once, oldest first, in pieces of any size, and the counters
+    record the backlog, the longest worker turn and the admission queue."""
+    ar = Arenas(3000, payload.SEED_SERVE + 4, median=16 * KiB, cap=256 * KiB)
+    n = len(ar.reqs)
+    server = mpt.mpt_serve_start(ctx)
+    for k, s_ar, s_off, d_ar, d_off, nb, dr in ar.reqs:
+        mpt.mpt_serve_submit(server, ar.ptr(s_ar, s_off), ar.ptr(d_ar, d_off), nb, dr, k)
+    t0 = time.time()
+    while mpt.mpt_serve_stats(server)["completed"] < n and time.time() - t0 < 60:
+        time.sleep(0.01)
+    stats = mpt.mpt_serve_stats(server)
+    got = []
+    while len(got) < n and time.time() - t0 < 60:
+        got += mpt.mpt_serve_poll(server, cap=97)
+    mpt.mpt_serve_stop(server)
+    assert stats["completed"] == n and stats["max_pending_completions"] == n
+    assert stats["max_turn_ns"] > 0 and stats["max_waiting"] >= 1
+    assert sorted(c[0] for c in got) == list(range(n))
+    assert all(c[5] == mpt.MPT_OK for c in got)
+    assert all(a[3] <= b[3] for a, b in zip(got, got[1:]))  # oldest completion first
+    assert ar.digests("dst") == ar.digests("src")

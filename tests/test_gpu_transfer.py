@@ -234,6 +234,61 @@ def test_pointer_kind_checked(ctx):
     mpt.mpt_plan_destroy(plan)
 
 
+def test_overlapping_source_and_destination_rejected(ctx):
+    """The paths copy their chunks at the same time, so a message whose source and
+    destination ranges share bytes has no defined result: every entry point refuses it with
+    MPT_EINVAL and moves nothing.  Ranges that only touch are fine."""
+    import torch
+    n = 64 * 1024
+    buf = Buf(3 * n, "dev")
+    data = seeded("u8", 77, 3 * n)
+    buf.fill(data)
+    base = buf.ptr
+    plan = mpt.mpt_plan(ctx, n, P.D2D, [(P.CE, 32768, 16384), (P.SM, 32768, 16384)])
+    try:
+        for dst, src in ((base + 16, base), (base, base + n - 16), (base, base)):
+            for call in (lambda: mpt.mpt_capture(ctx, plan, dst, src),
+                         lambda: mpt.mpt_prepare(ctx, plan, dst, src, mpt.MPT_PREPARE_EAGER),
+                         lambda: mpt.mpt_launch_eager(ctx, plan, dst, src),
+                         lambda: mpt.mpt_sm_copy(ctx, dst, src, n)):
+                with pytest.raises(mpt.MptError) as e:
+                    call()
+                assert e.value.status == mpt.MPT_EINVAL and "overlap" in str(e.value)
+        torch.cuda.synchronize()
+        assert np.array_equal(buf.numpy(), data), "a refused copy moved bytes"
+        # adjacent ranges [base, base+n) -> [base+n, base+2n) are a valid copy
+        g = mpt.mpt_capture(ctx, plan, base + n, base)
+        mpt.mpt_launch(g)
+        mpt.mpt_graph_release(g)
+        out = buf.numpy()
+        assert np.array_equal(out[n:2 * n], T.copy(data[:n]))
+        assert np.array_equal(out[:n], data[:n]) and np.array_equal(out[2 * n:], data[2 * n:])
+    finally:
+        mpt.mpt_plan_destroy(plan)
+
+
+def test_batch_source_overlapping_a_destination_rejected(ctx):
+    """A batch's transfers run at the same time: a source that overlaps any destination of
+    the same batch (its own or another transfer's) is refused."""
+    n = 4096
+    buf = Buf(4 * n, "dev")
+    data = seeded("u8", 78, 4 * n)
+    buf.fill(data)
+    b = buf.ptr
+    for xf in ([(b, b + n // 2, n, P.D2D)],                                 # its own destination
+               [(b, b + 2 * n, n, P.D2D), (b + 3 * n, b + n // 2, n, P.D2D)]):  # another's
+        with pytest.raises(mpt.MptError) as e:
+            mpt.mpt_batch_submit(ctx, xf)
+        assert e.value.status == mpt.MPT_EINVAL and "overlaps a destination" in str(e.value)
+    # sources may overlap one another
+    h = mpt.mpt_batch_submit(ctx, [(b, b + 2 * n, n, P.D2D), (b, b + 3 * n, n, P.D2D)])
+    mpt.mpt_batch_wait(h)
+    mpt.mpt_batch_release(h)
+    out = buf.numpy()
+    assert np.array_equal(out[:2 * n], data[:2 * n]), "a refused batch moved bytes"
+    assert np.array_equal(out[2 * n:3 * n], data[:n]) and np.array_equal(out[3 * n:], data[:n])
+
+
 def test_staged_chunk_above_stage_size_rejected(ctx):
     n = 32 * MiB
     src, dst = Buf(n, "dev"), Buf(n, "dev")
