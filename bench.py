@@ -528,8 +528,11 @@ def run_ours(args):
             up = mpt.mpt_plan(ctx, total, mpt.MPT_H2D, None)
             down = mpt.mpt_plan(ctx, total, mpt.MPT_D2H, None)
         else:  # copy engines only: the link legs leave every SM to the sweep
-            up = mpt.mpt_plan(ctx, total, mpt.MPT_H2D, [(mpt.MPT_PATH_CE, 65536, 512 * MiB)])
-            down = mpt.mpt_plan(ctx, total, mpt.MPT_D2H, [(mpt.MPT_PATH_CE, 65536, 512 * MiB)])
+            # one memcpy node per leg by default: one copy engine nearly fills a link
+            # direction, and parallel branches of both legs could land on the same engines
+            chunk = args.e2e_chunk_mib * MiB if args.e2e_chunk_mib else (total + 15) // 16 * 16
+            up = mpt.mpt_plan(ctx, total, mpt.MPT_H2D, [(mpt.MPT_PATH_CE, 65536, chunk)])
+            down = mpt.mpt_plan(ctx, total, mpt.MPT_D2H, [(mpt.MPT_PATH_CE, 65536, chunk)])
         g_up = [mpt.mpt_capture(ctx, up, sp, hsrc.data_ptr()) for sp, _ in sets]
         g_down = [mpt.mpt_capture(ctx, down, hdst.data_ptr(), dp) for _, dp in sets]
         sweep_h = [step_handles,
@@ -575,7 +578,7 @@ def run_ours(args):
             bool(torch.equal(hdst[offs[20]:offs[20] + SIZES[20]], hsrc[offs[20]:offs[20] + SIZES[20]]))
         e2e = {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": total, "d2h_bytes_per_step": total,
                "steps": e2e_steps, "pipelined": "2 device arena sets; step k down while step k+1 comes up",
-               "link_plans": args.e2e_plan}
+               "link_plans": args.e2e_plan, "link_chunk_mib": args.e2e_chunk_mib or "whole leg"}
         for g in g_up + g_down + sweep_h[1]:
             mpt.mpt_graph_release(g)
         for p in (up, down):
@@ -1678,6 +1681,8 @@ def main(argv=None):
                     help="cap on K back-to-back launches per size in the per-transfer sweep")
     ap.add_argument("--cpu-all-cores-seconds", type=float, default=5.0,
                     help="oracle sample on every host core (0 skips it)")
+    ap.add_argument("--e2e-chunk-mib", type=int, default=0,
+                    help="copy-engine chunk of the e2e link legs in MiB (0 = one chunk per leg)")
     ap.add_argument("--e2e-plan", choices=["tuned", "ce"], default="ce",
                     help="plans of the end-to-end link legs: tuned, or copy engines only")
     ap.add_argument("--no-cpu", action="store_true")
