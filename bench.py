@@ -627,7 +627,8 @@ def run_ours(args):
                 serving_replay = run_serving_replay(mpt, torch, ctx, rates, args.serve_seconds,
                                                     trace_dir=args.serve_trace_dir,
                                                     max_inflight=args.serve_max_inflight,
-                                                    verify=not args.serve_no_verify)
+                                                    verify=not args.serve_no_verify,
+                                                    warmup=not args.serve_no_warmup)
         finally:
             gc.enable()
             gc.unfreeze()
@@ -970,22 +971,27 @@ def run_batched(mpt, torch, ctx, stream, reps=5):
         "parity_ok": bool(ok)}
 
 
-def _serve_warmup(mpt, ctx, rows, **server_args):
-    """Untimed warm-up before a serving run's clock starts, on a server of its own (so the
-    timed server's counters start clean): submit `rows` (src, dst, bytes, dir) at once and
-    drain their completions.  Building a long trace leaves the GPU idle for seconds, and the
-    first batches after that ran far below the link rate."""
-    server = mpt.mpt_serve_start(ctx, **server_args)
-    try:
-        for k, (sp, dp, nb, d) in enumerate(rows):
-            mpt.mpt_serve_submit(server, sp, dp, nb, d, k)
-        got, t_end = 0, time.perf_counter() + 30
-        while got < len(rows) and time.perf_counter() < t_end:
+def _serve_warmup(mpt, server, rows, seconds=0.5, tag0=1 << 62):
+    """Untimed warm-up on the server about to be timed, right before its schedule starts:
+    waves of `rows` (src, dst, bytes, dir), each drained before the next, for at least
+    `seconds`; then the server's high-water marks are reset.  Building a long trace leaves
+    the GPU idle for seconds, and about 0.1 s into the next activity it ran far below the
+    link rate for 50-100 ms (a clock or link power state coming up); half a second of load
+    gets it past that before the clock starts."""
+    t_end = time.perf_counter() + seconds
+    tag = tag0
+    while True:
+        for sp, dp, nb, d in rows:
+            mpt.mpt_serve_submit(server, sp, dp, nb, d, tag)
+            tag += 1
+        got, t_fail = 0, time.perf_counter() + 30
+        while got < len(rows) and time.perf_counter() < t_fail:
             got += len(mpt.mpt_serve_poll(server))
-    finally:
-        mpt.mpt_serve_stop(server)
-    if got < len(rows):
-        raise RuntimeError("serving warm-up did not complete")
+        if got < len(rows):
+            raise RuntimeError("serving warm-up did not complete")
+        if time.perf_counter() >= t_end:
+            break
+    mpt.mpt_serve_reset_stats(server)
 
 
 def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30, streams=0, batch_ctas=0):
@@ -1024,8 +1030,8 @@ def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30, streams=0, batc
             s_t = src_host if d == mpt.MPT_H2D else src_dev
             warm.append((s_t.data_ptr(), ring[kind].data_ptr() + wh[kind], nb, d))
             wh[kind] += (nb + 255) // 256 * 256
-        _serve_warmup(mpt, ctx, warm, staging_budget_bytes=budget, streams=streams, batch_ctas=batch_ctas)
         server = mpt.mpt_serve_start(ctx, staging_budget_bytes=budget, streams=streams, batch_ctas=batch_ctas)
+        _serve_warmup(mpt, server, warm)
         meta = {}
 
         def harvest():
@@ -1069,7 +1075,7 @@ def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30, streams=0, batc
             q.append((k, start))
             return start
 
-        t0 = mpt.mpt_now_ns() + 20_000_000
+        t0 = mpt.mpt_now_ns() + 2_000_000
         for k, (t_arr, nb, d) in enumerate(sched):
             due = t0 + int(t_arr * 1e9)
             while mpt.mpt_now_ns() < due:
@@ -1112,7 +1118,7 @@ def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30, streams=0, batc
 
 
 def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30, trace_dir=None, max_inflight=0,
-                       verify=True):
+                       verify=True, warmup=True):
     """The serving workload with a native load generator (mpt_serve_replay keeps the Poisson
     schedule to about a microsecond), so latency from the scheduled arrival is the server's.
     Destinations come from sequential rings (12 GiB device, 4 GiB host), each lap tens of
@@ -1174,14 +1180,24 @@ def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30, trace_di
                     next_idx[k] = nxt[i][2]
         late = (ctypes.c_uint64 * n)()
         due = (ctypes.c_uint64 * n)()
-        # the first rows stay short of either ring's end
-        _serve_warmup(mpt, ctx, rows[:2048], staging_budget_bytes=budget, max_inflight_batches=max_inflight)
+        if warmup:
+            # the GPU touches every byte of host memory the run will use (the host ring and
+            # the host source) once through the zero-copy kernel, before the server takes
+            # the context; the wave warm-up follows on the server
+            ws = torch.cuda.Stream()
+            for o in range(0, ring["host"].numel(), src_dev.numel()):
+                k = min(src_dev.numel(), ring["host"].numel() - o)
+                mpt.mpt_sm_copy(ctx, ring["host"].data_ptr() + o, src_dev.data_ptr(), k, stream=ws)
+            mpt.mpt_sm_copy(ctx, ring["dev"].data_ptr(), src_host.data_ptr(), src_host.numel(), stream=ws)
+            ws.synchronize()
         if trace_dir:  # the server writes one line per batch at stop
             os.environ["MPT_SERVE_BATCH_LOG"] = os.path.join(trace_dir, f"replay_batches_{int(rate)}.csv")
         server = mpt.mpt_serve_start(ctx, staging_budget_bytes=budget, max_inflight_batches=max_inflight)
         os.environ.pop("MPT_SERVE_BATCH_LOG", None)
-        # the schedule starts 50 ms from now: every step above (seconds for a long trace) is done
-        t0 = mpt.mpt_now_ns() + 50_000_000
+        if warmup:
+            _serve_warmup(mpt, server, rows[:2048])  # the first rows stay short of either ring's end
+        # the schedule starts 2 ms from now: every step above (seconds for a long trace) is done
+        t0 = mpt.mpt_now_ns() + 2_000_000
         np.frombuffer(due, dtype=np.uint64)[:] = due_rel + np.uint64(t0)
         err = []
 
@@ -1695,6 +1711,7 @@ def main(argv=None):
     ap.add_argument("--serve-rates", default="1000,10000,50000")
     ap.add_argument("--serve-max-inflight", type=int, default=0, help="replay: batches in flight (0 = default)")
     ap.add_argument("--serve-no-verify", action="store_true", help="replay: skip the digest checks")
+    ap.add_argument("--serve-no-warmup", action="store_true", help="replay: start the schedule without a warm-up")
     ap.add_argument("--serve-trace-dir", default=None,
                     help="write per-request arrays and the server's per-batch log of each replay here")
     ap.add_argument("--serve-modes", default="python,inorder,replay",

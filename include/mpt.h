@@ -544,6 +544,12 @@ MPT_API mpt_status mpt_serve_poll(mpt_server_t server, mpt_completion* out, size
 
 MPT_API mpt_status mpt_serve_stats(mpt_server_t server, mpt_serve_stats_t* out);
 
+/* Zero the high-water marks of mpt_serve_stats (every max_* field), leaving the running
+ * counts (submitted, completed, batches, inflight_bytes, rejected) as they are: for example
+ * after a warm-up, or at the start of each monitoring interval.  A worker update that races
+ * with the reset may survive it.  Errors: EINVAL (NULL server). */
+MPT_API mpt_status mpt_serve_reset_stats(mpt_server_t server);
+
 /* Replay a request trace: submit xfers[i] (tag tags[i]) at its scheduled time due_ns[i]
  * (mpt_now_ns clock, non-decreasing), spinning between arrivals, from the calling thread --
  * a load generator that keeps the schedule to about a microsecond where a slower client

@@ -358,6 +358,10 @@ def mpt_serve_stats(server: int) -> dict:
     return {name: getattr(st, name) for name, _ in _ffi.mpt_serve_stats_t._fields_}
 
 
+def mpt_serve_reset_stats(server: int) -> None:
+    _check(lib().mpt_serve_reset_stats(server), "mpt_serve_reset_stats")
+
+
 def mpt_serve_stop(server: int) -> None:
     _check(lib().mpt_serve_stop(server), "mpt_serve_stop")
 

@@ -149,6 +149,7 @@ SIGNATURES = {
     "mpt_serve_replay": (C.c_int, [H, P(mpt_xfer), P(C.c_uint64), P(C.c_uint64), C.c_size_t, P(C.c_uint64)]),
     "mpt_serve_poll": (C.c_int, [H, P(mpt_completion), C.c_size_t, P(C.c_size_t)]),
     "mpt_serve_stats": (C.c_int, [H, P(mpt_serve_stats_t)]),
+    "mpt_serve_reset_stats": (C.c_int, [H]),
     "mpt_serve_stop": (C.c_int, [H]),
     "mpt_demo_jacobi_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_uint32, C.c_uint64, C.c_void_p]),
     "mpt_selftest_flag_timeout": (C.c_int, [H, C.c_uint64, P(C.c_uint32)]),

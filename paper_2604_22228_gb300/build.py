@@ -40,7 +40,7 @@ def _compile(nvcc: str, src: str) -> str:
 def build(force: bool = False) -> str:
     """Compile every source and link libmpt.so; returns its path."""
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, h) for h in ("kernels.cuh", "copy_device.cuh", "internal.h", "ctx.h", "host_pool.h")] + [os.path.join(INCLUDE, "mpt.h")]
+    deps = srcs + [os.path.join(CSRC, h) for h in ("kernels.cuh", "batch_kernels.cuh", "copy_device.cuh", "internal.h", "ctx.h", "host_pool.h")] + [os.path.join(INCLUDE, "mpt.h")]
     if not force and os.path.exists(OUT):
         newest = max(os.path.getmtime(d) for d in deps)
         if os.path.getmtime(OUT) >= newest:

@@ -49,7 +49,15 @@ template <bool kAny>
 __device__ __forceinline__ void batch_body(const BatchArgs& a) {
   __shared__ uint32_t s_item;
   const BatchHeader h = *a.hdr;
-  if (threadIdx.x == 0) atomicMax(a.start_inv, ~now_ns());
+  if (threadIdx.x == 0) {
+    const uint64_t t = now_ns();
+    atomicMax(a.start_inv, ~t);
+    // when the first and the last CTA of the grid started: a spread far above the launch
+    // time means the grid was only partly resident (other kernels held the SMs)
+    const uint32_t k = atomicAdd(a.started, 1u);
+    if (k == 0) a.host_stamps[0] = t;
+    if (k == gridDim.x - 1) a.host_stamps[1] = t;
+  }
   while (true) {
     if (threadIdx.x == 0) s_item = atomicAdd(a.cursor, 1u);
     __syncthreads();
@@ -123,6 +131,7 @@ void slot_free(BatchSlot& s) {
   if (s.h_scratch) cudaFreeHost(s.h_scratch);
   if (s.h_table) cudaFreeHost(s.h_table);
   if (s.h_flags) cudaFreeHost(s.h_flags);
+  if (s.h_stamps) cudaFreeHost(s.h_stamps);
   if (s.d_mem) cudaFree(s.d_mem);
   s = BatchSlot{};
 }
@@ -160,6 +169,11 @@ mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t cta
   s.args.cursor = reinterpret_cast<uint32_t*>(s.d_ctrl);
   s.args.start_inv = reinterpret_cast<unsigned long long*>(s.d_ctrl + 8);
   s.args.done = reinterpret_cast<uint32_t*>(s.d_ctrl + 256);
+  s.args.started = reinterpret_cast<uint32_t*>(s.d_ctrl + 16);
+  CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&s.h_stamps), 2 * sizeof(unsigned long long),
+                         cudaHostAllocMapped | cudaHostAllocPortable));
+  s.h_stamps[0] = s.h_stamps[1] = 0;
+  CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&s.args.host_stamps), s.h_stamps, 0));
   s.args.times = s.d_times;
   uint32_t* hf_dev = nullptr;
   CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&hf_dev), s.h_flags, 0));
@@ -309,6 +323,12 @@ struct mpt_batch_s {
   size_t n;
   uint64_t submit_ns;
 };
+
+uint64_t mpt::batch_cta_spread_ns(mpt_batch_t b) {
+  const volatile unsigned long long* t = b->ctx->slots[b->slot].h_stamps;
+  const uint64_t first = t[0], last = t[1];
+  return last >= first ? last - first : 0;
+}
 
 float mpt::batch_gpu_ms(mpt_batch_t b) {
   const mpt::BatchSlot& s = b->ctx->slots[b->slot];

@@ -1,0 +1,51 @@
+// Interface of the batched-transfer kernels (persistent descriptor-table kernel and the
+// completion kernel of its copy-engine lanes) between batch.cu and the runtime.  Kept apart
+// from kernels.cuh, which the copy kernels are compiled from.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mpt {
+
+// ---- batched transfers: persistent descriptor-table kernel --------------------------
+constexpr uint32_t kDescHostDst = 1;   // destination is host memory: publish with system fences
+constexpr uint32_t kDescHostSide = 2;  // one side is host memory: coherent loads, no read-only path
+constexpr uint32_t kDescDma = 4;       // moved by a copy-engine lane, not by the kernel (ntiles 0)
+
+struct BatchHeader {
+  uint32_t n;            // descriptors in this batch
+  uint32_t total_tiles;  // sum of tiles over descriptors
+  uint32_t tile_bytes;
+  uint32_t epoch;        // value written to a finished descriptor's host flag
+};
+
+struct BatchDesc {
+  uint64_t src, dst, bytes;
+  uint32_t first_tile;  // prefix sum of tiles before this descriptor
+  uint32_t ntiles;      // max(1, ceil(bytes / tile)); 0 for a descriptor a DMA lane moves
+  uint32_t flags;
+  uint32_t pad;
+};
+
+struct BatchArgs {
+  const BatchHeader* hdr;
+  const BatchDesc* desc;
+  uint32_t* cursor;              // next tile to claim (reset to 0 per launch)
+  unsigned long long* start_inv; // ~(kernel start time), max over CTAs
+  uint32_t* done;                // tiles finished per descriptor (reset per launch)
+  unsigned long long* times;     // completion time per descriptor (global timer, ns)
+  uint32_t* host_flags;          // device alias of page-locked flags, one per descriptor
+  uint32_t* started;             // CTAs that have started (reset to 0 per launch)
+  unsigned long long* host_stamps;  // device alias of page-locked [first, last] CTA start times
+};
+
+// Completion of one DMA-lane item: dma_map[item] is the descriptor its copy-engine node
+// moved (~0 when the item is unused); stamps its time and raises its host flag.
+__global__ void k_batch_dma_done(BatchArgs a, const uint32_t* dma_map, uint32_t item);
+
+// k_batch needs every descriptor's source and destination to agree modulo 16;
+// k_batch_any copies any alignment.
+__global__ void k_batch(BatchArgs a);
+__global__ void k_batch_any(BatchArgs a);
+
+}  // namespace mpt

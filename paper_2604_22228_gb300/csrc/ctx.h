@@ -9,6 +9,7 @@
 
 #include "host_pool.h"
 #include "internal.h"
+#include "batch_kernels.cuh"
 #include "kernels.cuh"
 
 namespace mpt {
@@ -60,6 +61,7 @@ struct BatchSlot {
   size_t table_bytes = 0, ctrl_bytes = 0;
   uint8_t* h_table = nullptr;   // page-locked table, copied to d_table by the graph
   uint32_t* h_flags = nullptr;  // page-locked, mapped: per-descriptor completion epochs
+  unsigned long long* h_stamps = nullptr;  // page-locked, mapped: first and last CTA start
   void* d_mem = nullptr;
   uint8_t* d_table = nullptr;
   uint8_t* d_ctrl = nullptr;
@@ -96,6 +98,10 @@ mpt_status batch_check_xfer(mpt_ctx_t c, const mpt_xfer& x, int* src_kind, int* 
 // Device time in ms between the timing events around a finished batch's replay (from the
 // stream reaching the replay to its end), or -1 when the batch was not timed.
 float batch_gpu_ms(mpt_batch_t b);
+
+// Time between the first and the last CTA start of a finished batch's kernel (global timer):
+// near the launch time when the whole grid became resident at once.
+uint64_t batch_cta_spread_ns(mpt_batch_t b);
 
 inline uint32_t tune_key(uint32_t dir, uint32_t mode, uint32_t bucket) { return (dir << 16) | (mode << 8) | bucket; }
 

@@ -24,6 +24,7 @@
 #include <chrono>
 #include <condition_variable>
 #include <cstdio>
+#include <cstring>
 #include <deque>
 #include <mutex>
 #include <thread>
@@ -50,6 +51,7 @@ struct BatchRecord {
   uint64_t launch_ns, done_ns, reqs, bytes, bytes_dir[3];
   uint32_t stream;
   float gpu_ms;  // device time of the replay (timing events), -1 if unknown
+  uint64_t cta_spread_ns;  // first to last CTA start of the batch kernel
 };
 
 struct InFlight {
@@ -91,8 +93,11 @@ struct mpt_server_s {
   std::atomic<uint64_t> max_pending{0}, max_turn_ns{0}, max_waiting{0};
   std::atomic<uint64_t> max_batch_ns{0}, max_batch_reqs{0}, max_batch_bytes{0};  // the longest batch
   std::atomic<uint64_t> max_harvest_ns{0}, max_admit_ns{0}, max_launch_ns{0};    // worker turn phases
+  bool shortest_first = false;            // order each batch by size before launching it
   std::string batch_log;                  // MPT_SERVE_BATCH_LOG: CSV written at stop
-  std::vector<mpt::BatchRecord> records;  // worker-owned until the worker exits
+  // worker-owned until the worker exits; a deque, since a vector's doubling would copy
+  // millions of records inside one worker turn
+  std::deque<mpt::BatchRecord> records;
 };
 
 namespace mpt {
@@ -157,7 +162,7 @@ void serve_loop(mpt_server_s* s) {
         if (!s->batch_log.empty())
           s->records.push_back(BatchRecord{f.launch_ns, t_done, f.reqs.size(), f.bytes,
                                            {f.bytes_dir[0], f.bytes_dir[1], f.bytes_dir[2]}, f.stream,
-                                           batch_gpu_ms(f.batch)});
+                                           batch_gpu_ms(f.batch), batch_cta_spread_ns(f.batch)});
         if (took > s->max_batch_ns) {
           s->max_batch_ns = took;
           s->max_batch_reqs = f.reqs.size();
@@ -204,6 +209,9 @@ void serve_loop(mpt_server_s* s) {
     }
     bool launched = false;
     if (!building.empty() && flight.size() < s->cfg.max_inflight_batches && si < s->streams.size()) {
+      if (s->shortest_first)  // tiles go out in descriptor order: short requests first
+        std::stable_sort(building.begin(), building.end(),
+                         [](const Request& a, const Request& b) { return a.x.bytes < b.x.bytes; });
       xs.resize(building.size());
       for (size_t k = 0; k < building.size(); ++k) xs[k] = building[k].x;
       mpt_batch_t b = nullptr;
@@ -293,6 +301,7 @@ mpt_status mpt_serve_start(mpt_ctx_t ctx, const mpt_serve_config* cfg, mpt_serve
   c.batch_ctas = want_ctas;
   s->cfg = c;
   if (const char* log = std::getenv("MPT_SERVE_BATCH_LOG")) s->batch_log = log;
+  if (const char* o = std::getenv("MPT_SERVE_ORDER")) s->shortest_first = std::strcmp(o, "size") == 0;
   ctx->batch_timing = !s->batch_log.empty();
   if (cudaSetDevice(ctx->device) != cudaSuccess) {
     delete s;
@@ -383,6 +392,15 @@ mpt_status mpt_serve_stats(mpt_server_t s, mpt_serve_stats_t* out) {
   return MPT_OK;
 }
 
+mpt_status mpt_serve_reset_stats(mpt_server_t s) {
+  if (!s) return fail(MPT_EINVAL, "mpt_serve_reset_stats: NULL server");
+  for (std::atomic<uint64_t>* m : {&s->max_inflight_bytes, &s->max_pending, &s->max_turn_ns, &s->max_waiting,
+                                   &s->max_batch_ns, &s->max_batch_reqs, &s->max_batch_bytes, &s->max_harvest_ns,
+                                   &s->max_admit_ns, &s->max_launch_ns})
+    m->store(0);
+  return MPT_OK;
+}
+
 mpt_status mpt_serve_stop(mpt_server_t s) {
   if (!s) return MPT_OK;
   {
@@ -402,12 +420,12 @@ mpt_status mpt_serve_stop(mpt_server_t s) {
   }
   if (!s->batch_log.empty()) {  // one line per batch, launch order not guaranteed
     if (FILE* f = std::fopen(s->batch_log.c_str(), "w")) {
-      std::fprintf(f, "launch_ns,done_ns,requests,bytes,d2d_bytes,h2d_bytes,d2h_bytes,stream,gpu_ms\n");
+      std::fprintf(f, "launch_ns,done_ns,requests,bytes,d2d_bytes,h2d_bytes,d2h_bytes,stream,gpu_ms,cta_spread_us\n");
       for (const BatchRecord& r : s->records)
-        std::fprintf(f, "%llu,%llu,%llu,%llu,%llu,%llu,%llu,%u,%.4f\n", (unsigned long long)r.launch_ns,
+        std::fprintf(f, "%llu,%llu,%llu,%llu,%llu,%llu,%llu,%u,%.4f,%.1f\n", (unsigned long long)r.launch_ns,
                      (unsigned long long)r.done_ns, (unsigned long long)r.reqs, (unsigned long long)r.bytes,
                      (unsigned long long)r.bytes_dir[0], (unsigned long long)r.bytes_dir[1],
-                     (unsigned long long)r.bytes_dir[2], r.stream, r.gpu_ms);
+                     (unsigned long long)r.bytes_dir[2], r.stream, r.gpu_ms, r.cta_spread_ns / 1e3);
       std::fclose(f);
     }
   }

@@ -232,7 +232,11 @@ def test_backlog_of_a_slow_client_drains_in_order(ctx):
     got = []
     while len(got) < n and time.time() - t0 < 60:
         got += mpt.mpt_serve_poll(server, cap=97)
+    mpt.mpt_serve_reset_stats(server)  # high-water marks to zero, running counts kept
+    after = mpt.mpt_serve_stats(server)
     mpt.mpt_serve_stop(server)
+    assert all(v == 0 for k, v in after.items() if k.startswith("max_"))
+    assert after["completed"] == n and after["submitted"] == n and after["batches"] == stats["batches"]
     assert stats["completed"] == n and stats["max_pending_completions"] == n
     assert stats["max_turn_ns"] > 0 and stats["max_waiting"] >= 1
     assert sorted(c[0] for c in got) == list(range(n))
