@@ -1117,6 +1117,25 @@ def run_serving(mpt, torch, ctx, rates, seconds, budget=8 << 30, streams=0, batc
     return out
 
 
+def ring_next_overwrite(place):
+    """For destinations laid out in rings lap after lap (place[k] = (ring, lap, start, end),
+    starts and ends increasing with k within a lap), the index of the first request of the
+    next lap whose destination overlaps request k's, or -1: from that request's scheduled
+    time on, k's destination bytes may be overwritten."""
+    import bisect
+    lap_rows = {}
+    for k, (kind, lap, a, b) in enumerate(place):
+        lap_rows.setdefault((kind, lap), []).append((b, a, k))
+    out = [-1] * len(place)
+    for k, (kind, lap, a, b) in enumerate(place):
+        nxt = lap_rows.get((kind, lap + 1))
+        if nxt:
+            i = bisect.bisect_right(nxt, (a, 1 << 64, 1 << 64))  # the first whose end is past a
+            if i < len(nxt) and nxt[i][1] < b:
+                out[k] = nxt[i][2]
+    return out
+
+
 def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30, trace_dir=None, max_inflight=0,
                        verify=True, warmup=True):
     """The serving workload with a native load generator (mpt_serve_replay keeps the Poisson
@@ -1165,19 +1184,8 @@ def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30, trace_di
         xf = mpt.make_xfers(rows)
         tags = (ctypes.c_uint64 * n)(*range(n))
         due_rel = np.array([int(t * 1e9) for t, _, _ in sched], dtype=np.uint64)
-        # the ring reuses a destination when the next lap reaches it: next_idx[k] is the first
-        # request of the next lap overlapping k's destination; a digest of k taken after that
-        # request is due may see its bytes and proves nothing
-        lap_rows = {}
-        for k, (kind, lap, a, b) in enumerate(place):
-            lap_rows.setdefault((kind, lap), []).append((b, a, k))   # ends increase with k
-        next_idx = [-1] * n
-        for k, (kind, lap, a, b) in enumerate(place):
-            nxt = lap_rows.get((kind, lap + 1))
-            if nxt:
-                i = bisect.bisect_right(nxt, (a, 1 << 64, 1 << 64))  # first whose end > a
-                if i < len(nxt) and nxt[i][1] < b:
-                    next_idx[k] = nxt[i][2]
+        # a digest of request k taken after next_idx[k] is due may see that request's bytes
+        next_idx = ring_next_overwrite(place)
         late = (ctypes.c_uint64 * n)()
         due = (ctypes.c_uint64 * n)()
         if warmup:
