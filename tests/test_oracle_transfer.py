@@ -148,3 +148,28 @@ def test_fill_window_matches_prefix_stream():
         full = payload.fill(kind, 33, 5000)
         for off, n in [(0, 10), (1, 7), (3, 100), (4095, 905), (17, 0)]:
             assert np.array_equal(payload.fill_window(kind, 33, off, n), full[off:off + n]), (kind, off, n)
+
+
+def test_workload_generators_follow_their_stated_distributions():
+    """The synthetic inputs stand in for the paper's workloads, so their distributions are
+    pinned: batch sizes log-uniform on [256 B, 16 MiB] (quartiles at 4 KiB, 64 KiB and
+    1 MiB); serving arrivals Poisson (exponential gaps with mean 1/rate, coefficient of
+    variation 1), sizes lognormal around 1 MiB with sigma 1.5, directions 50/25/25."""
+    import math
+    sizes, _, _ = payload.batch_workload(4096)
+    s = sorted(sizes)
+    for q, want in ((0.25, 4096), (0.5, 65536), (0.75, 1 << 20)):
+        got = s[int(q * len(s))]
+        assert abs(math.log(got / want)) < 0.35, (q, got)   # 1/8 of the log range is 1.39
+    sched = payload.serving_schedule(10000.0, 2.0)
+    n = len(sched)
+    gaps = [b[0] - a[0] for a, b in zip(sched, sched[1:])]
+    mean = sum(gaps) / len(gaps)
+    sd = math.sqrt(sum((g - mean) ** 2 for g in gaps) / len(gaps))
+    assert abs(mean * 10000.0 - 1.0) < 0.03 and abs(sd / mean - 1.0) < 0.05
+    logs = [math.log(nb / (1 << 20)) for _, nb, _ in sched if 1 << 10 < nb < 200 << 20]
+    mu = sum(logs) / len(logs)
+    sigma = math.sqrt(sum((x - mu) ** 2 for x in logs) / len(logs))
+    assert abs(mu) < 0.05 and abs(sigma - 1.5) < 0.06, (mu, sigma)
+    mix = [sum(1 for _, _, d in sched if d == k) / n for k in (0, 1, 2)]
+    assert abs(mix[0] - 0.5) < 0.02 and abs(mix[1] - 0.25) < 0.02 and abs(mix[2] - 0.25) < 0.02
