@@ -585,10 +585,10 @@ def run_ours(args):
             mpt.mpt_plan_destroy(p)
         del src2, dst2
 
-    config1 = None
+    copy64 = None
     if not args.no_baselines:
-        config1 = run_config1(mpt, torch, ctx, stream)
-        ok = ok and config1["parity_ok"]
+        copy64 = run_copy64_split(mpt, torch, ctx, stream)
+        ok = ok and copy64["parity_ok"]
     lifecycle = run_graph_lifecycle(mpt, torch, ctx, stream)
     windows = None if args.no_windows else run_windows(mpt, torch, ctx)
     jacobi = None if args.no_jacobi else run_jacobi(mpt, torch, ctx)
@@ -694,7 +694,7 @@ def run_ours(args):
             "clocks": clk, "parity_ok": ok, "host_elapsed_s": round(host_elapsed, 4), "tune_s": round(tune_s, 2),
             "batched": batched, "serving": serving, "serving_replay": serving_replay, "host_sweep": host_sweep,
             "graph_lifecycle": lifecycle,
-            "windows": windows, "jacobi": jacobi, "config1_64MiB": config1, "pageable_host": pageable,
+            "windows": windows, "jacobi": jacobi, "copy64MiB_ce_sm_50_50": copy64, "pageable_host": pageable,
             "sweep": sweep, "wall_s": round(time.perf_counter() - t_wall0, 2),
         }
         print(json.dumps(line), flush=True)
@@ -779,7 +779,7 @@ def run_pageable_sweep(mpt, torch, ctx, stream, sizes=(4 * MiB, 16 * MiB, 64 * M
             "note": "GB/s of message bytes; host buffers pageable (torch CPU tensors, not pinned)"}
 
 
-def run_config1(mpt, torch, ctx, stream, replays=100, warm=10):
+def run_copy64_split(mpt, torch, ctx, stream, replays=100, warm=10):
     """The 64 MiB worked configuration: one uint8 message (seed 0x5EED0001) over copy engine +
     SM kernel at 50/50 with 4 MiB chunks in one graph, against each path alone.  10 warm-up
     replays, then `replays` replays each bracketed by CUDA events, a 256 MiB write before each

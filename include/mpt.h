@@ -402,7 +402,7 @@ MPT_API mpt_status mpt_tune_get(mpt_ctx_t ctx, uint32_t dir, uint64_t nbytes, ui
 MPT_API mpt_status mpt_batch_configure(mpt_ctx_t ctx, uint32_t slots, uint32_t max_xfers, uint32_t ctas,
                                        uint32_t tile_bytes);
 
-/* DMA lanes of the batch (config 4's "kernel plus DMA lanes"): per direction (D2D, H2D,
+/* DMA lanes of the batch (the batch kernel plus copy-engine lanes): per direction (D2D, H2D,
  * D2H) `lanes` copy-engine lanes, each taking up to `items_per_lane` entries of at least
  * `min_bytes` per batch, largest first to the least-loaded lane of the entry's direction;
  * the kernel moves everything else.  Entries with a pageable host side stay with the
@@ -414,7 +414,7 @@ MPT_API mpt_status mpt_batch_configure(mpt_ctx_t ctx, uint32_t slots, uint32_t m
 MPT_API mpt_status mpt_batch_configure_dma(mpt_ctx_t ctx, uint32_t lanes, uint32_t items_per_lane,
                                            uint64_t min_bytes);
 
-/* Batch autotuner (config 4: autotuned CTA count and tile size).  Runs the representative
+/* Batch autotuner (CTA count, tile size and DMA lanes chosen by measurement).  Runs the representative
  * batch `xfers` (n entries; their destinations are written) `reps` times (0 = 3) under each
  * candidate setting -- kernel CTAs in {1, 2, 3} x SMs, tile bytes in {64, 128, 256, 512,
  * 1024} KiB, DMA lanes off or 2 per direction for entries of at least 4 MiB -- and keeps the
