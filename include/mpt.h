@@ -222,6 +222,15 @@ MPT_API mpt_status mpt_lane_times(mpt_ctx_t ctx, float* out_ms, uint32_t cap, ui
  * receives an implementation-defined code of the wait that gave up. */
 MPT_API mpt_status mpt_ctx_status(mpt_ctx_t ctx, uint32_t* site);
 
+/* Set the wait limit of the staged host-to-device path's device-side flag waits (hop two
+ * waiting for a chunk's hop one, Algorithm 2 StageHostCopy) for every graph of this context,
+ * captured before or after the call: the limit lives in device memory and each wait reads it
+ * when it starts.  ns = 0 restores the default (2 s); ns above 10 s is refused.  A wait that
+ * runs out records MPT_ETIMEDOUT (mpt_ctx_status) and its CTA stops; the transfer's
+ * destination is then incomplete, and the next replay of the same graph starts from zeroed
+ * flags.  Synchronises the device first.  Errors: EINVAL, ECUDA. */
+MPT_API mpt_status mpt_ctx_set_wait_limit(mpt_ctx_t ctx, uint64_t ns);
+
 /* ---- planning (Sec. 4.3 horizontal + vertical split; Algorithm 1) ----------------- */
 
 /* Build the chunk plan for an `nbytes` message in direction `dir` over `npaths` paths.
@@ -469,8 +478,32 @@ MPT_API mpt_status mpt_batch_wait(mpt_batch_t batch, uint64_t timeout_ns);
  * global timer); waits for the batch.  out_ns has n entries. */
 MPT_API mpt_status mpt_batch_times(mpt_batch_t batch, uint64_t* out_ns);
 
+/* Wait up to timeout_ns for the whole batch while watching its per-transfer completion
+ * flags from the host, and write to out_ns[i] (n entries) the mpt_now_ns time at which
+ * transfer i's flag was first seen, minus t0_ns (0 if it was seen before t0_ns).  With t0_ns
+ * taken just before mpt_batch_submit, out_ns is each transfer's latency from submission as
+ * a host thread observes it -- the same origin and observer as mpt_copy_each, so that
+ * batched and per-transfer copies compare like for like (Sec. 5.3's windowed bandwidth: many
+ * messages in flight).  The flags are scanned in a spin loop, so resolution is a few
+ * microseconds.  Errors: EINVAL, ETIMEDOUT (still running, or the batch ended with a
+ * transfer unflagged), ECUDA. */
+MPT_API mpt_status mpt_batch_watch(mpt_batch_t batch, uint64_t t0_ns, uint64_t* out_ns, uint64_t timeout_ns);
+
 /* Release the handle and its slot. */
 MPT_API mpt_status mpt_batch_release(mpt_batch_t batch);
+
+/* The per-transfer baseline of a batch: every transfer as its own cudaMemcpyAsync, in table
+ * order, transfer i on streams[xfers[i].dir] (three entries: D2D, H2D, D2H; entries may
+ * repeat, NULL is the legacy default stream).  Giving each direction its own stream keeps
+ * device-to-device copies from queueing behind copies limited by the host link (Sec. 4.5,
+ * contention avoidance).  out_ns NULL: asynchronous, returns once every copy is enqueued.
+ * out_ns non-NULL (n entries): after enqueueing, waits up to timeout_ns and writes each
+ * transfer's completion time as seen by this host thread (its completion event polled in a
+ * spin loop), in nanoseconds after the call was entered.  The copies use cudaMemcpyDefault,
+ * so pointer kinds are not checked beyond NULL and the direction code.  Errors: EINVAL,
+ * ETIMEDOUT, ECUDA. */
+MPT_API mpt_status mpt_copy_each(mpt_ctx_t ctx, const mpt_xfer* xfers, size_t n, void* const* streams, uint64_t* out_ns,
+                                 uint64_t timeout_ns);
 
 /* ---- serving loop (continuous batching over the batch ring) ------------------------ */
 

@@ -113,6 +113,11 @@ def mpt_ctx_status(ctx: int) -> tuple[int, int]:
     return st, site.value
 
 
+def mpt_ctx_set_wait_limit(ctx: int, ns: int) -> None:
+    """Wait limit of the staged host-to-device path's device-side flag waits (0 = default)."""
+    _check(lib().mpt_ctx_set_wait_limit(ctx, ns), "mpt_ctx_set_wait_limit")
+
+
 def mpt_plan(ctx, nbytes: int, direction: int, paths, align: int = 16, layout: int = MPT_LAYOUT_CONTIG) -> int:
     h = C.c_void_p()
     if paths is None:
@@ -305,6 +310,24 @@ def mpt_batch_times(batch: int, n: int) -> list[int]:
     out = (C.c_uint64 * n)()
     _check(lib().mpt_batch_times(batch, out), "mpt_batch_times")
     return list(out)
+
+
+def mpt_batch_watch(batch: int, t0_ns: int, n: int, timeout_ns: int = 60 * 10 ** 9) -> list[int]:
+    """Per-transfer completion times (ns after t0_ns) as first seen from the host; waits."""
+    out = (C.c_uint64 * max(1, n))()
+    _check(lib().mpt_batch_watch(batch, t0_ns, out, timeout_ns), "mpt_batch_watch")
+    return list(out[:n])
+
+
+def mpt_copy_each(ctx: int, xfers, streams, wait: bool = True, timeout_ns: int = 60 * 10 ** 9):
+    """Every transfer as its own cudaMemcpyAsync on streams[dir] (three streams: D2D, H2D,
+    D2H).  wait: block and return each completion time in ns after the call began."""
+    n = len(xfers)
+    arr = xfers if isinstance(xfers, C.Array) else make_xfers(xfers)
+    ss = (C.c_void_p * 3)(*[_stream(s) for s in streams])
+    out = (C.c_uint64 * max(1, n))() if wait else None
+    _check(lib().mpt_copy_each(ctx, arr, n, ss, out, timeout_ns), "mpt_copy_each")
+    return list(out[:n]) if wait else None
 
 
 def mpt_batch_release(batch: int) -> None:

@@ -106,6 +106,7 @@ SIGNATURES = {
     "mpt_ctx_destroy": (C.c_int, [H]),
     "mpt_ctx_info": (C.c_int, [H, P(mpt_device_info)]),
     "mpt_ctx_status": (C.c_int, [H, P(C.c_uint32)]),
+    "mpt_ctx_set_wait_limit": (C.c_int, [H, C.c_uint64]),
     "mpt_trace_lanes": (C.c_int, [H, C.c_uint32]),
     "mpt_lane_times": (C.c_int, [H, P(C.c_float), C.c_uint32, P(C.c_uint32)]),
     "mpt_plan": (C.c_int, [H, C.c_uint64, C.c_uint32, P(mpt_path_spec), C.c_uint32, C.c_uint32, C.c_uint32,
@@ -142,7 +143,9 @@ SIGNATURES = {
     "mpt_batch_poll": (C.c_int, [H, P(C.c_size_t), P(C.c_uint8)]),
     "mpt_batch_wait": (C.c_int, [H, C.c_uint64]),
     "mpt_batch_times": (C.c_int, [H, P(C.c_uint64)]),
+    "mpt_batch_watch": (C.c_int, [H, C.c_uint64, P(C.c_uint64), C.c_uint64]),
     "mpt_batch_release": (C.c_int, [H]),
+    "mpt_copy_each": (C.c_int, [H, P(mpt_xfer), C.c_size_t, P(C.c_void_p), P(C.c_uint64), C.c_uint64]),
     "mpt_now_ns": (C.c_uint64, []),
     "mpt_serve_start": (C.c_int, [H, P(mpt_serve_config), P(H)]),
     "mpt_serve_submit": (C.c_int, [H, P(mpt_xfer), C.c_uint64, C.c_uint64]),

@@ -27,26 +27,50 @@ def _nvcc() -> str:
     raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libmpt.so")
 
 
+CFLAGS = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-fvisibility=hidden"]
+HEADERS = ["kernels.cuh", "batch_kernels.cuh", "copy_device.cuh", "internal.h", "ctx.h", "host_pool.h"]
+STAMP = OUT + ".sha256"
+
+
 def _compile(nvcc: str, src: str) -> str:
     obj = os.path.join(OBJDIR, os.path.basename(src) + ".o")
-    cmd = [nvcc, ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-fvisibility=hidden", "-I", INCLUDE,
-           "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
+    cmd = [nvcc] + CFLAGS + ["-I", INCLUDE, "-I", CSRC, "-c", os.path.join(CSRC, src), "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed on {src}:\n{r.stdout}\n{r.stderr}")
     return obj
 
 
+def source_hash(nvcc: str | None = None) -> str:
+    """sha256 over every source and header the library is built from (names and bytes), the
+    compile flags, the machine type and the nvcc in use: the key under which a built
+    libmpt.so may be reused."""
+    import hashlib
+    import platform
+    h = hashlib.sha256()
+    files = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(INCLUDE, "mpt.h")]
+    for f in files:
+        h.update(os.path.relpath(f, ROOT).encode() + b"\0")
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    h.update(" ".join(CFLAGS).encode())
+    h.update(platform.machine().encode())
+    h.update((nvcc or "").encode())
+    return h.hexdigest()
+
+
 def build(force: bool = False) -> str:
-    """Compile every source and link libmpt.so; returns its path."""
-    srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, h) for h in ("kernels.cuh", "batch_kernels.cuh", "copy_device.cuh", "internal.h", "ctx.h", "host_pool.h")] + [os.path.join(INCLUDE, "mpt.h")]
-    if not force and os.path.exists(OUT):
-        newest = max(os.path.getmtime(d) for d in deps)
-        if os.path.getmtime(OUT) >= newest:
-            return OUT
-    os.makedirs(OBJDIR, exist_ok=True)
+    """Compile every source and link libmpt.so; returns its path.  An existing libmpt.so is
+    reused only when the stamp written beside it at link time holds the current
+    source_hash(); anything else (edited sources or flags, another machine type, a library
+    copied in from elsewhere without its stamp) rebuilds."""
     nvcc = _nvcc()
+    key = source_hash(nvcc)
+    if not force and os.path.exists(OUT) and os.path.exists(STAMP):
+        with open(STAMP) as f:
+            if f.read().strip() == key:
+                return OUT
+    os.makedirs(OBJDIR, exist_ok=True)
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(lambda s: _compile(nvcc, s), SOURCES))
     tmp = OUT + ".tmp"
@@ -54,7 +78,12 @@ def build(force: bool = False) -> str:
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+    if os.path.exists(STAMP):
+        os.unlink(STAMP)
     os.replace(tmp, OUT)
+    with open(STAMP + ".tmp", "w") as f:
+        f.write(key + "\n")
+    os.replace(STAMP + ".tmp", STAMP)
     return OUT
 
 

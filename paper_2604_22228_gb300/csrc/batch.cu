@@ -298,6 +298,8 @@ mpt_status batch_setup(mpt_ctx_t c) {
 void batch_teardown(mpt_ctx_t c) {
   for (auto& s : c->slots) slot_free(s);
   c->slots.clear();
+  for (cudaEvent_t e : c->each_ev) cudaEventDestroy(e);
+  c->each_ev.clear();
 }
 
 mpt_status batch_check_xfer(mpt_ctx_t c, const mpt_xfer& x, int* src_kind, int* dst_kind) {
@@ -627,6 +629,85 @@ mpt_status mpt_batch_times(mpt_batch_t b, uint64_t* out_ns) {
   CUDA_TRY(cudaMemcpy(&start_inv, s.args.start_inv, sizeof start_inv, cudaMemcpyDeviceToHost));
   const unsigned long long start = ~start_inv;
   for (size_t i = 0; i < b->n; ++i) out_ns[i] = t[i] >= start ? t[i] - start : 0;
+  return MPT_OK;
+}
+
+mpt_status mpt_batch_watch(mpt_batch_t b, uint64_t t0_ns, uint64_t* out_ns, uint64_t timeout_ns) {
+  if (!b || !out_ns) return fail(MPT_EINVAL, "mpt_batch_watch: NULL argument");
+  const BatchSlot& s = b->ctx->slots[b->slot];
+  volatile const uint32_t* f = s.h_flags;
+  const size_t n = b->n;
+  std::vector<uint8_t> seen(n, 0);
+  size_t left = n, lo = 0;
+  const uint64_t start = host_ns();
+  bool finished = false;  // the batch's completion event has fired: one last scan decides
+  while (left) {
+    const uint64_t now = host_ns();
+    for (size_t i = lo; i < n; ++i) {
+      if (!seen[i] && f[i] == b->epoch) {
+        seen[i] = 1;
+        out_ns[i] = now >= t0_ns ? now - t0_ns : 0;
+        --left;
+      }
+    }
+    while (lo < n && seen[lo]) ++lo;
+    if (!left) break;
+    if (finished) return fail(MPT_ETIMEDOUT, "mpt_batch_watch: the batch ended with %zu transfers unflagged", left);
+    const cudaError_t e = cudaEventQuery(s.done_ev);
+    if (e == cudaSuccess) {
+      finished = true;
+      continue;
+    }
+    if (e != cudaErrorNotReady) return fail(MPT_ECUDA, "mpt_batch_watch: %s", cudaGetErrorString(e));
+    if (now - start >= timeout_ns) return fail(MPT_ETIMEDOUT, "mpt_batch_watch: batch still running");
+  }
+  return MPT_OK;
+}
+
+mpt_status mpt_copy_each(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* const* streams, uint64_t* out_ns,
+                         uint64_t timeout_ns) {
+  const uint64_t t0 = host_ns();
+  if (!c || (n && (!xfers || !streams))) return fail(MPT_EINVAL, "mpt_copy_each: NULL argument");
+  for (size_t i = 0; i < n; ++i) {
+    const mpt_xfer& x = xfers[i];
+    if (x.dir > MPT_D2H) return fail(MPT_EINVAL, "mpt_copy_each: transfer %zu has direction %u", i, x.dir);
+    if (x.bytes && (!x.src || !x.dst)) return fail(MPT_EINVAL, "mpt_copy_each: transfer %zu has a NULL pointer", i);
+  }
+  CUDA_TRY(cudaSetDevice(c->device));
+  if (out_ns) {
+    while (c->each_ev.size() < n) {
+      cudaEvent_t e;
+      CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      c->each_ev.push_back(e);
+    }
+  }
+  std::vector<size_t> order[3];  // per direction, transfer indices in issue order
+  for (size_t i = 0; i < n; ++i) {
+    const mpt_xfer& x = xfers[i];
+    cudaStream_t s = static_cast<cudaStream_t>(streams[x.dir]);
+    if (x.bytes) CUDA_TRY(cudaMemcpyAsync(x.dst, x.src, x.bytes, cudaMemcpyDefault, s));
+    if (out_ns) {
+      CUDA_TRY(cudaEventRecord(c->each_ev[i], s));
+      order[x.dir].push_back(i);
+    }
+  }
+  if (!out_ns) return MPT_OK;
+  // one stream's copies finish in issue order: poll only the oldest unfinished one of each
+  size_t head[3] = {0, 0, 0}, left = n;
+  while (left) {
+    for (int d = 0; d < 3; ++d) {
+      while (head[d] < order[d].size()) {
+        const size_t i = order[d][head[d]];
+        const cudaError_t e = cudaEventQuery(c->each_ev[i]);
+        if (e == cudaErrorNotReady) break;
+        if (e != cudaSuccess) return fail(MPT_ECUDA, "mpt_copy_each: %s", cudaGetErrorString(e));
+        out_ns[i] = host_ns() - t0;
+        ++head[d];
+        --left;
+      }
+    }
+    if (left && host_ns() - t0 >= timeout_ns) return fail(MPT_ETIMEDOUT, "mpt_copy_each: copies still running");
+  }
   return MPT_OK;
 }
 

@@ -132,6 +132,7 @@ struct mpt_ctx_s {
   bool pageable = false;              // the GPU reaches pageable host memory (coherent host)
   uint32_t* d_status = nullptr;       // device status word
   unsigned long long* d_hash = nullptr;
+  uint64_t* d_wait_ns = nullptr;      // device word: wait limit of the staged consumer's flag waits
   mpt::EagerLane lane[MPT_MAX_PATHS];
   cudaEvent_t fork = nullptr;
   std::unordered_map<mpt::GraphKey, mpt_graph_s*, mpt::GraphKeyHash> cache;
@@ -165,4 +166,5 @@ struct mpt_ctx_s {
   uint64_t batch_dma_min = 0;                         // smallest entry a DMA lane takes
   bool batch_dma_set = false;                         // configured (else environment defaults)
   bool batch_timing = false;                          // bracket each batch replay with timing events
+  std::vector<cudaEvent_t> each_ev;                   // completion events of mpt_copy_each (grown on demand)
 };

@@ -59,9 +59,9 @@ __global__ void k_zc_copy_any(CopyArgs a);
 
 // ---- flag-chained stage consumer (host-to-device staged path) ----------------------
 // The copy engine fills stage chunk k and a memset node then sets ready[k] = 1.  The
-// consumer kernel waits (bounded) for ready[k], copies the chunk from the stage to its
-// destination, and the CTA finishing the chunk's last tile clears ready[k] and done[k],
-// so a replay of the graph finds every flag at 0 again.
+// consumer kernel waits (bounded) for ready[k] and copies the chunk from the stage to its
+// destination, counting the chunk's tiles in done[k].  A memset node at the head of every
+// replay zeroes ready[] and done[] before any other node of the path runs.
 struct StageChunk {
   uint64_t dst_off;    // destination offset of the chunk
   uint64_t stage_off;  // its offset in the stage buffer
@@ -77,7 +77,8 @@ struct StageArgs {
   uint32_t nchunks;
   uint32_t tiles_per_chunk;  // ceil(max chunk bytes / tile)
   uint32_t* status;
-  uint64_t timeout_ns;
+  uint64_t timeout_ns;       // wait limit per chunk flag when wait_ns is null
+  const uint64_t* wait_ns;   // the context's wait-limit word (device memory), read at each wait
 };
 
 __global__ void k_stage_consume(StageArgs a);
@@ -91,5 +92,6 @@ constexpr uint32_t kSiteStageFlag = 2;
 constexpr uint32_t kSiteBatch = 3;
 
 constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;  // 2 s
+constexpr uint64_t kMaxWaitLimitNs = 10000000000ull;   // 10 s
 
 }  // namespace mpt

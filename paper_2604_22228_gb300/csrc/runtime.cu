@@ -373,7 +373,10 @@ mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const voi
           }
         } else if (plan->dir == MPT_H2D) {
           // Copy engine fills a device stage chunk by chunk; after each chunk a memset node
-          // raises its ready flag; one consumer kernel moves chunks out as flags rise.
+          // raises its ready flag; one consumer kernel moves chunks out as flags rise.  A
+          // memset node at the head zeroes every flag and tile counter on each replay, and
+          // all other nodes of the path run after it, so no flag left raised by an earlier
+          // replay (one whose consumer gave up waiting) can be taken for this replay's.
           const uint32_t nch = hi - lo;
           std::vector<StageChunk> table(nch);
           uint64_t stage_bytes = 0;
@@ -397,10 +400,22 @@ mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const voi
           info.staging_bytes += stage_bytes;
           uint32_t* ready = static_cast<uint32_t*>(ctrl);
           uint8_t* ds8 = static_cast<uint8_t*>(dstage);
+          cudaGraphNode_t head;
+          {
+            cudaMemsetParams zp{};
+            zp.dst = ctrl;
+            zp.value = 0;
+            zp.elementSize = 4;
+            zp.width = 2 * nch;  // ready[nch] then done[nch]
+            zp.height = 1;
+            zp.pitch = 0;
+            CUDA_TRY(cudaGraphAddMemsetNode(&head, g->graph, nullptr, 0, &zp));
+            info.memset_nodes++;
+          }
           for (uint32_t k = 0; k < nch; ++k) {
             const mpt_chunk& ch = plan->chunks[lo + k];
             cudaGraphNode_t h1, m;
-            CUDA_TRY(cudaGraphAddMemcpyNode1D(&h1, g->graph, nullptr, 0, ds8 + table[k].stage_off, s8 + ch.offset,
+            CUDA_TRY(cudaGraphAddMemcpyNode1D(&h1, g->graph, &head, 1, ds8 + table[k].stage_off, s8 + ch.offset,
                                               ch.bytes, cudaMemcpyHostToDevice));
             cudaMemsetParams mp{};
             mp.dst = ready + k;
@@ -424,6 +439,7 @@ mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const voi
           sa.tiles_per_chunk = (uint32_t)((cb + tile - 1) / tile);
           sa.status = c->d_status;
           sa.timeout_ns = kDefaultTimeoutNs;
+          sa.wait_ns = c->d_wait_ns;
           void* params[] = {&sa};
           cudaKernelNodeParams kp{};
           kp.func = reinterpret_cast<void*>(&k_stage_consume);
@@ -432,7 +448,7 @@ mpt_status build_graph(mpt_ctx_t c, const mpt_plan_s* plan, void* dst, const voi
           kp.blockDim = dim3(kVecThreads);
           kp.kernelParams = params;
           cudaGraphNode_t kn;
-          CUDA_TRY(cudaGraphAddKernelNode(&kn, g->graph, nullptr, 0, &kp));
+          CUDA_TRY(cudaGraphAddKernelNode(&kn, g->graph, &head, 1, &kp));
           info.kernel_nodes++;
         } else {
           // Device-to-host through a two-slot device stage: SM copy into the slot, then a
@@ -844,7 +860,13 @@ mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out) {
   if (cudaMalloc(&words, 256) != cudaSuccess) return bail(fail(MPT_ENOMEM, "mpt_ctx_create: status word"));
   c->d_status = static_cast<uint32_t*>(words);
   c->d_hash = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(words) + 128);
+  c->d_wait_ns = reinterpret_cast<uint64_t*>(static_cast<uint8_t*>(words) + 64);
   if (cudaMemset(words, 0, 256) != cudaSuccess) return bail(fail(MPT_ECUDA, "mpt_ctx_create: memset"));
+  {
+    const uint64_t lim = kDefaultTimeoutNs;
+    if (cudaMemcpy(c->d_wait_ns, &lim, sizeof lim, cudaMemcpyHostToDevice) != cudaSuccess)
+      return bail(fail(MPT_ECUDA, "mpt_ctx_create: wait limit"));
+  }
   for (uint32_t p = 0; p < MPT_MAX_PATHS; ++p) {
     EagerLane& L = c->lane[p];
     for (int i = 0; i < 2; ++i)
@@ -973,6 +995,18 @@ mpt_status mpt_lane_times(mpt_ctx_t c, float* out_ms, uint32_t cap, uint32_t* n)
     k = p + 1;
   }
   *n = k;
+  return MPT_OK;
+}
+
+mpt_status mpt_ctx_set_wait_limit(mpt_ctx_t c, uint64_t ns) {
+  if (!c) return fail(MPT_EINVAL, "mpt_ctx_set_wait_limit: NULL context");
+  if (ns > kMaxWaitLimitNs)
+    return fail(MPT_EINVAL, "mpt_ctx_set_wait_limit: %llu ns exceeds the maximum of %llu ns", (unsigned long long)ns,
+                (unsigned long long)kMaxWaitLimitNs);
+  const uint64_t lim = ns ? ns : kDefaultTimeoutNs;
+  CUDA_TRY(cudaSetDevice(c->device));
+  CUDA_TRY(cudaDeviceSynchronize());
+  CUDA_TRY(cudaMemcpy(c->d_wait_ns, &lim, sizeof lim, cudaMemcpyHostToDevice));
   return MPT_OK;
 }
 

@@ -3,8 +3,12 @@
 // host buffer, and a memset node after each raises that chunk's ready flag.  This one
 // consumer kernel, launched beside them in the same graph, walks the chunks' 64 KiB tiles,
 // waits (bounded) for each chunk's flag, and moves the tile from the stage to its
-// destination.  The CTA that finishes a chunk's last tile puts the chunk's flag and tile
-// counter back to 0, so the next replay of the graph starts from resting flags.
+// destination.
+//
+// Flags and tile counters are put back to 0 by a memset node at the head of every replay,
+// ordered before the copy-engine nodes and before this kernel.  A replay therefore never
+// sees a flag raised by an earlier one, even when an earlier replay's wait gave up part way
+// (its CTAs return at once, leaving raised flags and partial counts behind).
 //
 // The stage is written by copy engines while this kernel runs, so its bytes are read with
 // coherent loads after an acquire of the flag, never through the read-only (.nc) path.
@@ -22,7 +26,8 @@ __global__ void __launch_bounds__(kVecThreads) k_stage_consume(StageArgs a) {
     const uint32_t k = t / a.tiles_per_chunk;
     const uint32_t lt = t - k * a.tiles_per_chunk;
     if (tid == 0) {
-      const uint64_t deadline = global_ns() + a.timeout_ns;
+      const uint64_t limit = a.wait_ns ? *(volatile const uint64_t*)a.wait_ns : a.timeout_ns;
+      const uint64_t deadline = global_ns() + limit;
       int seen = 0;
       while (true) {
         uint32_t v;
@@ -49,11 +54,7 @@ __global__ void __launch_bounds__(kVecThreads) k_stage_consume(StageArgs a) {
     __syncthreads();
     if (tid == 0) {
       __threadfence();
-      const uint32_t prev = atomicAdd(a.done + k, 1u);
-      if (prev == a.tiles_per_chunk - 1) {
-        a.done[k] = 0;
-        asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(a.ready + k), "r"(0u) : "memory");
-      }
+      atomicAdd(a.done + k, 1u);  // tiles of chunk k moved (read back by tests and tools)
     }
   }
 }

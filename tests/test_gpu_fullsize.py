@@ -1,8 +1,10 @@
 """Parity at the benchmark's largest sizes, in the launch configuration bench.py times:
 the 1 GiB device-to-device message through the tuned handle (graph or direct issue), and
-2 GiB host-to-device and device-to-host through the tuned plans.  Whole-buffer digests must
-match and sampled windows must equal the oracle's bytes (the payload stream, since a
-transfer's result is its source)."""
+2 GiB host-to-device and device-to-host through the tuned plans.  Every destination byte is
+compared with the oracle's (the payload stream regenerated on the host, since a transfer's
+result is its source) in 64 MiB pieces; the GPU digest is a second check.  Messages above
+4 GiB are checked by digest against the oracle's digest of the same bytes, plus windows at
+the 4 GiB boundary."""
 import numpy as np
 import pytest
 
@@ -26,6 +28,15 @@ def _handle(ctx, n, direction, dst, src):
     plan = mpt.mpt_plan(ctx, n, direction, None, 16,
                         mpt.MPT_PLAN_EAGER if mode == mpt.MPT_PREPARE_EAGER else mpt.MPT_LAYOUT_CONTIG)
     return plan, mpt.mpt_prepare(ctx, plan, dst, src, mode)
+
+
+def _check_all(got_at, kind, seed, n, piece=64 * MiB):
+    """Compare the whole destination with the oracle copy of the payload, piece by piece."""
+    for off in range(0, n, piece):
+        w = min(piece, n - off)
+        want = T.copy(payload.fill_window(kind, seed, off, w))
+        got = got_at(off, w)
+        assert np.array_equal(got, want), f"first mismatch at {off + int(np.argmax(got != want))}"
 
 
 def _check_windows(got_at, kind, seed, n, rng, count=24, width=4096):
@@ -55,10 +66,9 @@ def test_d2d_1gib_tuned(ctx):
     for _ in range(2):
         mpt.mpt_launch(h, torch.cuda.current_stream())
     torch.cuda.synchronize()
-    assert mpt.mpt_hash_device(ctx, dst.data_ptr(), n) == mpt.mpt_hash_device(ctx, src.data_ptr(), n)
+    _check_all(lambda o, w: dst[o:o + w].cpu().numpy(), "f32", payload.SEED_D2D_SWEEP, n)
     assert int(dst[n:].sum()) == 0  # nothing written past the message
-    _check_windows(lambda o, w: dst[o:o + w].cpu().numpy(), "f32", payload.SEED_D2D_SWEEP, n,
-                   np.random.default_rng(1))
+    assert mpt.mpt_hash_device(ctx, dst.data_ptr(), n) == mpt.mpt_hash_device(ctx, src.data_ptr(), n)
     mpt.mpt_graph_release(h)
     mpt.mpt_plan_destroy(plan)
 
@@ -79,10 +89,10 @@ def test_host_2gib_tuned(ctx, direction):
     plan, h = _handle(ctx, n, direction, dst.data_ptr(), src.data_ptr())
     mpt.mpt_launch(h, torch.cuda.current_stream())
     torch.cuda.synchronize()
-    assert mpt.mpt_hash_device(ctx, dst.data_ptr(), n) == mpt.mpt_hash_device(ctx, src.data_ptr(), n)
     view = (lambda o, w: dst[o:o + w].cpu().numpy()) if direction == mpt.MPT_H2D else \
         (lambda o, w: dst.numpy()[o:o + w])
-    _check_windows(view, "u32", payload.SEED_HOST_SWEEP, n, np.random.default_rng(2))
+    _check_all(view, "u32", payload.SEED_HOST_SWEEP, n)
+    assert mpt.mpt_hash_device(ctx, dst.data_ptr(), n) == mpt.mpt_hash_device(ctx, src.data_ptr(), n)
     mpt.mpt_graph_release(h)
     mpt.mpt_plan_destroy(plan)
 
@@ -96,28 +106,46 @@ def test_digest_of_full_message_matches_oracle(ctx):
     assert mpt.mpt_hash_device(ctx, t.data_ptr(), n) == T.hash64(data)
 
 
-def _tiled_source(n, seed):
+BEYOND_N = 4 * GiB + 4096 + 13
+BEYOND_SEED = payload.SEED_D2D_SWEEP + 5
+BEYOND_PERIOD = GiB - 28672
+
+
+@pytest.fixture(scope="module")
+def beyond_oracle():
+    """The tiled message above 4 GiB built on the host, and the oracle's digest of it."""
+    base_np = payload.fill("u32", BEYOND_SEED, BEYOND_PERIOD)
+    host = np.empty(BEYOND_N, dtype=np.uint8)
+    for o in range(0, BEYOND_N, BEYOND_PERIOD):
+        m = min(BEYOND_PERIOD, BEYOND_N - o)
+        host[o:o + m] = base_np[:m]
+    digest = T.hash64(host)
+    del host
+    return base_np, digest
+
+
+def _tiled_source(n, base_np, period):
     """n bytes on the device: the seeded u32 payload repeated with a period that does not
     divide 2^32, so a 64-bit offset truncated to 32 bits reads different bytes."""
     import torch
-    period = GiB - 28672
-    base_np = payload.fill("u32", seed, period)
     base = torch.from_numpy(base_np).cuda()
     src = torch.empty(n, dtype=torch.uint8, device="cuda")
     for o in range(0, n, period):
         m = min(period, n - o)
         src[o:o + m].copy_(base[:m])
-    return src, base_np, period
+    return src
 
 
 @pytest.mark.parametrize("case", ["sm_eager", "sm_graph", "sm8k_graph", "bulk_graph", "ce_sm_graph", "batch"])
-def test_d2d_beyond_4gib(ctx, case):
+def test_d2d_beyond_4gib(ctx, case, beyond_oracle):
     """A message above 4 GiB: 64-bit offsets in every path (kernel tile offsets, copy-engine
-    chunk offsets, batch descriptors).  Whole-buffer digest, untouched tail, and windows at
-    the 4 GiB boundary against the oracle's bytes."""
+    chunk offsets, batch descriptors).  Whole-buffer digest against the oracle's digest of
+    the same bytes, untouched tail, and windows at the 4 GiB boundary against the oracle's
+    bytes."""
     import torch
-    n = 4 * GiB + 4096 + 13
-    src, base_np, period = _tiled_source(n, payload.SEED_D2D_SWEEP + 5)
+    n, period = BEYOND_N, BEYOND_PERIOD
+    base_np, want_digest = beyond_oracle
+    src = _tiled_source(n, base_np, period)
     dst = torch.zeros(n + 4096, dtype=torch.uint8, device="cuda")
     s = torch.cuda.current_stream()
     if case == "batch":
@@ -142,7 +170,7 @@ def test_d2d_beyond_4gib(ctx, case):
         mpt.mpt_graph_release(h)
         mpt.mpt_plan_destroy(plan)
     torch.cuda.synchronize()
-    assert mpt.mpt_hash_device(ctx, dst.data_ptr(), n) == mpt.mpt_hash_device(ctx, src.data_ptr(), n)
+    assert mpt.mpt_hash_device(ctx, dst.data_ptr(), n) == want_digest
     assert int(dst[n:].sum()) == 0
     for off in (0, (1 << 32) - 2048, 1 << 32, n - 4096):
         p = off % period
