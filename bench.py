@@ -1769,7 +1769,10 @@ def run_kernel_only_stage_h2d(args, mpt, torch):
 
 
 def run_kernel_only(args):
-    """One kernel alone on one message (for profiling): K launches timed with CUDA events."""
+    """One kernel alone on one message (for profiling): K launches timed with CUDA events on
+    seeded random bytes, checked by comparing the destination's digest with the source's.
+    With --kernel-only bulk and --bulk-config -1, every bulk-kernel configuration in turn (one
+    JSON line each)."""
     import torch
 
     import paper_2604_22228_gb300 as mpt
@@ -1780,7 +1783,6 @@ def run_kernel_only(args):
         return run_kernel_only_jacobi(args, mpt, torch)
     if args.kernel_only == "stage_h2d":
         return run_kernel_only_stage_h2d(args, mpt, torch)
-    ctx = mpt.mpt_ctx_create(0)
     host = args.kernel_only in ("zc", "zc_d2h")
     if args.kernel_only == "zc":  # host -> device
         a = torch.empty(n, dtype=torch.uint8).pin_memory()
@@ -1790,26 +1792,40 @@ def run_kernel_only(args):
         b = torch.empty(n, dtype=torch.uint8).pin_memory()
     else:
         b = torch.empty(n, dtype=torch.uint8, device="cuda")
-    a.fill_(7)
+    g = torch.Generator(device="cuda").manual_seed(SEED)
+    a.copy_(torch.randint(0, 256, (n,), dtype=torch.uint8, device="cuda", generator=g))
     variant = {"bulk": mpt.MPT_SM_BULK, "vec8k": mpt.MPT_SM_TILE8K}.get(args.kernel_only, mpt.MPT_SM_VEC128)
-    s = torch.cuda.Stream()
-    for _ in range(args.warmup):
-        mpt.mpt_sm_copy(ctx, b.data_ptr(), a.data_ptr(), n, variant, args.kernel_ctas, s)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    for _ in range(args.steps):
-        mpt.mpt_sm_copy(ctx, b.data_ptr(), a.data_ptr(), n, variant, args.kernel_ctas, s)
-    e1.record(s)
-    e1.synchronize()
-    ms = e0.elapsed_time(e1) / args.steps
-    ok = bool(torch.equal(a[:1 << 20].cpu(), b[:1 << 20].cpu()))
-    st, _ = mpt.mpt_ctx_status(ctx)
-    mpt.mpt_ctx_destroy(ctx)
-    moved = n if host else 2 * n
-    print(json.dumps({"kernel": args.kernel_only, "bytes": n, "ctas": args.kernel_ctas, "launches": args.steps,
-                      "ms_per_launch": round(ms, 5), "gbs": round(moved / (ms / 1e3) / 1e9, 1),
-                      "ok": ok and st == 0}), flush=True)
-    return 0 if ok and st == 0 else 1
+    configs = [None]
+    if args.kernel_only == "bulk" and args.bulk_config is not None:
+        configs = list(range(mpt.MPT_BULK_CONFIGS)) if args.bulk_config < 0 else [args.bulk_config]
+    rc = 0
+    for cfg in configs:
+        if cfg is not None:
+            os.environ["MPT_BULK_CONFIG"] = str(cfg)
+        ctx = mpt.mpt_ctx_create(0)
+        s = torch.cuda.Stream()
+        b.zero_()
+        torch.cuda.synchronize()
+        for _ in range(args.warmup):
+            mpt.mpt_sm_copy(ctx, b.data_ptr(), a.data_ptr(), n, variant, args.kernel_ctas, s)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(args.steps):
+            mpt.mpt_sm_copy(ctx, b.data_ptr(), a.data_ptr(), n, variant, args.kernel_ctas, s)
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        ok = mpt.mpt_hash_device(ctx, b.data_ptr(), n) == mpt.mpt_hash_device(ctx, a.data_ptr(), n)
+        st, _ = mpt.mpt_ctx_status(ctx)
+        mpt.mpt_ctx_destroy(ctx)
+        moved = n if host else 2 * n
+        line = {"kernel": args.kernel_only, "bytes": n, "ctas": args.kernel_ctas, "launches": args.steps,
+                "ms_per_launch": round(ms, 5), "gbs": round(moved / (ms / 1e3) / 1e9, 1), "ok": ok and st == 0}
+        if cfg is not None:
+            line["bulk_config"] = cfg
+        print(json.dumps(line), flush=True)
+        rc |= 0 if ok and st == 0 else 1
+    return rc
 
 
 def main(argv=None):
@@ -1855,6 +1871,8 @@ def main(argv=None):
                     help="time one copy kernel alone on --kernel-bytes (profiling)")
     ap.add_argument("--kernel-bytes", type=int, default=256 * MiB)
     ap.add_argument("--kernel-ctas", type=int, default=0)
+    ap.add_argument("--bulk-config", type=int, default=None,
+                    help="bulk kernel configuration for --kernel-only bulk (-1: every configuration in turn)")
     ap.add_argument("--batch-only", choices=["mix", "d2d", "h2d"], default=None,
                     help="run one batch of the batched workload's shape alone (profiling)")
     ap.add_argument("--batch-n", type=int, default=4096)

@@ -31,6 +31,7 @@ MPT_SHARE_ONE = 65536
 MPT_MAX_PATHS = 8
 MPT_MAX_CHUNKS = 1 << 20
 MPT_NOALLOC_MAX_RANGES = 1024
+MPT_BULK_CONFIGS = 7
 
 
 class mpt_path_spec(C.Structure):

@@ -30,6 +30,12 @@ __device__ __forceinline__ void record_timeout(uint32_t* status, uint32_t site) 
   if (status) atomicCAS(status, 0u, (site << 8) | kTimedOut);
 }
 
+// A kernel refused its arguments: record (site << 8) | MPT_EINVAL the same way.
+__device__ __forceinline__ void record_invalid(uint32_t* status, uint32_t site) {
+  constexpr uint32_t kInvalid = 1;  // MPT_EINVAL
+  if (status) atomicCAS(status, 0u, (site << 8) | kInvalid);
+}
+
 // Read-only path (ld.global.nc): only for data no agent writes while the kernel runs.
 __device__ __forceinline__ uint4 ld_stream(const uint4* p) {
   uint4 v;
@@ -48,6 +54,25 @@ __device__ __forceinline__ uint4 ld_plain(const uint4* p) {
 __device__ __forceinline__ void st_plain(uint4* p, const uint4& v) {
   asm volatile("st.global.v4.u32 [%0], {%1,%2,%3,%4};" ::"l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
                : "memory");
+}
+
+// Index of the range that launch tile t belongs to (ranges are few: a linear scan).
+template <typename Args>
+__device__ __forceinline__ int find_range(const Args& a, uint32_t t) {
+  int r = 0;
+  while (r + 1 < (int)a.nranges && t >= a.tile_start[r + 1]) ++r;
+  return r;
+}
+
+// Head (bytes before the destination-aligned body) and tail (bytes after it) of a range;
+// threads 0..15 copy the head, threads 32..47 the tail (blocks of at least 48 threads).
+template <typename Range>
+__device__ __forceinline__ void copy_edges(const uint8_t* s, uint8_t* o, const Range& d, uint64_t body_bytes) {
+  const uint32_t tid = threadIdx.x;
+  if (tid < d.head) o[tid] = s[tid];
+  const uint64_t tail_start = d.head + body_bytes;
+  const uint32_t tail = (uint32_t)(d.bytes - tail_start);
+  if (tid >= 32 && tid < 32 + tail) o[tail_start + (tid - 32)] = s[tail_start + (tid - 32)];
 }
 
 // Bytes [4k + r/8, 4k + r/8 + 16) of the 32-byte little-endian concatenation w0 | w1

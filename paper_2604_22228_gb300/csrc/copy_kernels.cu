@@ -6,15 +6,12 @@
 //                  engines (Sec. 4.3's horizontal split over paths).
 //  k_sm_copy_vec8k the same loop with one vector per thread (8 KiB tiles), so that a
 //                  message of a few MiB spreads over every SM instead of a few dozen.
-//  k_sm_copy_bulk  same contract, body moved by cp.async.bulk global->shared->global
-//                  (non-multicast) through a four-stage shared-memory ring driven by one
-//                  thread per CTA and tracked by mbarriers.
 //  k_zc_copy       zero-copy kernel: the vec128 loop with plain (coherent) loads, used on
 //                  mapped page-locked host memory for host<->device transfers.
 //  k_hash          digest of a byte range (test utility).
 //
-// Every device-side wait is bounded by the global timer and records MPT_ETIMEDOUT in
-// the context's status word instead of spinning forever.
+// The bulk-copy variant of the SM copy kernel (cp.async.bulk through shared memory) is in
+// copy_bulk.cu.
 #include "kernels.cuh"
 #include "copy_device.cuh"
 
@@ -23,12 +20,6 @@
 namespace mpt {
 
 namespace {
-
-__device__ __forceinline__ int find_range(const CopyArgs& a, uint32_t t) {
-  int r = 0;
-  while (r + 1 < (int)a.nranges && t >= a.tile_start[r + 1]) ++r;
-  return r;
-}
 
 // Before waiting on the kernel ahead (programmatic dependent launch), one thread asks L2 for
 // the source bytes of the CTA's first tile.  This is only a hint to L2, the GPU's point of
@@ -53,17 +44,6 @@ __device__ __forceinline__ void prefetch_first_tile(const CopyArgs& a) {
   const uintptr_t base = reinterpret_cast<uintptr_t>(a.src + d.src_off);
   const uintptr_t p0 = (base + lo) & ~(uintptr_t)15, p1 = (base + hi + 15) & ~(uintptr_t)15;
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p0), "r"((uint32_t)(p1 - p0)) : "memory");
-}
-
-// Head (bytes before the destination-aligned body) and tail (bytes after it) of a range;
-// threads 0..15 copy the head, threads 32..47 the tail.
-__device__ __forceinline__ void copy_edges(const uint8_t* s, uint8_t* o, const RangeDesc& d,
-                                           uint64_t body_bytes) {
-  const uint32_t tid = threadIdx.x;
-  if (tid < d.head) o[tid] = s[tid];
-  const uint64_t tail_start = d.head + body_bytes;
-  const uint32_t tail = (uint32_t)(d.bytes - tail_start);
-  if (tid >= 32 && tid < 32 + tail) o[tail_start + (tid - 32)] = s[tail_start + (tid - 32)];
 }
 
 // kU 16-byte vectors per thread per tile: tiles of kVecThreads * kU * 16 bytes (64 KiB for
@@ -121,82 +101,6 @@ __device__ __forceinline__ void copy_tiles_vec(const CopyArgs& a) {
   }
 }
 
-// ---- cp.async.bulk + mbarrier helpers -----------------------------------------------
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// Wait for phase `parity` of the barrier to complete; false if the deadline passes.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t deadline) {
-  while (true) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(done)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (global_ns() > deadline) return false;
-  }
-}
-
-__device__ __forceinline__ void bulk_load(uint32_t dst_smem, const void* src, uint32_t bytes,
-                                          uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          dst_smem),
-      "l"(src), "r"(bytes), "r"(bar)
-      : "memory");
-}
-
-__device__ __forceinline__ void bulk_store(void* dst, uint32_t src_smem, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src_smem),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
-
-template <int N>
-__device__ __forceinline__ void bulk_wait_read() {
-  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
-}
-
-__device__ __forceinline__ void bulk_wait_all() {
-  asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
-}
-
-// Global addresses and length of the bulk body piece of tile t.
-__device__ __forceinline__ uint32_t bulk_piece(const CopyArgs& a, uint32_t t, const uint8_t*& gs,
-                                               uint8_t*& gd) {
-  const int r = find_range(a, t);
-  const uint32_t lt = t - a.tile_start[r];
-  const RangeDesc& d = a.r[r];
-  const uint64_t body = ((d.bytes - d.head) >> 4) << 4;
-  const uint64_t off = (uint64_t)lt * kBulkStageBytes;
-  gs = a.src + d.src_off + d.head + off;
-  gd = a.dst + d.dst_off + d.head + off;
-  if (off >= body) return 0;
-  const uint64_t n = body - off;
-  return n < kBulkStageBytes ? (uint32_t)n : kBulkStageBytes;
-}
-
 }  // namespace
 
 __global__ void __launch_bounds__(kVecThreads) k_sm_copy_vec(CopyArgs a) {
@@ -226,79 +130,6 @@ __global__ void __launch_bounds__(kVecThreads) k_zc_copy(CopyArgs a) {
 __global__ void __launch_bounds__(kVecThreads) k_zc_copy_any(CopyArgs a) {
   pdl_enter();
   copy_tiles_vec<true, true, kVecUnroll>(a);
-}
-
-__global__ void __launch_bounds__(kBulkThreads, 1) k_sm_copy_bulk(CopyArgs a) {
-  extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bar[kBulkStages];
-  const uint32_t tid = threadIdx.x;
-  pdl_enter();
-
-  // Bytes outside the 16-byte body go with plain loads by the CTA owning tile 0.
-  for (uint32_t t = blockIdx.x; t < a.ntiles; t += gridDim.x) {
-    const int r = find_range(a, t);
-    if (t != a.tile_start[r]) continue;
-    const RangeDesc d = a.r[r];
-    copy_edges(a.src + d.src_off, a.dst + d.dst_off, d, ((d.bytes - d.head) >> 4) << 4);
-  }
-
-  if (tid == 0) {
-    for (int s = 0; s < kBulkStages; ++s) mbar_init(smem_addr(&bar[s]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  __syncthreads();
-  if (tid != 0) return;
-
-  const uint32_t n_my =
-      blockIdx.x < a.ntiles ? (a.ntiles - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
-  const uint32_t base = smem_addr(smem);
-  const uint64_t deadline = global_ns() + kDefaultTimeoutNs;
-
-  auto issue_load = [&](uint32_t i) {
-    const uint32_t s = i % kBulkStages;
-    const uint32_t b = smem_addr(&bar[s]);
-    const uint8_t* gs;
-    uint8_t* gd;
-    const uint32_t n = bulk_piece(a, blockIdx.x + i * gridDim.x, gs, gd);
-    if (n) {
-      mbar_arrive_expect_tx(b, n);
-      bulk_load(base + s * kBulkStageBytes, gs, n, b);
-    } else {
-      mbar_arrive(b);
-    }
-  };
-
-  const uint32_t prologue = n_my < (uint32_t)kBulkStages ? n_my : (uint32_t)kBulkStages;
-  for (uint32_t i = 0; i < prologue; ++i) issue_load(i);
-
-  uint32_t i = 0;
-  bool failed = false;
-  for (; i < n_my; ++i) {
-    const uint32_t s = i % kBulkStages;
-    if (!mbar_wait(smem_addr(&bar[s]), (i / kBulkStages) & 1u, deadline)) {
-      failed = true;
-      break;
-    }
-    const uint8_t* gs;
-    uint8_t* gd;
-    const uint32_t n = bulk_piece(a, blockIdx.x + i * gridDim.x, gs, gd);
-    if (n) bulk_store(gd, base + s * kBulkStageBytes, n);
-    bulk_commit();
-    // Refill the stage of tile i-1 once its store has finished reading shared memory.
-    if (i >= 1 && i - 1 + kBulkStages < n_my) {
-      bulk_wait_read<1>();
-      issue_load(i - 1 + kBulkStages);
-    }
-  }
-  bulk_wait_all();
-  if (failed) {
-    record_timeout(a.status, kSiteBulkLoad);
-    // Give loads still in flight a bounded chance to land before shared memory is released.
-    const uint64_t drain = global_ns() + kDefaultTimeoutNs;
-    const uint32_t hi = (i + kBulkStages < n_my) ? i + kBulkStages : n_my;
-    for (uint32_t j = i; j < hi; ++j) mbar_wait(smem_addr(&bar[j % kBulkStages]), (j / kBulkStages) & 1u, drain);
-  }
 }
 
 namespace {
@@ -342,10 +173,12 @@ __global__ void __launch_bounds__(256) k_hash(const uint8_t* p, uint64_t n, unsi
 // ---- host side -------------------------------------------------------------------------
 
 int make_copy_args(CopyArgs& a, const void* src, void* dst, const RangeDesc* ranges, int n,
-                   int variant, uint32_t* status) {
+                   int variant, uint32_t* status, uint32_t bulk_cfg) {
   a.src = static_cast<const uint8_t*>(src);
   a.dst = static_cast<uint8_t*>(dst);
   a.status = status;
+  a.bulk_cfg = variant == 1 ? bulk_cfg : 0;
+  a.piece = variant == 1 ? bulk_config(bulk_cfg).stage_bytes : 0;
   a.nranges = 0;
   a.any_shift = 0;
   uint64_t tiles = 0;
@@ -361,8 +194,7 @@ int make_copy_args(CopyArgs& a, const void* src, void* dst, const RangeDesc* ran
     if (d.shift) a.any_shift = 1;
     const uint64_t body = ((d.bytes - d.head) >> 4) << 4;
     const uint64_t tile_vecs = variant == 3 ? (uint64_t)kVecThreads : kVecTileVecs;
-    uint64_t t = variant == 1 ? (body + kBulkStageBytes - 1) / kBulkStageBytes
-                              : ((body >> 4) + tile_vecs - 1) / tile_vecs;
+    uint64_t t = variant == 1 ? (body + a.piece - 1) / a.piece : ((body >> 4) + tile_vecs - 1) / tile_vecs;
     if (t == 0) t = 1;  // a range too short for a body still needs its edge bytes copied
     a.r[a.nranges] = d;
     tiles += t;

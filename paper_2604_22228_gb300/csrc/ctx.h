@@ -145,6 +145,7 @@ struct mpt_ctx_s {
   uint32_t traced = 0;         // lanes timed by the last such launch
   bool pdl = true;             // direct kernel issue overlaps the previous copy kernel's end
   uint32_t stage_slots = 3;    // pinned slots of the device-to-device host-staged path (MPT_STAGE_SLOTS)
+  uint32_t bulk_cfg = 0;       // configuration of the bulk-copy kernel (MPT_BULK_CONFIG)
   std::unique_ptr<mpt::HostCopyPool> host_pool;  // CPU hops of host-thread staging (made on first use)
   unsigned host_threads = 0;   // pool workers (MPT_HOST_THREADS; 0 = min(8, cores / 2) - 1)
   std::map<uint32_t, mpt::TuneEntry> tuned;  // tune_key -> choice

@@ -12,9 +12,7 @@ constexpr int kInlineRanges = 16;     // ranges carried by value in one launch
 constexpr int kVecThreads = 512;      // vec128 kernel block size
 constexpr int kVecUnroll = 8;         // 16-byte vectors in flight per thread per tile
 constexpr uint64_t kVecTileVecs = (uint64_t)kVecThreads * kVecUnroll;  // 64 KiB tiles
-constexpr int kBulkThreads = 128;     // bulk kernel block size (thread 0 drives the ring)
-constexpr int kBulkStages = 4;        // shared-memory ring depth
-constexpr uint32_t kBulkStageBytes = 48 * 1024;  // one cp.async.bulk per stage
+constexpr int kBulkThreads = 64;      // bulk kernel block: a producer warp and a consumer warp
 
 // One contiguous range to copy: src + src_off -> dst + dst_off, `bytes` long.
 // head: bytes copied singly until the destination is 16-byte aligned; shift: the source
@@ -37,15 +35,32 @@ struct CopyArgs {
   uint32_t tile_start[kInlineRanges + 1];
   RangeDesc r[kInlineRanges];
   uint32_t* status;                      // device status word (bounded waits)
+  uint32_t bulk_cfg;                     // bulk variant: index into the bulk configurations
+  uint32_t piece;                        // bulk variant: tile bytes (that configuration's stage)
 };
 
+// One configuration of the bulk-copy kernel: a ring of `stages` shared-memory stages of
+// `stage_bytes` (one cp.async.bulk load and one store per tile), stores allowed to be still
+// reading shared memory for `keep` tiles behind the newest, `ctas_per_sm` CTAs resident per
+// SM (the default grid), and the kernel instantiated for it.
+struct BulkConfig {
+  uint32_t stages;
+  uint32_t stage_bytes;
+  uint32_t keep;
+  uint32_t ctas_per_sm;
+  const void* fn;
+};
+uint32_t bulk_config_count();
+const BulkConfig& bulk_config(uint32_t i);  // i < bulk_config_count()
+constexpr uint32_t kBulkDefaultConfig = 0;
+
 // Fill `a` for up to kInlineRanges ranges with the tiling of `variant` (0 vec128,
-// 1 bulk, 2 zero-copy, 3 vec128 with 8 KiB tiles).  Returns kArgsOk, kArgsNeedVec when a bulk launch must fall
-// back to vec128 (source and destination differ modulo 16, which cp.async.bulk cannot
-// copy), or kArgsTooLarge.
+// 1 bulk in configuration bulk_cfg, 2 zero-copy, 3 vec128 with 8 KiB tiles).  Returns
+// kArgsOk, kArgsNeedVec when a bulk launch must fall back to vec128 (source and destination
+// differ modulo 16, which cp.async.bulk cannot copy), or kArgsTooLarge.
 constexpr int kArgsOk = 0, kArgsNeedVec = 1, kArgsTooLarge = 2;
 int make_copy_args(CopyArgs& a, const void* src, void* dst, const RangeDesc* ranges, int n,
-                   int variant, uint32_t* status);
+                   int variant, uint32_t* status, uint32_t bulk_cfg = kBulkDefaultConfig);
 
 // *_any variants also copy ranges whose source and destination differ modulo 16
 // (RangeDesc.shift != 0); the plain ones are leaner and need every shift to be 0.
@@ -53,7 +68,6 @@ __global__ void k_sm_copy_vec(CopyArgs a);
 __global__ void k_sm_copy_vec_any(CopyArgs a);
 __global__ void k_sm_copy_vec8k(CopyArgs a);
 __global__ void k_sm_copy_vec8k_any(CopyArgs a);
-__global__ void k_sm_copy_bulk(CopyArgs a);
 __global__ void k_zc_copy(CopyArgs a);
 __global__ void k_zc_copy_any(CopyArgs a);
 
@@ -90,6 +104,7 @@ __global__ void k_hash(const uint8_t* p, uint64_t n, unsigned long long* out);
 constexpr uint32_t kSiteBulkLoad = 1;
 constexpr uint32_t kSiteStageFlag = 2;
 constexpr uint32_t kSiteBatch = 3;
+constexpr uint32_t kSiteBulkArgs = 4;  // a bulk kernel given a tile size other than its stage
 
 constexpr uint64_t kDefaultTimeoutNs = 2000000000ull;  // 2 s
 constexpr uint64_t kMaxWaitLimitNs = 10000000000ull;   // 10 s

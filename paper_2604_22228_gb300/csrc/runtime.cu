@@ -101,11 +101,11 @@ void cache_drop(mpt_ctx_t c, mpt_graph_s* g) {
 
 // Default grids, from measurements on GB300: the vec128 kernel needs about 16 CTAs per SM
 // over a large message (four resident, grid-striding over 64 KiB tiles) to keep HBM busy;
-// the bulk ring one CTA per SM, two waves; the zero-copy kernel saturates the host link
-// with one CTA per SM.
+// the bulk kernel runs one wave, its configuration's resident CTAs on every SM; the
+// zero-copy kernel saturates the host link with one CTA per SM.
 uint32_t default_ctas(mpt_ctx_t c, uint32_t kind, uint32_t variant) {
   if (kind == MPT_PATH_ZC) return (uint32_t)c->sms;
-  return variant == MPT_SM_BULK ? 2u * (uint32_t)c->sms : 16u * (uint32_t)c->sms;
+  return variant == MPT_SM_BULK ? bulk_config(c->bulk_cfg).ctas_per_sm * (uint32_t)c->sms : 16u * (uint32_t)c->sms;
 }
 
 // Chunks of one path merged into maximal contiguous ranges (CONTIG plans give one).
@@ -122,8 +122,8 @@ std::vector<RangeDesc> path_ranges(const mpt_plan_s* plan, uint32_t p) {
   return out;
 }
 
-void* kernel_fn(int variant, bool any_shift) {
-  if (variant == 1) return reinterpret_cast<void*>(&k_sm_copy_bulk);
+void* kernel_fn(int variant, bool any_shift, uint32_t bulk_cfg) {
+  if (variant == 1) return const_cast<void*>(bulk_config(bulk_cfg).fn);
   if (variant == 2) return any_shift ? reinterpret_cast<void*>(&k_zc_copy_any) : reinterpret_cast<void*>(&k_zc_copy);
   if (variant == 3)
     return any_shift ? reinterpret_cast<void*>(&k_sm_copy_vec8k_any) : reinterpret_cast<void*>(&k_sm_copy_vec8k);
@@ -133,11 +133,11 @@ void* kernel_fn(int variant, bool any_shift) {
 // Build CopyArgs for up to kInlineRanges ranges; the bulk variant falls back to vec128
 // when a range's source and destination differ modulo 16.
 mpt_status prepare_copy(CopyArgs& a, int& variant, const void* src, void* dst, const RangeDesc* r, int n,
-                        uint32_t* status) {
-  int rc = make_copy_args(a, src, dst, r, n, variant, status);
+                        uint32_t* status, uint32_t bulk_cfg = kBulkDefaultConfig) {
+  int rc = make_copy_args(a, src, dst, r, n, variant, status, bulk_cfg);
   if (rc == kArgsNeedVec) {
     variant = 0;
-    rc = make_copy_args(a, src, dst, r, n, variant, status);
+    rc = make_copy_args(a, src, dst, r, n, variant, status, bulk_cfg);
   }
   if (rc != kArgsOk) return fail(MPT_EINVAL, "copy of more than 2^31 tiles");
   return MPT_OK;
@@ -148,17 +148,21 @@ dim3 grid_for(const CopyArgs& a, uint32_t ctas) {
 }
 
 uint32_t block_for(int variant) { return variant == 1 ? (uint32_t)kBulkThreads : (uint32_t)kVecThreads; }
-size_t smem_for(int variant) { return variant == 1 ? (size_t)kBulkStages * kBulkStageBytes : 0; }
+size_t smem_for(int variant, const CopyArgs& a) {
+  if (variant != 1) return 0;
+  const BulkConfig& b = bulk_config(a.bulk_cfg);
+  return (size_t)b.stages * b.stage_bytes;
+}
 
 mpt_status add_copy_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndeps, cudaGraphNode_t* node,
                          int variant, const CopyArgs& a, uint32_t ctas, mpt_graph_info& info) {
   CopyArgs args = a;
   void* params[] = {&args};
   cudaKernelNodeParams kp{};
-  kp.func = kernel_fn(variant, a.any_shift != 0);
+  kp.func = kernel_fn(variant, a.any_shift != 0, a.bulk_cfg);
   kp.gridDim = grid_for(a, ctas);
   kp.blockDim = dim3(block_for(variant));
-  kp.sharedMemBytes = (unsigned)smem_for(variant);
+  kp.sharedMemBytes = (unsigned)smem_for(variant, a);
   kp.kernelParams = params;
   CUDA_TRY(cudaGraphAddKernelNode(node, g, deps, ndeps, &kp));
   info.kernel_nodes++;
@@ -169,11 +173,11 @@ mpt_status add_copy_node(cudaGraph_t g, const cudaGraphNode_t* deps, size_t ndep
 // the end of a copy kernel before it on the stream (the kernels wait for that kernel's
 // completion before touching memory).  Not used inside a stream capture.
 mpt_status launch_copy(cudaStream_t s, int variant, const CopyArgs& a, uint32_t ctas, bool pdl = false) {
-  void* kfn = kernel_fn(variant, a.any_shift != 0);
+  void* kfn = kernel_fn(variant, a.any_shift != 0, a.bulk_cfg);
   CopyArgs args = a;
   void* params[] = {&args};
   if (!pdl) {
-    CUDA_TRY(cudaLaunchKernel(kfn, grid_for(a, ctas), dim3(block_for(variant)), params, smem_for(variant), s));
+    CUDA_TRY(cudaLaunchKernel(kfn, grid_for(a, ctas), dim3(block_for(variant)), params, smem_for(variant, a), s));
     return MPT_OK;
   }
   cudaLaunchAttribute attr[1];
@@ -182,7 +186,7 @@ mpt_status launch_copy(cudaStream_t s, int variant, const CopyArgs& a, uint32_t 
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = grid_for(a, ctas);
   cfg.blockDim = dim3(block_for(variant));
-  cfg.dynamicSmemBytes = smem_for(variant);
+  cfg.dynamicSmemBytes = smem_for(variant, a);
   cfg.stream = s;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
@@ -201,7 +205,7 @@ mpt_status for_each_copy(mpt_ctx_t c, const mpt_plan_s* plan, uint32_t p, const 
     int n = (int)std::min<size_t>(kInlineRanges, ranges.size() - i);
     int variant = base_variant;
     CopyArgs a;
-    mpt_status st = prepare_copy(a, variant, src, dst, ranges.data() + i, n, c->d_status);
+    mpt_status st = prepare_copy(a, variant, src, dst, ranges.data() + i, n, c->d_status, c->bulk_cfg);
     if (st != MPT_OK) return st;
     if (a.ntiles == 0) continue;
     uint32_t ctas = spec.ctas ? spec.ctas : default_ctas(c, spec.kind, (uint32_t)variant);
@@ -882,10 +886,15 @@ mpt_status mpt_ctx_create(int device, const char* tune_file, mpt_ctx_t* out) {
   }
   if (cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess)
     return bail(fail(MPT_ECUDA, "mpt_ctx_create: events"));
-  if (cudaFuncSetAttribute(reinterpret_cast<const void*>(&k_sm_copy_bulk),
-                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)(kBulkStages * kBulkStageBytes)) != cudaSuccess)
-    return bail(fail(MPT_ECUDA, "mpt_ctx_create: bulk kernel shared memory"));
+  for (uint32_t i = 0; i < bulk_config_count(); ++i) {
+    const BulkConfig& b = bulk_config(i);
+    if (cudaFuncSetAttribute(b.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(b.stages * b.stage_bytes)) !=
+        cudaSuccess)
+      return bail(fail(MPT_ECUDA, "mpt_ctx_create: bulk kernel shared memory"));
+  }
+  c->bulk_cfg = (uint32_t)env_u64("MPT_BULK_CONFIG", kBulkDefaultConfig);
+  if (c->bulk_cfg >= bulk_config_count())
+    return bail(fail(MPT_EINVAL, "mpt_ctx_create: MPT_BULK_CONFIG must be below %u", bulk_config_count()));
   c->cache_cap = (size_t)std::max<uint64_t>(1, env_u64("MPT_GRAPH_CACHE", 64));
   c->stage_max = std::max<uint64_t>(4096, env_u64("MPT_STAGE_BYTES", 8ull << 20));
   c->rebind_enabled = env_u64("MPT_GRAPH_REBIND", 1) != 0;
@@ -1205,7 +1214,7 @@ mpt_status mpt_sm_copy(mpt_ctx_t c, void* dst, const void* src, uint64_t nbytes,
   RangeDesc r{0, 0, nbytes, 0, 0};
   int v = host ? 2 : (variant == MPT_SM_TILE8K ? 3 : (int)variant);
   CopyArgs a;
-  mpt_status st = prepare_copy(a, v, src, dst, &r, 1, c->d_status);
+  mpt_status st = prepare_copy(a, v, src, dst, &r, 1, c->d_status, c->bulk_cfg);
   if (st != MPT_OK) return st;
   const uint32_t g = ctas ? ctas : default_ctas(c, host ? MPT_PATH_ZC : MPT_PATH_SM, (uint32_t)v);
   return launch_copy(static_cast<cudaStream_t>(stream), v, a, g);
