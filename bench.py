@@ -416,6 +416,8 @@ def run_ours(args):
         if kind == "tuned":
             return mpt.mpt_plan(ctx, n, mpt.MPT_D2D, None)
         chunk = max(16, min(n, 4 * MiB)) // 16 * 16 or 16
+        if kind == "hs":  # the staged path's chunk is its stage: 8 MiB
+            chunk = max(16, min(n, 8 * MiB)) // 16 * 16 or 16
         if kind == "ce":
             specs = [(mpt.MPT_PATH_CE, 65536, chunk)]
         elif kind == "hs":  # device -> page-locked host slot -> device (Algorithm 2 StageHostCopy)

@@ -88,8 +88,8 @@ typedef enum { MPT_MODE_GRAPH = 0, MPT_MODE_EAGER = 1 } mpt_mode;
 #define MPT_SM_BULK 1u     /* cp.async.bulk global->shared->global ring per CTA */
 /* Ring configurations of the MPT_SM_BULK kernel, chosen per context by MPT_BULK_CONFIG=i
  * (0 <= i < MPT_BULK_CONFIGS, default 0) at context creation.  Stages x stage bytes, CTAs per SM:
- * 0: 4 x 48 KiB, 1; 1: 8 x 24 KiB, 1; 2: 12 x 16 KiB, 1; 3: 6 x 32 KiB, 1;
- * 4: 4 x 24 KiB, 2; 5: 6 x 16 KiB, 2; 6: 8 x 12 KiB, 2. */
+ * 0: 4 x 48 KiB, 1; 1: as 0 with an L2 evict-first policy; 2: 3 x 64 KiB, 1; 3: 2 x 48 KiB, 2;
+ * 4: as 3 with an L2 evict-first policy; 5: 3 x 32 KiB, 2; 6: 8 x 24 KiB, 1. */
 #define MPT_BULK_CONFIGS 7u
 #define MPT_SM_TILE8K 2u   /* VEC128 over 8 KiB tiles: a message of a few MiB reaches every SM
                               (BULK takes precedence when both are set) */

@@ -66,16 +66,40 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_
   return true;
 }
 
-__device__ __forceinline__ void bulk_load(uint32_t dst_smem, const void* src, uint32_t bytes, uint32_t bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-                   dst_smem),
-               "l"(src), "r"(bytes), "r"(bar)
-               : "memory");
+// kHint 1: both directions carry an L2 evict-first policy (each byte is touched once).
+template <int kHint>
+__device__ __forceinline__ void bulk_load(uint32_t dst_smem, const void* src, uint32_t bytes, uint32_t bar,
+                                          uint64_t policy) {
+  if (kHint) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
+            dst_smem),
+        "l"(src), "r"(bytes), "r"(bar), "l"(policy)
+        : "memory");
+  } else {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     dst_smem),
+                 "l"(src), "r"(bytes), "r"(bar)
+                 : "memory");
+  }
 }
 
-__device__ __forceinline__ void bulk_store(void* dst, uint32_t src_smem, uint32_t bytes) {
-  asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src_smem), "r"(bytes)
-               : "memory");
+template <int kHint>
+__device__ __forceinline__ void bulk_store(void* dst, uint32_t src_smem, uint32_t bytes, uint64_t policy) {
+  if (kHint) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(dst),
+                 "r"(src_smem), "r"(bytes), "l"(policy)
+                 : "memory");
+  } else {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(src_smem), "r"(bytes)
+                 : "memory");
+  }
+}
+
+__device__ __forceinline__ uint64_t evict_first_policy() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
 }
 
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
@@ -105,7 +129,7 @@ __device__ __forceinline__ uint32_t body_piece(const CopyArgs& a, uint32_t t, co
 
 }  // namespace
 
-template <int kStages, uint32_t kStageBytes, int kKeep, int kPerSm>
+template <int kStages, uint32_t kStageBytes, int kKeep, int kPerSm, int kHint>
 __global__ void __launch_bounds__(kBulkThreads, kPerSm) k_sm_copy_bulk(CopyArgs a) {
   static_assert(kKeep >= 1 && kKeep < kStages, "stores kept reading must leave stages for loads");
   static_assert(kStageBytes % 1024 == 0, "stages stay 1 KiB aligned in shared memory");
@@ -145,6 +169,7 @@ __global__ void __launch_bounds__(kBulkThreads, kPerSm) k_sm_copy_bulk(CopyArgs 
   const uint32_t base = smem_addr(smem);
   volatile uint32_t* abort_v = &abort_flag;
   const uint64_t deadline = global_ns() + kDefaultTimeoutNs;
+  const uint64_t policy = kHint ? evict_first_policy() : 0;
 
   if (tid == 0) {  // producer
     for (uint32_t i = 0; i < n_my; ++i) {
@@ -160,7 +185,7 @@ __global__ void __launch_bounds__(kBulkThreads, kPerSm) k_sm_copy_bulk(CopyArgs 
       const uint32_t fb = smem_addr(&full[s]);
       if (n) {
         mbar_arrive_expect_tx(fb, n);
-        bulk_load(base + s * kStageBytes, gs, n, fb);
+        bulk_load<kHint>(base + s * kStageBytes, gs, n, fb, policy);
       } else {
         mbar_arrive(fb);
       }
@@ -178,7 +203,7 @@ __global__ void __launch_bounds__(kBulkThreads, kPerSm) k_sm_copy_bulk(CopyArgs 
       const uint8_t* gs;
       uint8_t* gd;
       const uint32_t n = body_piece<kStageBytes>(a, blockIdx.x + i * gridDim.x, gs, gd);
-      if (n) bulk_store(gd, base + s * kStageBytes, n);
+      if (n) bulk_store<kHint>(gd, base + s * kStageBytes, n, policy);
       bulk_commit();
       if (i >= (uint32_t)kKeep) {
         bulk_wait_read<kKeep>();  // the store of tile i - kKeep has read its stage
@@ -200,21 +225,24 @@ __global__ void __launch_bounds__(kBulkThreads, kPerSm) k_sm_copy_bulk(CopyArgs 
 
 namespace {
 
-// The configurations compiled in, measured on GB300 (see bulk_config's users): a deep ring of
-// mid-sized stages at one CTA per SM, and rings of half the shared memory at two CTAs per SM.
-template <int S, uint32_t B, int K, int P>
+// The configurations compiled in.  On GB300 (CUDA events, back-to-back launches of one
+// message) all of them move 6.3-6.55 TB/s at 1-4 GiB; large stages do best at one CTA per SM
+// (0: 6.40-6.44 TB/s), two CTAs per SM with two stages each at 4 GiB (3, 4: 6.52-6.55 TB/s).
+// Smaller and deeper rings (16 KiB and 12 KiB stages) measured 2-5 % slower and were dropped.
+template <int S, uint32_t B, int K, int P, int H = 0>
 BulkConfig cfg() {
-  return BulkConfig{(uint32_t)S, B, (uint32_t)K, (uint32_t)P, reinterpret_cast<const void*>(&k_sm_copy_bulk<S, B, K, P>)};
+  return BulkConfig{(uint32_t)S, B, (uint32_t)K, (uint32_t)P,
+                    reinterpret_cast<const void*>(&k_sm_copy_bulk<S, B, K, P, H>)};
 }
 
 const BulkConfig kConfigs[] = {
-    cfg<4, 48 * 1024, 1, 1>(),   // 0: 192 KiB, four 48 KiB stages
-    cfg<8, 24 * 1024, 2, 1>(),   // 1: 192 KiB, eight 24 KiB stages
-    cfg<12, 16 * 1024, 3, 1>(),  // 2: 192 KiB, twelve 16 KiB stages
-    cfg<6, 32 * 1024, 2, 1>(),   // 3: 192 KiB, six 32 KiB stages
-    cfg<4, 24 * 1024, 1, 2>(),   // 4: 2 x 96 KiB, four 24 KiB stages each
-    cfg<6, 16 * 1024, 2, 2>(),   // 5: 2 x 96 KiB, six 16 KiB stages each
-    cfg<8, 12 * 1024, 2, 2>(),   // 6: 2 x 96 KiB, eight 12 KiB stages each
+    cfg<4, 48 * 1024, 1, 1>(),     // 0: 192 KiB, four 48 KiB stages (default)
+    cfg<4, 48 * 1024, 1, 1, 1>(),  // 1: as 0, L2 evict-first on loads and stores
+    cfg<3, 64 * 1024, 1, 1>(),     // 2: 192 KiB, three 64 KiB stages
+    cfg<2, 48 * 1024, 1, 2>(),     // 3: 2 x 96 KiB, two 48 KiB stages each
+    cfg<2, 48 * 1024, 1, 2, 1>(),  // 4: as 3, L2 evict-first
+    cfg<3, 32 * 1024, 1, 2>(),     // 5: 2 x 96 KiB, three 32 KiB stages each
+    cfg<8, 24 * 1024, 2, 1>(),     // 6: 192 KiB, eight 24 KiB stages, two stores reading
 };
 
 }  // namespace

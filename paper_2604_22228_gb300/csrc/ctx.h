@@ -15,6 +15,7 @@
 namespace mpt {
 
 constexpr uint32_t kMaxStageSlots = 4;
+constexpr uint32_t kLaneStreams = 4;  // streams per eager lane: copy-engine chains (two for staged hops)
 
 struct GraphKey {
   uint64_t src, dst, nbytes, dir, plan_hash;
@@ -29,7 +30,8 @@ struct GraphKeyHash {
 // Per-path lane of the eager engine: hop-one and hop-two streams, per-slot events of the
 // two-slot staging ring, and the lane's staging buffers (grown on demand).
 struct EagerLane {
-  cudaStream_t s[2] = {nullptr, nullptr};
+  cudaStream_t s[kLaneStreams] = {};
+  cudaEvent_t join[kLaneStreams] = {};         // end of each extra copy-engine chain of a launch
   cudaEvent_t hop1[kMaxStageSlots] = {};
   cudaEvent_t hop2[kMaxStageSlots] = {};
   unsigned long long hop2_capture[kMaxStageSlots] = {};  // capture id the hop2 event was recorded in (0 = none)
@@ -146,6 +148,7 @@ struct mpt_ctx_s {
   bool pdl = true;             // direct kernel issue overlaps the previous copy kernel's end
   uint32_t stage_slots = 3;    // pinned slots of the device-to-device host-staged path (MPT_STAGE_SLOTS)
   uint32_t bulk_cfg = 0;       // configuration of the bulk-copy kernel (MPT_BULK_CONFIG)
+  uint32_t ce_lanes = 1;       // chains a copy-engine path's chunks are dealt over (MPT_CE_LANES)
   std::unique_ptr<mpt::HostCopyPool> host_pool;  // CPU hops of host-thread staging (made on first use)
   unsigned host_threads = 0;   // pool workers (MPT_HOST_THREADS; 0 = min(8, cores / 2) - 1)
   std::map<uint32_t, mpt::TuneEntry> tuned;  // tune_key -> choice

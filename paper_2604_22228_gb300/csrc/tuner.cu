@@ -272,8 +272,12 @@ struct Candidate {
 std::vector<Candidate> candidates(mpt_ctx_t c, uint32_t dir, uint64_t n, uint32_t mode) {
   std::vector<Candidate> out;
   const uint32_t sms = (uint32_t)c->sms;
+  // chunk sizes of 64 KiB and more are rounded up to 64 KiB multiples: copy engines move
+  // chunks whose boundaries are not page-aligned at about half speed (GB300, 3 x 21.33 MiB:
+  // 51 us against 27 us for 3 x 21.375 MiB)
   auto chunk_for = [](uint64_t bytes, uint64_t parts) {
-    return std::max<uint64_t>(16, round_up((bytes + parts - 1) / std::max<uint64_t>(parts, 1), 16));
+    const uint64_t c = (bytes + parts - 1) / std::max<uint64_t>(parts, 1);
+    return std::max<uint64_t>(16, c >= (64u << 10) ? round_up(c, 64u << 10) : round_up(c, 16));
   };
   auto one = [&](uint32_t kind, uint64_t chunk, uint32_t ctas, uint32_t flags) {
     Candidate k{};
@@ -316,8 +320,10 @@ std::vector<Candidate> candidates(mpt_ctx_t c, uint32_t dir, uint64_t n, uint32_
     for (uint32_t ctas : {sms, 4 * sms, 16 * sms}) one(MPT_PATH_SM, whole, ctas, MPT_SM_VEC128);
     if (n <= (32ull << 20) && n > (64u << 10))
       for (uint32_t ctas : {4 * sms, 16 * sms}) one(MPT_PATH_SM, whole, ctas, MPT_SM_TILE8K);
-    if (n >= (1u << 20))
-      for (uint32_t ctas : {sms, 2 * sms}) one(MPT_PATH_SM, whole, ctas, MPT_SM_BULK);
+    if (n >= (1u << 20)) {  // the bulk kernel: one wave of its resident CTAs, and two
+      const uint32_t wave = bulk_config(c->bulk_cfg).ctas_per_sm * sms;
+      for (uint32_t ctas : {wave, 2 * wave}) one(MPT_PATH_SM, whole, ctas, MPT_SM_BULK);
+    }
     for (uint64_t parts : {1, 2, 3, 4, 8}) {
       if (parts > 1 && n < parts * (64u << 10)) continue;
       one(MPT_PATH_CE, chunk_for(n, parts), 0, 0);
