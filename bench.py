@@ -688,6 +688,7 @@ def run_ours(args):
         copy64 = run_copy64_split(mpt, torch, ctx, stream)
         ok = ok and copy64["parity_ok"]
     lifecycle = run_graph_lifecycle(mpt, torch, ctx, stream)
+    host_link = None if args.no_host_sweep else run_host_link(mpt, torch, ctx, stream)
     windows = None if args.no_windows else run_windows(mpt, torch, ctx)
     ok = ok and (windows is None or windows["parity_ok"])
     jacobi = None if args.no_jacobi else run_jacobi(mpt, torch, ctx)
@@ -792,7 +793,7 @@ def run_ours(args):
             "e2e": e2e, "cpu_baseline": cpu, "gpu_launches": kernels_per_step * args.steps,
             "clocks": clk, "parity_ok": ok, "host_elapsed_s": round(host_elapsed, 4), "tune_s": round(tune_s, 2),
             "batched": batched, "serving": serving, "serving_replay": serving_replay, "host_sweep": host_sweep,
-            "graph_lifecycle": lifecycle,
+            "graph_lifecycle": lifecycle, "host_link": host_link,
             "windows": windows, "jacobi": jacobi, "copy64MiB_ce_sm_50_50": copy64, "pageable_host": pageable,
             "sweep": sweep, "wall_s": round(time.perf_counter() - t_wall0, 2),
         }
@@ -1470,6 +1471,107 @@ def run_host_sweep(mpt, torch, ctx, stream, max_bytes=2 << 30, reps=3, tune=True
     ok = bool(torch.equal(host_dst[:1 << 20], dev_b[:1 << 20].cpu())) and bool(torch.equal(dev_a[:1 << 20].cpu(), host_src[:1 << 20]))
     return {"rows": rows, "parity_ok": ok,
             "note": "GB/s of message bytes; host link measured at 211 GB/s H2D and 193 GB/s D2H for copy engine and zero-copy alike"}
+
+
+def _numa_of(addr: int):
+    """NUMA placement of the mapping holding `addr` (pages per node from /proc/self/numa_maps),
+    or None where the kernel does not report it."""
+    try:
+        rows = []
+        for line in open("/proc/self/numa_maps"):
+            parts = line.split()
+            rows.append((int(parts[0], 16), parts[1:]))
+        rows.sort()
+        best = None
+        for start, rest in rows:
+            if start <= addr:
+                best = rest
+            else:
+                break
+        if best is None:
+            return None
+        return {k: int(v) for k, v in (x.split("=") for x in best if x.startswith("N") and "=" in x)} or None
+    except Exception:
+        return None
+
+
+def run_host_link(mpt, torch, ctx, stream, nbytes=1 << 30):
+    """An independent bound for the host-link routes: host-memory bandwidth with CPU threads
+    alone (read, write, copy over page-locked memory from mpt_host_alloc), the GPU's copy
+    engines and zero-copy kernel alone, and the two at once (CPU threads streaming a buffer of
+    their own while the GPU moves another), where both share the host memory.  Also where the
+    page-locked buffers live (NUMA nodes)."""
+    import threading
+    cores = os.cpu_count() or 1
+    hp = [mpt.mpt_host_alloc(nbytes) for _ in range(3)]  # GPU's host side, CPU's buffer, copy target
+    dev = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    out = {"bytes": nbytes, "host_cores": cores,
+           "numa_nodes": sorted(d for d in os.listdir("/sys/devices/system/node") if d.startswith("node"))
+           if os.path.isdir("/sys/devices/system/node") else None,
+           "pinned_buffer_numa_pages": _numa_of(hp[0])}
+    # CPU alone
+    cpu = {}
+    for op, name in ((0, "read"), (1, "write"), (2, "copy")):
+        cpu[name] = {str(t): round(mpt.mpt_host_bandwidth(hp[1], nbytes, t, op, 3), 1)
+                     for t in sorted({1, 4, 8, max(1, cores - 1), cores})}
+    out["cpu_alone_gbs"] = cpu
+    # GPU alone: one copy-engine node per direction, both directions, the zero-copy kernel
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    up = mpt.mpt_plan(ctx, nbytes, mpt.MPT_H2D, [(mpt.MPT_PATH_CE, 65536, nbytes)])
+    down = mpt.mpt_plan(ctx, nbytes, mpt.MPT_D2H, [(mpt.MPT_PATH_CE, 65536, nbytes)])
+    g_up = mpt.mpt_capture(ctx, up, dev.data_ptr(), hp[0])
+    dev2 = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    g_down = mpt.mpt_capture(ctx, down, hp[2], dev2.data_ptr())
+    s2 = torch.cuda.Stream()
+
+    def gpu_rate(launch, reps):
+        launch()
+        e0.record(stream)
+        for _ in range(reps):
+            launch()
+        e1.record(stream)
+        e1.synchronize()
+        return nbytes * reps / (e0.elapsed_time(e1) / 1e3) / 1e9
+
+    def both():
+        s2.wait_stream(stream)
+        mpt.mpt_launch(g_up, stream)
+        mpt.mpt_launch(g_down, s2)
+        stream.wait_stream(s2)
+    gpu = {"ce_h2d": gpu_rate(lambda: mpt.mpt_launch(g_up, stream), 5),
+           "ce_d2h": gpu_rate(lambda: mpt.mpt_launch(g_down, stream), 5),
+           "ce_both_per_direction": gpu_rate(both, 5),
+           "zc_h2d": gpu_rate(lambda: mpt.mpt_sm_copy(ctx, dev.data_ptr(), hp[0], nbytes, 0, 0, stream), 5),
+           "zc_d2h": gpu_rate(lambda: mpt.mpt_sm_copy(ctx, hp[2], dev2.data_ptr(), nbytes, 0, 0, stream), 5)}
+    out["gpu_alone_gbs"] = {k: round(v, 1) for k, v in gpu.items()}
+
+    # both at once: CPU threads stream their own buffer for the whole GPU window
+    def together(launch, op, threads):
+        done, rates = threading.Event(), []
+
+        def worker():
+            while not done.is_set():
+                rates.append(mpt.mpt_host_bandwidth(hp[1], nbytes, threads, op, 1))
+        t = threading.Thread(target=worker)
+        t.start()
+        time.sleep(0.05)
+        g = gpu_rate(launch, 30)
+        done.set()
+        t.join()
+        return {"gpu_gbs": round(g, 1), "cpu_gbs": round(statistics.median(rates), 1), "cpu_reps": len(rates)}
+    th = max(1, cores - 1)
+    out["together"] = {
+        f"ce_h2d+cpu_read_{th}t": together(lambda: mpt.mpt_launch(g_up, stream), 0, th),
+        f"ce_d2h+cpu_write_{th}t": together(lambda: mpt.mpt_launch(g_down, stream), 1, th),
+        f"ce_h2d+cpu_read_4t": together(lambda: mpt.mpt_launch(g_up, stream), 0, 4),
+    }
+    for g in (g_up, g_down):
+        mpt.mpt_graph_release(g)
+    for p_ in (up, down):
+        mpt.mpt_plan_destroy(p_)
+    for p_ in hp:
+        mpt.mpt_host_free(p_)
+    return out
 
 
 def run_graph_lifecycle(mpt, torch, ctx, stream):

@@ -646,6 +646,16 @@ MPT_API mpt_status mpt_hash_ranges_noalloc(const void* const* ptrs, const uint64
 MPT_API mpt_status mpt_host_alloc(uint64_t nbytes, void** out);
 MPT_API mpt_status mpt_host_free(void* ptr);
 
+/* Host-memory bandwidth with CPU threads alone: the memory every host-link path (copy
+ * engines, zero-copy kernel, staged paths; Sec. 4.3, Sec. 5.2) reads or writes on the host
+ * side.  `threads` host threads each stream over their contiguous part of [ptr, ptr+nbytes),
+ * `reps` times: op 0 reads every 8-byte word, op 1 writes every word, op 2 copies the first
+ * half of the buffer into the second.  *out_gbs gets the best rep's host-memory traffic in
+ * GB/s (bytes read plus bytes written).  Blocking; host only, no GPU work.  Errors: EINVAL
+ * (NULL argument, op above 2, threads outside 1..1024, a buffer under 4 KiB per thread). */
+MPT_API mpt_status mpt_host_bandwidth(void* ptr, uint64_t nbytes, uint32_t threads, uint32_t op, uint32_t reps,
+                                      double* out_gbs);
+
 #ifdef __cplusplus
 }
 #endif

@@ -418,3 +418,11 @@ def mpt_host_alloc(nbytes: int) -> int:
 
 def mpt_host_free(ptr) -> None:
     _check(lib().mpt_host_free(_ptr(ptr)), "mpt_host_free")
+
+
+def mpt_host_bandwidth(ptr, nbytes: int, threads: int, op: int, reps: int = 3) -> float:
+    """Host-memory GB/s of `threads` CPU threads streaming over [ptr, ptr+nbytes): op 0 read,
+    1 write, 2 copy (first half into the second half)."""
+    out = C.c_double()
+    _check(lib().mpt_host_bandwidth(_ptr(ptr), nbytes, threads, op, reps, C.byref(out)), "mpt_host_bandwidth")
+    return out.value

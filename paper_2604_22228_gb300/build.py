@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(PKG, "libmpt.so")
 OBJDIR = os.path.join(PKG, "_build")
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
-SOURCES = ["copy_kernels.cu", "copy_bulk.cu", "stage_consume.cu", "runtime.cu", "planner.cpp", "api_plan.cpp", "model.cpp", "tuner.cu", "batch.cu", "serve.cu", "jacobi.cu", "noalloc.cu", "host_pool.cpp"]
+SOURCES = ["copy_kernels.cu", "copy_bulk.cu", "stage_consume.cu", "runtime.cu", "planner.cpp", "api_plan.cpp", "model.cpp", "tuner.cu", "batch.cu", "serve.cu", "jacobi.cu", "noalloc.cu", "host_pool.cpp", "host_probe.cpp"]
 
 
 def _nvcc() -> str:
