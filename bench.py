@@ -60,28 +60,32 @@ def load_peaks():
 
 
 def roofline_traffic(variant: str, ctas: int):
-    """DRAM bytes per 1 GiB launch from the committed ncu summary, or None when the kernel
-    source changed since the capture (or no capture exists for this variant/launch)."""
+    """DRAM bytes per 1 GiB launch of the SM copy kernel `variant` ("vec" or "bulk") at its
+    default grid (ctas 0) from the committed ncu summary, or None when that kernel's sources
+    changed since the capture (or no capture exists for this variant and launch)."""
     import re
     prof = os.path.join(ROOT, "profiles", f"k_sm_copy_{variant}_1GiB.md")
-    if not os.path.exists(prof) or ctas not in (0,):
+    if not os.path.exists(prof) or ctas != 0:
         return None
     text = open(prof).read()
     m = re.search(r"traffic_bytes_per_launch \| (\d+)", text)
     h = re.search(r"kernel source sha256 \([^)]*\): ([0-9a-f]{64})", text)
-    if not m or not h or kernel_source_sha() != h.group(1):
+    if not m or not h or kernel_source_sha(variant) != h.group(1):
         return None
     return int(m.group(1))
 
 
-KERNEL_SOURCES = ("copy_kernels.cu", "copy_device.cuh", "kernels.cuh")
+# the files each SM copy kernel variant is compiled from (device code and its launch arguments)
+KERNEL_SOURCES = {"vec": ("copy_kernels.cu", "copy_device.cuh", "kernels.cuh"),
+                  "bulk": ("copy_bulk.cu", "copy_device.cuh", "kernels.cuh", "bulk_config.h")}
 
 
-def kernel_source_sha() -> str:
-    """sha256 over the files the copy kernels are compiled from, in KERNEL_SOURCES order."""
+def kernel_source_sha(variant: str = "vec") -> str:
+    """sha256 over the files the SM copy kernel `variant` is compiled from, in KERNEL_SOURCES
+    order."""
     import hashlib
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in KERNEL_SOURCES[variant]:
         h.update(open(os.path.join(ROOT, "paper_2604_22228_gb300", "csrc", name), "rb").read())
     return h.hexdigest()
 
@@ -582,12 +586,15 @@ def run_ours(args):
         for p in eager_plans:
             mpt.mpt_plan_destroy(p)
 
-    # ---- dominant kernel alone: SM copy kernel on the 1 GiB message, CUDA events ----
+    # ---- dominant kernel alone: the SM copy kernel that the 1 GiB message's plan runs (the
+    # message takes about half of every step), on that message at the kernel's default grid
+    # (the launch the committed ncu capture used), CUDA events ----
     kin = args.kernel_launches
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    # the kernel's own default launch (vec128, 16 CTAs per SM): the configuration the
-    # committed ncu capture of this launch used
     variant, ctas = 0, 0
+    for q in mpt.mpt_plan_paths(step_plans[-1]):
+        if q["kind"] == mpt.MPT_PATH_SM and q["flags"] & mpt.MPT_SM_BULK:
+            variant = mpt.MPT_SM_BULK
     with torch.cuda.stream(stream):
         for _ in range(3):
             mpt.mpt_sm_copy(ctx, base_d + offs[-1], base_s + offs[-1], SIZES[-1], variant, ctas, stream)
@@ -642,19 +649,29 @@ def run_ours(args):
         ev_mid = [torch.cuda.Event() for _ in sets]
         ev_down = [torch.cuda.Event() for _ in sets]
 
-        def e2e_step(k):
+        stage_marks = []
+
+        def e2e_step(k, marks=None):
             i = k % 2
+            m = [torch.cuda.Event(enable_timing=True) for _ in range(6)] if marks is not None else None
             s_up.wait_event(ev_mid[i])       # the set's previous sweep has read its inputs
+            if m: m[0].record(s_up)
             mpt.mpt_launch(g_up[i], s_up)
+            if m: m[1].record(s_up)
             ev_up[i].record(s_up)
             s_mid.wait_event(ev_up[i])
             s_mid.wait_event(ev_down[i])     # the set's previous results have gone down
+            if m: m[2].record(s_mid)
             for h in sweep_h[i]:
                 mpt.mpt_launch(h, s_mid)
+            if m: m[3].record(s_mid)
             ev_mid[i].record(s_mid)
             s_down.wait_event(ev_mid[i])
+            if m: m[4].record(s_down)
             mpt.mpt_launch(g_down[i], s_down)
+            if m: m[5].record(s_down)
             ev_down[i].record(s_down)
+            if m: marks.append(m)
 
         e2e_steps = max(2, min(args.steps, 10))
         for k in range(2):
@@ -663,7 +680,7 @@ def run_ours(args):
         dist_barrier(world)
         e0.record(s_up)
         for k in range(e2e_steps):
-            e2e_step(k)
+            e2e_step(k, stage_marks)
         s_up.wait_stream(s_mid)
         s_up.wait_stream(s_down)
         e1.record(s_up)
@@ -674,7 +691,14 @@ def run_ours(args):
         torch.cuda.synchronize()
         ok = ok and bool(torch.equal(hdst[big:big + 4096], hsrc[big:big + 4096])) and \
             bool(torch.equal(hdst[offs[20]:offs[20] + SIZES[20]], hsrc[offs[20]:offs[20] + SIZES[20]]))
+        # per stage: its duration and its start after the region's start, median over the steps
+        stage = {}
+        for j, name in ((0, "up"), (2, "sweep"), (4, "down")):
+            stage[f"{name}_ms"] = round(statistics.median(m[j].elapsed_time(m[j + 1]) for m in stage_marks), 3)
+        stage["step_period_ms"] = round(statistics.median(
+            stage_marks[k][0].elapsed_time(stage_marks[k + 1][0]) for k in range(len(stage_marks) - 1)), 3)
         e2e = {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": total, "d2h_bytes_per_step": total,
+               "stages": stage,
                "steps": e2e_steps, "pipelined": "2 device arena sets; step k down while step k+1 comes up",
                "link_plans": args.e2e_plan, "link_chunk_mib": args.e2e_chunk_mib or "whole leg"}
         for g in g_up + g_down + sweep_h[1]:

@@ -87,7 +87,7 @@ typedef enum { MPT_MODE_GRAPH = 0, MPT_MODE_EAGER = 1 } mpt_mode;
 #define MPT_SM_VEC128 0u   /* 128-bit vector loads/stores, grid-stride over 64 KiB tiles */
 #define MPT_SM_BULK 1u     /* cp.async.bulk global->shared->global ring per CTA */
 /* Ring configurations of the MPT_SM_BULK kernel, chosen per context by MPT_BULK_CONFIG=i
- * (0 <= i < MPT_BULK_CONFIGS, default 0) at context creation.  Stages x stage bytes, CTAs per SM:
+ * (0 <= i < MPT_BULK_CONFIGS, default 3) at context creation.  Stages x stage bytes, CTAs per SM:
  * 0: 4 x 48 KiB, 1; 1: as 0 with an L2 evict-first policy; 2: 3 x 64 KiB, 1; 3: 2 x 48 KiB, 2;
  * 4: as 3 with an L2 evict-first policy; 5: 3 x 32 KiB, 2; 6: 8 x 24 KiB, 1. */
 #define MPT_BULK_CONFIGS 7u

@@ -28,7 +28,7 @@ def _nvcc() -> str:
 
 
 CFLAGS = [ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3,-fvisibility=hidden"]
-HEADERS = ["kernels.cuh", "batch_kernels.cuh", "copy_device.cuh", "internal.h", "ctx.h", "host_pool.h"]
+HEADERS = ["kernels.cuh", "bulk_config.h", "batch_kernels.cuh", "copy_device.cuh", "internal.h", "ctx.h", "host_pool.h"]
 STAMP = OUT + ".sha256"
 
 

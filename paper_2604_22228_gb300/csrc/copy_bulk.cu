@@ -21,6 +21,7 @@
 // is released.
 #include "mpt.h"
 #include "kernels.cuh"
+#include "bulk_config.h"
 #include "copy_device.cuh"
 
 namespace mpt {
@@ -226,9 +227,10 @@ __global__ void __launch_bounds__(kBulkThreads, kPerSm) k_sm_copy_bulk(CopyArgs 
 namespace {
 
 // The configurations compiled in.  On GB300 (CUDA events, back-to-back launches of one
-// message) all of them move 6.3-6.55 TB/s at 1-4 GiB; large stages do best at one CTA per SM
-// (0: 6.40-6.44 TB/s), two CTAs per SM with two stages each at 4 GiB (3, 4: 6.52-6.55 TB/s).
-// Smaller and deeper rings (16 KiB and 12 KiB stages) measured 2-5 % slower and were dropped.
+// message, 32 CTAs per SM) configurations 0, 3 and 5 move 6.9-7.05 TB/s at 1-4 GiB; at
+// 256 MiB configuration 3 keeps 6.74 TB/s where 0 falls to 5.1 (a tile or so per CTA, and
+// one resident CTA per SM cannot hide a CTA's start).  Smaller and deeper rings (16 KiB and
+// 12 KiB stages) measured 2-5 % slower in one wave and were dropped.
 template <int S, uint32_t B, int K, int P, int H = 0>
 BulkConfig cfg() {
   return BulkConfig{(uint32_t)S, B, (uint32_t)K, (uint32_t)P,
@@ -236,10 +238,10 @@ BulkConfig cfg() {
 }
 
 const BulkConfig kConfigs[] = {
-    cfg<4, 48 * 1024, 1, 1>(),     // 0: 192 KiB, four 48 KiB stages (default)
+    cfg<4, 48 * 1024, 1, 1>(),     // 0: 192 KiB, four 48 KiB stages
     cfg<4, 48 * 1024, 1, 1, 1>(),  // 1: as 0, L2 evict-first on loads and stores
     cfg<3, 64 * 1024, 1, 1>(),     // 2: 192 KiB, three 64 KiB stages
-    cfg<2, 48 * 1024, 1, 2>(),     // 3: 2 x 96 KiB, two 48 KiB stages each
+    cfg<2, 48 * 1024, 1, 2>(),     // 3: 2 x 96 KiB, two 48 KiB stages each (default)
     cfg<2, 48 * 1024, 1, 2, 1>(),  // 4: as 3, L2 evict-first
     cfg<3, 32 * 1024, 1, 2>(),     // 5: 2 x 96 KiB, three 32 KiB stages each
     cfg<8, 24 * 1024, 2, 1>(),     // 6: 192 KiB, eight 24 KiB stages, two stores reading

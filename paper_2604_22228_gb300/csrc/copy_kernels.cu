@@ -13,6 +13,7 @@
 // The bulk-copy variant of the SM copy kernel (cp.async.bulk through shared memory) is in
 // copy_bulk.cu.
 #include "kernels.cuh"
+#include "bulk_config.h"
 #include "copy_device.cuh"
 
 #include <algorithm>

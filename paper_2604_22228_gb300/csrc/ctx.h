@@ -11,6 +11,7 @@
 #include "internal.h"
 #include "batch_kernels.cuh"
 #include "kernels.cuh"
+#include "bulk_config.h"
 
 namespace mpt {
 

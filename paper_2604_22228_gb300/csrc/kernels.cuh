@@ -39,28 +39,13 @@ struct CopyArgs {
   uint32_t piece;                        // bulk variant: tile bytes (that configuration's stage)
 };
 
-// One configuration of the bulk-copy kernel: a ring of `stages` shared-memory stages of
-// `stage_bytes` (one cp.async.bulk load and one store per tile), stores allowed to be still
-// reading shared memory for `keep` tiles behind the newest, `ctas_per_sm` CTAs resident per
-// SM (the default grid), and the kernel instantiated for it.
-struct BulkConfig {
-  uint32_t stages;
-  uint32_t stage_bytes;
-  uint32_t keep;
-  uint32_t ctas_per_sm;
-  const void* fn;
-};
-uint32_t bulk_config_count();
-const BulkConfig& bulk_config(uint32_t i);  // i < bulk_config_count()
-constexpr uint32_t kBulkDefaultConfig = 0;
-
 // Fill `a` for up to kInlineRanges ranges with the tiling of `variant` (0 vec128,
-// 1 bulk in configuration bulk_cfg, 2 zero-copy, 3 vec128 with 8 KiB tiles).  Returns
+// 1 bulk in configuration bulk_cfg (bulk_config.h), 2 zero-copy, 3 vec128 with 8 KiB tiles).  Returns
 // kArgsOk, kArgsNeedVec when a bulk launch must fall back to vec128 (source and destination
 // differ modulo 16, which cp.async.bulk cannot copy), or kArgsTooLarge.
 constexpr int kArgsOk = 0, kArgsNeedVec = 1, kArgsTooLarge = 2;
 int make_copy_args(CopyArgs& a, const void* src, void* dst, const RangeDesc* ranges, int n,
-                   int variant, uint32_t* status, uint32_t bulk_cfg = kBulkDefaultConfig);
+                   int variant, uint32_t* status, uint32_t bulk_cfg);
 
 // *_any variants also copy ranges whose source and destination differ modulo 16
 // (RangeDesc.shift != 0); the plain ones are leaner and need every shift to be 0.

@@ -317,13 +317,11 @@ std::vector<Candidate> candidates(mpt_ctx_t c, uint32_t dir, uint64_t n, uint32_
     return out;
   }
   if (dir == MPT_D2D) {
-    for (uint32_t ctas : {sms, 4 * sms, 16 * sms}) one(MPT_PATH_SM, whole, ctas, MPT_SM_VEC128);
+    for (uint32_t ctas : {sms, 4 * sms, 16 * sms, 64 * sms}) one(MPT_PATH_SM, whole, ctas, MPT_SM_VEC128);
     if (n <= (32ull << 20) && n > (64u << 10))
       for (uint32_t ctas : {4 * sms, 16 * sms}) one(MPT_PATH_SM, whole, ctas, MPT_SM_TILE8K);
-    if (n >= (1u << 20)) {  // the bulk kernel: one wave of its resident CTAs, and two
-      const uint32_t wave = bulk_config(c->bulk_cfg).ctas_per_sm * sms;
-      for (uint32_t ctas : {wave, 2 * wave}) one(MPT_PATH_SM, whole, ctas, MPT_SM_BULK);
-    }
+    if (n >= (1u << 20))  // the bulk kernel, many waves of its resident CTAs
+      for (uint32_t ctas : {16 * sms, 32 * sms}) one(MPT_PATH_SM, whole, ctas, MPT_SM_BULK);
     for (uint64_t parts : {1, 2, 3, 4, 8}) {
       if (parts > 1 && n < parts * (64u << 10)) continue;
       one(MPT_PATH_CE, chunk_for(n, parts), 0, 0);
