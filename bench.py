@@ -1527,7 +1527,7 @@ def run_host_link(mpt, torch, ctx, stream, nbytes=1 << 30):
     page-locked buffers live (NUMA nodes)."""
     import threading
     cores = os.cpu_count() or 1
-    hp = [mpt.mpt_host_alloc(nbytes) for _ in range(3)]  # GPU's host side, CPU's buffer, copy target
+    hp = [mpt.mpt_host_alloc(ctx, nbytes)[0] for _ in range(3)]  # GPU's host side, CPU's buffer, copy target
     dev = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
     out = {"bytes": nbytes, "host_cores": cores,
            "numa_nodes": sorted(d for d in os.listdir("/sys/devices/system/node") if d.startswith("node"))

@@ -641,9 +641,14 @@ MPT_API mpt_status mpt_hash_ranges_noalloc(const void* const* ptrs, const uint64
 
 /* ---- page-locked host memory ---------------------------------------------------- */
 
-/* Allocate `nbytes` of page-locked, device-mapped host memory (usable by copy engines and
- * by the zero-copy kernel at the same address).  Free with mpt_host_free. */
-MPT_API mpt_status mpt_host_alloc(uint64_t nbytes, void** out);
+/* Allocate `nbytes` of page-locked, device-mapped host memory for staging and zero-copy
+ * transfers (Sec. 4.3's host-staged path moves chunks through such buffers).  ctx (nullable):
+ * its device is made current first.  *host receives the host address; dev_alias (nullable)
+ * receives the address device code uses for it (cudaHostGetDevicePointer; with unified
+ * addressing, as on GB300, the same value).  Copy engines and the zero-copy kernel accept
+ * either.  The caller owns the buffer: free it with mpt_host_free.  Errors: EINVAL (NULL
+ * host), ENOMEM, ECUDA (no device address). */
+MPT_API mpt_status mpt_host_alloc(mpt_ctx_t ctx, uint64_t nbytes, void** host, void** dev_alias);
 MPT_API mpt_status mpt_host_free(void* ptr);
 
 /* Host-memory bandwidth with CPU threads alone: the memory every host-link path (copy

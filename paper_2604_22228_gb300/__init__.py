@@ -410,10 +410,11 @@ def mpt_hash_ranges_noalloc(ranges, stream=None) -> list[int]:
     return list(out[:n])
 
 
-def mpt_host_alloc(nbytes: int) -> int:
-    p = C.c_void_p()
-    _check(lib().mpt_host_alloc(nbytes, C.byref(p)), "mpt_host_alloc")
-    return p.value
+def mpt_host_alloc(ctx, nbytes: int) -> tuple[int, int]:
+    """(host address, device alias) of a new page-locked, device-mapped host buffer."""
+    p, d = C.c_void_p(), C.c_void_p()
+    _check(lib().mpt_host_alloc(ctx, nbytes, C.byref(p), C.byref(d)), "mpt_host_alloc")
+    return p.value, d.value
 
 
 def mpt_host_free(ptr) -> None:

@@ -1310,12 +1310,21 @@ mpt_status mpt_selftest_flag_timeout(mpt_ctx_t c, uint64_t timeout_ns, uint32_t*
   return mpt_ctx_status(c, site);
 }
 
-mpt_status mpt_host_alloc(uint64_t nbytes, void** out) {
-  if (!out) return fail(MPT_EINVAL, "mpt_host_alloc: out is NULL");
-  *out = nullptr;
-  if (cudaHostAlloc(out, std::max<uint64_t>(nbytes, 1), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
+mpt_status mpt_host_alloc(mpt_ctx_t c, uint64_t nbytes, void** host, void** dev_alias) {
+  if (!host) return fail(MPT_EINVAL, "mpt_host_alloc: host is NULL");
+  *host = nullptr;
+  if (dev_alias) *dev_alias = nullptr;
+  if (c) CUDA_TRY(cudaSetDevice(c->device));
+  if (cudaHostAlloc(host, std::max<uint64_t>(nbytes, 1), cudaHostAllocMapped | cudaHostAllocPortable) != cudaSuccess) {
     cudaGetLastError();
+    *host = nullptr;
     return fail(MPT_ENOMEM, "mpt_host_alloc: %llu bytes", (unsigned long long)nbytes);
+  }
+  if (dev_alias && cudaHostGetDevicePointer(dev_alias, *host, 0) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFreeHost(*host);
+    *host = nullptr;
+    return fail(MPT_ECUDA, "mpt_host_alloc: no device address for the mapped buffer");
   }
   return MPT_OK;
 }
