@@ -646,10 +646,16 @@ MPT_API mpt_status mpt_hash_ranges_noalloc(const void* const* ptrs, const uint64
  * its device is made current first.  *host receives the host address; dev_alias (nullable)
  * receives the address device code uses for it (cudaHostGetDevicePointer; with unified
  * addressing, as on GB300, the same value).  Copy engines and the zero-copy kernel accept
- * either.  The caller owns the buffer: free it with mpt_host_free.  Errors: EINVAL (NULL
- * host), ENOMEM, ECUDA (no device address). */
+ * either.  The caller owns the buffer: free it with mpt_host_free (with the same ctx, which
+ * records the buffer).  Errors: EINVAL (NULL host), ENOMEM, ECUDA (no device address). */
 MPT_API mpt_status mpt_host_alloc(mpt_ctx_t ctx, uint64_t nbytes, void** host, void** dev_alias);
-MPT_API mpt_status mpt_host_free(void* ptr);
+
+/* Free a buffer from mpt_host_alloc.  With the context it was allocated with, every graph that
+ * context has cached on the buffer (source or destination range overlapping it) is dropped
+ * from the cache first, as mpt_graph_evict would: a cached graph bound to freed page-locked
+ * memory must never be launched or retargeted.  Handles the caller still holds stay valid
+ * objects but must not be launched again.  ctx may be NULL (no eviction). */
+MPT_API mpt_status mpt_host_free(mpt_ctx_t ctx, void* ptr);
 
 /* Host-memory bandwidth with CPU threads alone: the memory every host-link path (copy
  * engines, zero-copy kernel, staged paths; Sec. 4.3, Sec. 5.2) reads or writes on the host

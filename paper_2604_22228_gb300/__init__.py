@@ -417,8 +417,9 @@ def mpt_host_alloc(ctx, nbytes: int) -> tuple[int, int]:
     return p.value, d.value
 
 
-def mpt_host_free(ptr) -> None:
-    _check(lib().mpt_host_free(_ptr(ptr)), "mpt_host_free")
+def mpt_host_free(ctx, ptr) -> None:
+    """Free an mpt_host_alloc buffer; with its context, cached graphs on it are dropped first."""
+    _check(lib().mpt_host_free(ctx, _ptr(ptr)), "mpt_host_free")
 
 
 def mpt_host_bandwidth(ptr, nbytes: int, threads: int, op: int, reps: int = 3) -> float:

@@ -159,7 +159,7 @@ SIGNATURES = {
     "mpt_selftest_flag_timeout": (C.c_int, [H, C.c_uint64, P(C.c_uint32)]),
     "mpt_hash_ranges_noalloc": (C.c_int, [P(C.c_void_p), P(C.c_uint64), C.c_uint32, C.c_void_p, P(C.c_uint64)]),
     "mpt_host_alloc": (C.c_int, [H, C.c_uint64, P(C.c_void_p), P(C.c_void_p)]),
-    "mpt_host_free": (C.c_int, [C.c_void_p]),
+    "mpt_host_free": (C.c_int, [H, C.c_void_p]),
     "mpt_host_bandwidth": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint32, C.c_uint32, C.c_uint32, P(C.c_double)]),
 }
 

@@ -172,4 +172,5 @@ struct mpt_ctx_s {
   bool batch_dma_set = false;                         // configured (else environment defaults)
   bool batch_timing = false;                          // bracket each batch replay with timing events
   std::vector<cudaEvent_t> each_ev;                   // completion events of mpt_copy_each (grown on demand)
+  std::unordered_map<uint64_t, uint64_t> host_bufs;   // page-locked buffers mpt_host_alloc made: address -> bytes
 };

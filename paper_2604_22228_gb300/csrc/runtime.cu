@@ -1326,11 +1326,27 @@ mpt_status mpt_host_alloc(mpt_ctx_t c, uint64_t nbytes, void** host, void** dev_
     *host = nullptr;
     return fail(MPT_ECUDA, "mpt_host_alloc: no device address for the mapped buffer");
   }
+  if (c) c->host_bufs[(uint64_t)(uintptr_t)*host] = nbytes;
   return MPT_OK;
 }
 
-mpt_status mpt_host_free(void* p) {
-  if (p) CUDA_TRY(cudaFreeHost(p));
+mpt_status mpt_host_free(mpt_ctx_t c, void* p) {
+  if (!p) return MPT_OK;
+  if (c) {
+    // cached graphs bound to the buffer must not outlive it: a graph whose memcpy nodes
+    // refer to freed page-locked memory cannot be launched or retargeted safely
+    auto it = c->host_bufs.find((uint64_t)(uintptr_t)p);
+    if (it != c->host_bufs.end()) {
+      const uint64_t a = it->first, b = it->first + std::max<uint64_t>(it->second, 1);
+      for (auto lit = c->lru.begin(); lit != c->lru.end();) {
+        mpt_graph_s* g = *lit++;
+        const auto touches = [&](uint64_t lo, uint64_t hi) { return lo < b && a < std::max(hi, lo + 1); };
+        if (touches(g->src_lo, g->src_hi) || touches(g->dst_lo, g->dst_hi)) cache_drop(c, g);
+      }
+      c->host_bufs.erase(it);
+    }
+  }
+  CUDA_TRY(cudaFreeHost(p));
   return MPT_OK;
 }
 

@@ -1,5 +1,8 @@
 """mpt_host_alloc: page-locked, device-mapped host buffers and their device alias, used by the
-zero-copy kernel and by copy-engine graphs, against the oracle."""
+zero-copy kernel and by copy-engine graphs, against the oracle; and mpt_host_free dropping the
+context's cached graphs on the buffer, so that none is ever launched or retargeted on freed
+memory.  A buffer allocated without a context is freed after mpt_graph_evict, as the header
+asks of every buffer a cached graph refers to."""
 import ctypes
 
 import numpy as np
@@ -47,7 +50,7 @@ def test_host_buffer_reaches_the_device_through_either_address(ctx, with_ctx):
         g = mpt.mpt_capture(ctx, plan, dst.data_ptr(), host)
         mpt.mpt_launch(g, s)
         torch.cuda.synchronize()
-        mpt.mpt_graph_release(g)
+        mpt.mpt_graph_release(g)  # the cache still holds the graph, bound to `host`
         mpt.mpt_plan_destroy(plan)
         assert np.array_equal(dst.cpu().numpy(), T.copy(data))
         # and back: device -> the host buffer
@@ -58,7 +61,36 @@ def test_host_buffer_reaches_the_device_through_either_address(ctx, with_ctx):
         got = np.ctypeslib.as_array((ctypes.c_uint8 * n).from_address(host)).copy()
         assert np.array_equal(got, T.copy(back))
     finally:
-        mpt.mpt_host_free(host)
+        if with_ctx:
+            mpt.mpt_host_free(ctx, host)  # drops the cached graph on the buffer, then frees it
+        else:
+            mpt.mpt_graph_evict(ctx, host)
+            mpt.mpt_host_free(None, host)
+    assert mpt.mpt_graph_evict(ctx, host) == 0  # nothing cached on the freed buffer
+
+
+def test_freeing_drops_only_the_graphs_on_the_buffer(ctx):
+    import torch
+    n = 2 * MiB
+    a, _ = mpt.mpt_host_alloc(ctx, n)
+    b, _ = mpt.mpt_host_alloc(ctx, n)
+    dev = torch.zeros(2 * n, dtype=torch.uint8, device="cuda")
+    plan = mpt.mpt_plan(ctx, n, mpt.MPT_H2D, [(mpt.MPT_PATH_CE, 65536, MiB)])
+    held = []
+    try:
+        # two graphs of the same plan, both held, so that neither is retargeted to the other
+        for h, off in ((a, 0), (b, n)):
+            held.append(mpt.mpt_capture(ctx, plan, dev.data_ptr() + off, h))
+        mpt.mpt_host_free(ctx, a)
+        assert mpt.mpt_graph_evict(ctx, a) == 0   # a's graph left the cache with the buffer
+        assert mpt.mpt_graph_evict(ctx, b) == 1   # b's graph was still cached
+        mpt.mpt_launch(held[1], torch.cuda.current_stream())  # b is still allocated
+        torch.cuda.synchronize()
+    finally:
+        for g in held:
+            mpt.mpt_graph_release(g)
+        mpt.mpt_plan_destroy(plan)
+        mpt.mpt_host_free(ctx, b)
 
 
 def test_host_alloc_refuses_a_null_output():
