@@ -73,8 +73,9 @@ def test_summary_ratios():
     s = bench.summary_ratios(_study())
     r = [1.0 + 0.01 * (k % 3) for k in range(len(bench.SIZES))]
     want = math.exp(sum(math.log(x) for x in r) / len(r))
-    assert abs(s["d2d_tuned_vs_best_single"]["geomean"] - want) < 1e-4
-    assert s["d2d_tuned_vs_best_single"]["min"] == 1.0 and s["d2d_tuned_vs_best_single"]["max"] == 1.02
+    d2d = s["d2d_tuned_vs_best_single"]
+    assert abs(d2d["isolated_geomean"] - want) < 1e-4 and d2d["isolated_min"] == 1.0
+    assert d2d["back_to_back_geomean"] == 0.99 and d2d["back_to_back_min"] == 0.99
     # host rows of 64 MiB and more only: 2^26 .. 2^31 (six sizes), 210/200 and 190/190
     assert s["h2d_ge64MiB_tuned_vs_best_single"] == {"geomean": 1.05, "min": 1.05, "max": 1.05}
     assert s["d2h_ge64MiB_tuned_vs_best_single"]["geomean"] == 1.0

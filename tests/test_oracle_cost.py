@@ -90,6 +90,29 @@ def test_shares_reproduce_split():
         assert P.path_bytes(n, specs, 16) == split
 
 
+def test_shares_for_split_closed_forms():
+    # N = 65536: a share is a byte count
+    assert C.shares_for_split(65536, [16384, 4096, 45056]) == [16384, 4096, 45056]
+    # halves of 32 KiB
+    assert C.shares_for_split(32768, [16384, 16384]) == [32768, 32768]
+    # thirds of 48 bytes: 65536 * 16 / 48 = 21845.33 rounds up to 21846 (floor(48 * 21846 /
+    # 65536) = 16), and the last path takes the rest of 65536
+    assert C.shares_for_split(48, [16, 16, 16]) == [21846, 21846, 21844]
+
+
+def test_shares_for_split_are_the_smallest_that_work():
+    # each listed share is the least w with floor(N * w / 65536) == b_p: one less falls short
+    rng = random.Random(11)
+    for _ in range(200):
+        n = rng.randrange(32, 4097)
+        b0 = 16 * rng.randrange(1, n // 16)
+        if b0 >= n:
+            continue
+        w0 = C.shares_for_split(n, [b0, n - b0])[0]
+        assert (n * w0) // 65536 == b0
+        assert (n * (w0 - 1)) // 65536 < b0
+
+
 def test_exhaustive_search_rejects_large_inputs():
     with pytest.raises(ValueError):
         C.brute_force(4097, P.D2D, [P.CE], model())
