@@ -58,19 +58,43 @@ __device__ __forceinline__ void batch_body(const BatchArgs& a) {
     if (k == 0) a.host_stamps[0] = t;
     if (k == gridDim.x - 1) a.host_stamps[1] = t;
   }
+  __shared__ uint32_t s_link;
+  const uint32_t dev_tiles = h.total_tiles - h.link_tiles;
+  // thread 0's claiming state: the class it claims from, and whether it has switched yet
+  bool on_link = blockIdx.x < h.link_ctas ? h.link_tiles > 0 : dev_tiles == 0;
+  bool switched = false;
   while (true) {
-    if (threadIdx.x == 0) s_item = atomicAdd(a.cursor, 1u);
+    if (threadIdx.x == 0) {
+      uint32_t item = ~0u;
+      while (true) {
+        const uint32_t lim = on_link ? h.link_tiles : dev_tiles;
+        if (lim) {
+          const uint32_t k = atomicAdd(on_link ? a.cursor : a.cursor_dev, 1u);
+          if (k < lim) {
+            item = k;
+            break;
+          }
+        }
+        if (switched) break;
+        switched = true;
+        on_link = !on_link;
+      }
+      s_item = item;
+      s_link = on_link ? 1u : 0u;
+    }
     __syncthreads();
     const uint32_t item = s_item;
+    const bool link = s_link != 0;
     __syncthreads();
-    if (item >= h.total_tiles) break;
-    // descriptor owning this tile: the last one whose first tile is <= item
-    uint32_t lo = 0, hi = h.n - 1;
+    if (item == ~0u) break;
+    // descriptor owning this tile: within its class, the last one whose first tile is <= item
+    uint32_t lo = link ? 0 : h.n_link, hi = (link ? h.n_link : h.n_tiled) - 1;
     while (lo < hi) {
       const uint32_t mid = (lo + hi + 1) >> 1;
-      if (a.desc[mid].first_tile <= item) lo = mid;
+      if (a.desc[a.order[mid]].first_tile <= item) lo = mid;
       else hi = mid - 1;
     }
+    lo = a.order[lo];
     const BatchDesc d = a.desc[lo];
     const uint64_t off = (uint64_t)(item - d.first_tile) * h.tile_bytes;
     if (off < d.bytes) {
@@ -142,7 +166,8 @@ mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t cta
   s.dma_items = c->batch_dma_lanes ? c->batch_dma_items : 0;
   const uint32_t ndma = kDmaDirs * s.dma_lanes * s.dma_items;
   const size_t map_off = sizeof(BatchHeader) + (size_t)max_xfers * sizeof(BatchDesc);
-  s.table_bytes = map_off + (size_t)ndma * sizeof(uint32_t);
+  const size_t order_off = map_off + (size_t)ndma * sizeof(uint32_t);
+  s.table_bytes = order_off + (size_t)max_xfers * sizeof(uint32_t);
   CUDA_TRY(cudaHostAlloc(&s.h_table, s.table_bytes, cudaHostAllocPortable));
   CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&s.h_flags), (size_t)max_xfers * sizeof(uint32_t),
                          cudaHostAllocMapped | cudaHostAllocPortable));
@@ -159,6 +184,7 @@ mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t cta
   s.d_times = reinterpret_cast<unsigned long long*>(base + times_off);
   CUDA_TRY(cudaMemset(s.d_mem, 0, scratch_off + 256));
   s.h_dma_map = reinterpret_cast<uint32_t*>(s.h_table + map_off);
+  s.h_order = reinterpret_cast<uint32_t*>(s.h_table + order_off);
   for (uint32_t k = 0; k < ndma; ++k) s.h_dma_map[k] = ~0u;
   if (ndma) CUDA_TRY(cudaHostAlloc(&s.h_scratch, 64, cudaHostAllocPortable));
   uint8_t* d_scratch = base + scratch_off;
@@ -166,7 +192,9 @@ mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t cta
   CUDA_TRY(cudaEventCreateWithFlags(&s.done_ev, cudaEventDisableTiming));
   s.args.hdr = reinterpret_cast<const BatchHeader*>(s.d_table);
   s.args.desc = reinterpret_cast<const BatchDesc*>(s.d_table + sizeof(BatchHeader));
+  s.args.order = reinterpret_cast<const uint32_t*>(s.d_table + order_off);
   s.args.cursor = reinterpret_cast<uint32_t*>(s.d_ctrl);
+  s.args.cursor_dev = reinterpret_cast<uint32_t*>(s.d_ctrl + 24);
   s.args.start_inv = reinterpret_cast<unsigned long long*>(s.d_ctrl + 8);
   s.args.done = reinterpret_cast<uint32_t*>(s.d_ctrl + 256);
   s.args.started = reinterpret_cast<uint32_t*>(s.d_ctrl + 16);
@@ -278,6 +306,8 @@ mpt_status batch_setup(mpt_ctx_t c) {
   // which the latency of host-link reads needs; all CTAs resident at once
   const uint32_t ctas = c->batch_ctas ? c->batch_ctas : 3u * (uint32_t)c->sms;
   if (!c->batch_tile) c->batch_tile = kDefaultTile;
+  c->batch_split = env_or("MPT_BATCH_SPLIT", 1) != 0;
+  c->batch_link_ctas = (uint32_t)env_or("MPT_BATCH_LINK_CTAS", 0);
   if (!c->batch_dma_set) {
     c->batch_dma_lanes = (uint32_t)std::min<uint64_t>(8, env_or("MPT_BATCH_DMA_LANES", 0));
     c->batch_dma_items = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(64, env_or("MPT_BATCH_DMA_ITEMS", 8)));
@@ -546,21 +576,43 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
       to_dma[i] = 1;
     }
   }
-  uint64_t tiles = 0;
+  // tiles numbered within two classes, link (a host side) and device, each descriptor's
+  // tiles contiguous in its class; order lists the descriptors with tiles, link class first
+  uint64_t tiles[2] = {0, 0};  // [0] link, [1] device
   const uint64_t tile = c->batch_tile;
   bool any_shift = false;
+  uint32_t n_link = 0, n_dev = 0;
   for (size_t i = 0; i < n; ++i) {
     const mpt_xfer& x = xfers[i];
     const uint32_t fl = (x.dir == MPT_D2H ? kDescHostDst : 0u) | (x.dir != MPT_D2D ? kDescHostSide : 0u) |
                         (to_dma[i] ? kDescDma : 0u);
     const uint64_t t = to_dma[i] ? 0 : std::max<uint64_t>(1, (x.bytes + tile - 1) / tile);
     if (!to_dma[i]) any_shift |= (((uintptr_t)x.src ^ (uintptr_t)x.dst) & 15) != 0 && x.bytes >= 16;
-    d[i] = BatchDesc{(uint64_t)(uintptr_t)x.src, (uint64_t)(uintptr_t)x.dst, x.bytes, (uint32_t)tiles, (uint32_t)t, fl, 0u};
-    tiles += t;
+    // one class for everything when the split is off
+    const int cls = (c->batch_split && x.dir == MPT_D2D) ? 1 : 0;
+    d[i] = BatchDesc{(uint64_t)(uintptr_t)x.src, (uint64_t)(uintptr_t)x.dst, x.bytes, (uint32_t)tiles[cls],
+                     (uint32_t)t, fl, 0u};
+    tiles[cls] += t;
+    if (t) (cls ? n_dev : n_link)++;
   }
-  if (tiles >= (1ull << 32)) return fail(MPT_EINVAL, "mpt_batch_submit: batch too large for 32-bit tile indices");
-  *h = BatchHeader{(uint32_t)n, (uint32_t)tiles, (uint32_t)tile, s.epoch};
+  if (tiles[0] + tiles[1] >= (1ull << 32))
+    return fail(MPT_EINVAL, "mpt_batch_submit: batch too large for 32-bit tile indices");
+  {
+    uint32_t li = 0, di = n_link;
+    for (size_t i = 0; i < n; ++i) {
+      if (!d[i].ntiles) continue;
+      const bool dev = c->batch_split && xfers[i].dir == MPT_D2D;
+      s.h_order[dev ? di++ : li++] = (uint32_t)i;
+    }
+  }
   const int gi = any_shift ? 1 : 0;
+  const uint32_t ctas = c->batch_ctas ? c->batch_ctas : 3u * (uint32_t)c->sms;
+  const uint32_t grid = gi == 0 ? ctas : std::min<uint32_t>(ctas, 2u * (uint32_t)c->sms);  // as slot_init
+  uint32_t link_ctas = grid;  // split off, or no device tiles: every CTA on the one class
+  if (c->batch_split && tiles[0] && tiles[1])
+    link_ctas = c->batch_link_ctas ? std::min(c->batch_link_ctas, grid) : std::max(1u, grid / 3);
+  *h = BatchHeader{(uint32_t)n, (uint32_t)(tiles[0] + tiles[1]), (uint32_t)tile, s.epoch,
+                   (uint32_t)tiles[0], n_link, n_link + n_dev, link_ctas};
   for (uint32_t k = 0; k < ndma; ++k) {  // retarget used lane items, switch the rest off
     const uint32_t i = s.h_dma_map[k];
     const uint8_t want = i != ~0u;

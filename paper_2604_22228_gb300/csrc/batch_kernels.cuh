@@ -12,16 +12,25 @@ constexpr uint32_t kDescHostDst = 1;   // destination is host memory: publish wi
 constexpr uint32_t kDescHostSide = 2;  // one side is host memory: coherent loads, no read-only path
 constexpr uint32_t kDescDma = 4;       // moved by a copy-engine lane, not by the kernel (ntiles 0)
 
+// Tiles come in two classes, each numbered from 0 and claimed through its own cursor: link
+// tiles (one side in host memory: they move over the host link) and device tiles (both sides
+// in this GPU's memory).  CTAs [0, link_ctas) claim link tiles first and the others device
+// tiles first; a CTA whose class runs out moves to the other.  The link, which bounds a
+// mixed batch, then stays busy from the start while the device tiles run beside it.
 struct BatchHeader {
   uint32_t n;            // descriptors in this batch
-  uint32_t total_tiles;  // sum of tiles over descriptors
+  uint32_t total_tiles;  // sum of tiles over descriptors, both classes
   uint32_t tile_bytes;
   uint32_t epoch;        // value written to a finished descriptor's host flag
+  uint32_t link_tiles;   // tiles of the link class (the rest are device tiles)
+  uint32_t n_link;       // descriptors with tiles in the link class: order[0, n_link)
+  uint32_t n_tiled;      // descriptors with tiles: order[n_link, n_tiled) are the device class
+  uint32_t link_ctas;    // CTAs that start on link tiles
 };
 
 struct BatchDesc {
   uint64_t src, dst, bytes;
-  uint32_t first_tile;  // prefix sum of tiles before this descriptor
+  uint32_t first_tile;  // prefix sum of tiles before this descriptor, within its class
   uint32_t ntiles;      // max(1, ceil(bytes / tile)); 0 for a descriptor a DMA lane moves
   uint32_t flags;
   uint32_t pad;
@@ -30,7 +39,9 @@ struct BatchDesc {
 struct BatchArgs {
   const BatchHeader* hdr;
   const BatchDesc* desc;
-  uint32_t* cursor;              // next tile to claim (reset to 0 per launch)
+  const uint32_t* order;         // descriptor indices with tiles: the link class, then the device class
+  uint32_t* cursor;              // next link tile to claim (reset to 0 per launch)
+  uint32_t* cursor_dev;          // next device tile to claim (reset to 0 per launch)
   unsigned long long* start_inv; // ~(kernel start time), max over CTAs
   uint32_t* done;                // tiles finished per descriptor (reset per launch)
   unsigned long long* times;     // completion time per descriptor (global timer, ns)

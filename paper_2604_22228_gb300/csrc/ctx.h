@@ -84,6 +84,7 @@ struct BatchSlot {
   // others disabled (no cost when no entry is large).
   uint32_t dma_lanes = 0, dma_items = 0;
   uint32_t* h_dma_map = nullptr;  // in the page-locked table: item -> descriptor (~0 unused)
+  uint32_t* h_order = nullptr;    // in the page-locked table: descriptors with tiles, link class first
   std::vector<cudaGraphNode_t> dma_cp[2], dma_fin[2];
   std::vector<uint8_t> dma_on[2];
   void* h_scratch = nullptr;      // page-locked 64 bytes: instantiation-time operand of host lanes
@@ -171,6 +172,8 @@ struct mpt_ctx_s {
   uint64_t batch_dma_min = 0;                         // smallest entry a DMA lane takes
   bool batch_dma_set = false;                         // configured (else environment defaults)
   bool batch_timing = false;                          // bracket each batch replay with timing events
+  bool batch_split = true;                            // link and device tiles claimed separately (MPT_BATCH_SPLIT)
+  uint32_t batch_link_ctas = 0;                       // CTAs starting on link tiles (MPT_BATCH_LINK_CTAS; 0 = a third)
   std::vector<cudaEvent_t> each_ev;                   // completion events of mpt_copy_each (grown on demand)
   std::unordered_map<uint64_t, uint64_t> host_bufs;   // page-locked buffers mpt_host_alloc made: address -> bytes
 };
