@@ -17,7 +17,7 @@ Output: one JSON line on stdout (rank 0), under 2 KB:
   e2e       the same sweep through the C ABI from page-locked host memory: inputs copied
             host->device and results device->host inside the timed region;
   cpu_baseline  the CPU oracle (planner + memcpy) on a bounded sample of the sweep;
-  summary   the ratios the study is judged by (multi-path or batched against the best single
+  summary   the ratios that sum the study up (multi-path or batched against the best single
             path or per-transfer copies; serving p99).
 The full study -- per size: tuned, each single path as a graph and by direct issue, splits,
 back-to-back rates; the host sweep, host-link bound, windows, batched, serving, Jacobi, graph
@@ -314,7 +314,7 @@ def _geomean(xs):
 
 
 def summary_ratios(line: dict) -> dict:
-    """The few ratios the study is judged by, each > 1 when the multi-path (or batched) side
+    """The few ratios that sum the study up, each > 1 when the multi-path (or batched) side
     wins: device sweep tuned vs best single path (geometric mean and minimum over sizes,
     messages back to back and single isolated launches),
     host transfers of 64 MiB and more tuned vs best single path per direction, the 64 MiB
