@@ -197,6 +197,20 @@ def workload_config(world: int) -> dict:
             "parallelism": f"replicas x{world}"}
 
 
+def _host_cpu() -> dict:
+    """Host cores and CPU model name (lscpu's, where it exists) for the oracle's rows."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    return {"cores": os.cpu_count(), "model": model}
+
+
 def _size_name(n: int) -> str:
     return f"{n >> 30} GiB" if n >= GiB else f"{n >> 20} MiB"
 
@@ -371,10 +385,13 @@ def headline(line: dict, study_path: str | None = None) -> dict:
         out["e2e"] = {k: v for k, v in out["e2e"].items()
                       if k in ("value", "unit", "h2d_bytes_per_step", "d2h_bytes_per_step", "steps")}
     cpu = out.get("cpu_baseline")
-    if isinstance(cpu, dict) and isinstance(cpu.get("all_cores"), dict):
-        cpu["all_cores"] = {k: cpu["all_cores"].get(k) for k in ("value", "cores")}
+    if isinstance(cpu, dict):
+        cpu.pop("host_cpu", None)
+        if isinstance(cpu.get("all_cores"), dict):
+            cpu["all_cores"] = {k: cpu["all_cores"].get(k) for k in ("value", "cores")}
     if isinstance(out.get("roofline"), dict):
         out["roofline"].pop("launch", None)
+        out["roofline"].pop("frac_of_nominal_7900", None)
     out["summary"] = summary_ratios(line)
     if isinstance(out["summary"].get("batched"), dict):
         out["summary"]["batched"].pop("latency_origin", None)
@@ -779,7 +796,8 @@ def run_ours(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         gbs, el, moved, desc = cpu_oracle_sample({}, budget_s=args.cpu_seconds)
-        cpu = {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc}
+        cpu = {"value": round(gbs, 3), "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": desc,
+               "host_cpu": _host_cpu()}
         if args.cpu_all_cores_seconds > 0:
             g_all, n_all, d_all = cpu_oracle_all_cores(args.cpu_all_cores_seconds)
             cpu["all_cores"] = {"value": round(g_all, 3), "unit": "GB/s", "cores": n_all, "sample": d_all}
@@ -827,6 +845,7 @@ def run_ours(args):
             "config": workload_config(world),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
+                         "frac_of_nominal_7900": round(achieved / 7900.0, 4),
                          "kernel": "k_sm_copy_" + ("bulk" if variant else "vec"),
                          "launch": "1 GiB message, 2 GiB algorithmic HBM bytes", "launch_ms": round(k_ms, 4),
                          "peak_source": f"{peak_kind} hbm_gbs (burst)"},
