@@ -1054,7 +1054,6 @@ def run_batched(mpt, torch, ctx, stream, reps=5):
     xf = mpt.make_xfers([(src[a].data_ptr() + so, dst.data_ptr() + do, sz, mpt.MPT_D2D if a == "dev" else mpt.MPT_H2D)
                          for a, so, do, sz in items])
     total = sum(sizes)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
     dev_lat = []
 
