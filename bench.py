@@ -1525,6 +1525,19 @@ def run_host_sweep(mpt, torch, ctx, stream, max_bytes=2 << 30, reps=3, tune=True
             mpt.mpt_graph_release(g)
         for p in (up, down):
             mpt.mpt_plan_destroy(p)
+        # both directions with one copy-engine node each: plans tuned one direction at a time
+        # need not be the best pair when both directions share the link
+        whole = (n + 15) // 16 * 16
+        up = mpt.mpt_plan(ctx, n, mpt.MPT_H2D, [(mpt.MPT_PATH_CE, 65536, whole)])
+        down = mpt.mpt_plan(ctx, n, mpt.MPT_D2H, [(mpt.MPT_PATH_CE, 65536, whole)])
+        gu = mpt.mpt_capture(ctx, up, dev_a.data_ptr(), host_src.data_ptr())
+        gd = mpt.mpt_capture(ctx, down, host_dst.data_ptr(), dev_b.data_ptr())
+        ms = timed(both, reps if n < (512 << 20) else 1)
+        row["bidir_ce_gbs_per_direction"] = round(n / (ms / 1e3) / 1e9, 2)
+        for g in (gu, gd):
+            mpt.mpt_graph_release(g)
+        for p in (up, down):
+            mpt.mpt_plan_destroy(p)
         rows.append(row)
     ok = bool(torch.equal(host_dst[:1 << 20], dev_b[:1 << 20].cpu())) and bool(torch.equal(dev_a[:1 << 20].cpu(), host_src[:1 << 20]))
     return {"rows": rows, "parity_ok": ok,
