@@ -1538,6 +1538,23 @@ def run_host_sweep(mpt, torch, ctx, stream, max_bytes=2 << 30, reps=3, tune=True
             mpt.mpt_graph_release(g)
         for p in (up, down):
             mpt.mpt_plan_destroy(p)
+        # both directions with plans tuned while the other direction is busy (duplex entries;
+        # below 1 MiB the untuned fallback, one copy-engine chunk)
+        if tune and n >= (1 << 20):
+            for direction in (mpt.MPT_H2D, mpt.MPT_D2H):
+                mpt.mpt_tune(ctx, direction, n, mpt.MPT_MODE_GRAPH | mpt.MPT_MODE_DUPLEX)
+        up = mpt.mpt_plan(ctx, n, mpt.MPT_H2D, None, 16, mpt.MPT_PLAN_DUPLEX)
+        down = mpt.mpt_plan(ctx, n, mpt.MPT_D2H, None, 16, mpt.MPT_PLAN_DUPLEX)
+        gu = mpt.mpt_capture(ctx, up, dev_a.data_ptr(), host_src.data_ptr())
+        gd = mpt.mpt_capture(ctx, down, host_dst.data_ptr(), dev_b.data_ptr())
+        ms = timed(both, reps if n < (512 << 20) else 1)
+        row["bidir_duplex_gbs_per_direction"] = round(n / (ms / 1e3) / 1e9, 2)
+        row["duplex_plans"] = [[(q["kind"], q["share"], q["chunk_bytes"]) for q in mpt.mpt_plan_paths(p)]
+                               for p in (up, down)]
+        for g in (gu, gd):
+            mpt.mpt_graph_release(g)
+        for p in (up, down):
+            mpt.mpt_plan_destroy(p)
         rows.append(row)
     ok = bool(torch.equal(host_dst[:1 << 20], dev_b[:1 << 20].cpu())) and bool(torch.equal(dev_a[:1 << 20].cpu(), host_src[:1 << 20]))
     return {"rows": rows, "parity_ok": ok,

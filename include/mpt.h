@@ -79,9 +79,21 @@ typedef enum { MPT_LAYOUT_CONTIG = 0, MPT_LAYOUT_INTERLEAVE = 1 } mpt_layout;
  * MPT_MODE_PAGEABLE, else zero-copy alone (host-thread staging where the device cannot reach
  * pageable memory). */
 #define MPT_PLAN_PAGEABLE 0x200u
+/* OR into mpt_plan's layout (H2D/D2H, page-locked host memory) when the opposite direction
+ * of the host link carries traffic at the same time (the paper's bidirectional test,
+ * Sec. 5.3): the tuner's entry measured in both directions at once (MPT_MODE_DUPLEX), else
+ * one copy-engine chunk -- one copy-engine node per direction kept both directions at their
+ * shared rate (171.6 GB/s each on GB300) where plans tuned one direction at a time, with
+ * zero-copy shares, reached 147-157 GB/s. */
+#define MPT_PLAN_DUPLEX 0x400u
 typedef enum { MPT_MODE_GRAPH = 0, MPT_MODE_EAGER = 1 } mpt_mode;
 /* OR into mpt_tune's / mpt_tune_get's mode: tune (look up) the pageable-host-memory choice. */
 #define MPT_MODE_PAGEABLE 0x10u
+/* OR into mpt_tune's / mpt_tune_get's mode (H2D/D2H, page-locked): tune (look up) the choice
+ * for a link whose other direction carries equal traffic (the paper's bidirectional test):
+ * each candidate path set runs in both directions at once, the same set mirrored on another
+ * stream, and is timed until both finish. */
+#define MPT_MODE_DUPLEX 0x20u
 
 /* mpt_path_spec.flags for SM-kernel paths: which copy kernel variant to run. */
 #define MPT_SM_VEC128 0u   /* 128-bit vector loads/stores, grid-stride over 64 KiB tiles */

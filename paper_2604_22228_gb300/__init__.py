@@ -17,7 +17,7 @@ import ctypes as C
 
 from . import _ffi
 from ._ffi import (MPT_D2D, MPT_D2H, MPT_H2D, MPT_LAYOUT_CONTIG, MPT_LAYOUT_INTERLEAVE, MPT_MAX_CHUNKS,  # noqa: F401
-                   MPT_NOALLOC_MAX_RANGES, MPT_BULK_CONFIGS, MPT_MAX_PATHS, MPT_PATH_CE, MPT_PATH_HS, MPT_PATH_SM, MPT_PATH_ZC, MPT_SHARE_ONE, MPT_SM_BULK, MPT_SM_TILE8K, MPT_HS_HOST_THREADS, MPT_PLAN_PAGEABLE, MPT_MODE_PAGEABLE, MPT_BATCH_TUNE_TIME, MPT_BATCH_TUNE_P99,
+                   MPT_NOALLOC_MAX_RANGES, MPT_BULK_CONFIGS, MPT_MAX_PATHS, MPT_PATH_CE, MPT_PATH_HS, MPT_PATH_SM, MPT_PATH_ZC, MPT_SHARE_ONE, MPT_SM_BULK, MPT_SM_TILE8K, MPT_HS_HOST_THREADS, MPT_PLAN_PAGEABLE, MPT_MODE_PAGEABLE, MPT_PLAN_DUPLEX, MPT_MODE_DUPLEX, MPT_BATCH_TUNE_TIME, MPT_BATCH_TUNE_P99,
                    MPT_SM_VEC128, MPT_PLAN_EAGER, MPT_MODE_GRAPH, MPT_MODE_EAGER, MPT_PREPARE_GRAPH,
                    MPT_PREPARE_EAGER, MPT_PREPARE_AUTO, STATUS_NAMES)
 from ._ffi import MPT_EAGAIN, MPT_ECUDA, MPT_EINVAL, MPT_ENOMEM, MPT_ENOTSUP, MPT_ETIMEDOUT, MPT_OK  # noqa: F401

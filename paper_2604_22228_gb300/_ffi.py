@@ -23,6 +23,7 @@ MPT_LAYOUT_CONTIG, MPT_LAYOUT_INTERLEAVE = 0, 1
 MPT_SM_VEC128, MPT_SM_BULK, MPT_SM_TILE8K = 0, 1, 2
 MPT_HS_HOST_THREADS = 1
 MPT_PLAN_PAGEABLE, MPT_MODE_PAGEABLE = 0x200, 0x10
+MPT_PLAN_DUPLEX, MPT_MODE_DUPLEX = 0x400, 0x20
 MPT_BATCH_TUNE_TIME, MPT_BATCH_TUNE_P99 = 0, 1
 MPT_PLAN_EAGER = 0x100
 MPT_MODE_GRAPH, MPT_MODE_EAGER = 0, 1

@@ -21,10 +21,13 @@ mpt_status mpt_plan(mpt_ctx_t ctx, uint64_t nbytes, uint32_t dir, const mpt_path
   *out = nullptr;
   mpt_path_spec specs[MPT_MAX_PATHS];
   std::memset(specs, 0, sizeof specs);
-  const uint32_t mode = ((layout & MPT_PLAN_EAGER) ? 1u : 0u) | ((layout & MPT_PLAN_PAGEABLE) ? MPT_MODE_PAGEABLE : 0u);
-  layout &= ~(MPT_PLAN_EAGER | MPT_PLAN_PAGEABLE);
+  const uint32_t mode = ((layout & MPT_PLAN_EAGER) ? 1u : 0u) | ((layout & MPT_PLAN_PAGEABLE) ? MPT_MODE_PAGEABLE : 0u) |
+                       ((layout & MPT_PLAN_DUPLEX) ? MPT_MODE_DUPLEX : 0u);
+  layout &= ~(MPT_PLAN_EAGER | MPT_PLAN_PAGEABLE | MPT_PLAN_DUPLEX);
   if ((mode & MPT_MODE_PAGEABLE) && dir == MPT_D2D)
     return fail(MPT_EINVAL, "mpt_plan: MPT_PLAN_PAGEABLE needs a host side (H2D or D2H)");
+  if ((mode & MPT_MODE_DUPLEX) && (dir == MPT_D2D || (mode & MPT_MODE_PAGEABLE)))
+    return fail(MPT_EINVAL, "mpt_plan: MPT_PLAN_DUPLEX needs a host side in page-locked memory");
   if (paths == nullptr) {
     if (align == 0 || (align & (align - 1)) != 0 || align > MPT_MAX_ALIGN)
       return fail(MPT_EINVAL, "mpt_plan: alignment %u is not a power of two <= %u", align, MPT_MAX_ALIGN);

@@ -161,6 +161,8 @@ struct mpt_ctx_s {
   void* tune_h = nullptr;
   uint64_t tune_host_bytes = 0;
   void* tune_pg = nullptr;            // pageable host buffer (MPT_MODE_PAGEABLE)
+  void* tune_h2 = nullptr;            // page-locked host buffer of the opposite direction (MPT_MODE_DUPLEX)
+  uint64_t tune_h2_bytes = 0;
   uint64_t tune_pg_bytes = 0;
   void* flush = nullptr;              // L2 flush buffer
   uint64_t flush_bytes = 0;

@@ -1000,6 +1000,7 @@ mpt_status mpt_ctx_destroy(mpt_ctx_t c) {
   }
   if (c->fork) cudaEventDestroy(c->fork);
   if (c->d_status) cudaFree(c->d_status);
+  if (c->tune_h2) cudaFreeHost(c->tune_h2);
   if (c->tune_a) cudaFree(c->tune_a);
   if (c->tune_b) cudaFree(c->tune_b);
   if (c->tune_h) cudaFreeHost(c->tune_h);

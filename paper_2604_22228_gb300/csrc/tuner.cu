@@ -238,9 +238,17 @@ mpt_status tuner_fill(mpt_ctx_t ctx, uint64_t nbytes, uint32_t dir, uint32_t mod
   if (!from_env) {
     if (!ctx) return fail(MPT_EINVAL, "mpt_plan: the tuner needs a context (or MPT_PATHS)");
     auto it = ctx->tuned.find(tune_key(dir, mode, size_bucket(nbytes)));
-    if (it != ctx->tuned.end()) e = it->second;
-    else if (mode & MPT_MODE_PAGEABLE) e = pageable_default(ctx, nbytes, align);
-    else e = model_choice(nbytes, dir, mode, align);
+    if (it != ctx->tuned.end()) {
+      e = it->second;
+    } else if (mode & MPT_MODE_PAGEABLE) {
+      e = pageable_default(ctx, nbytes, align);
+    } else if (mode & MPT_MODE_DUPLEX) {  // one copy-engine chunk: the best measured pair
+      e = TuneEntry{};
+      e.npaths = 1;
+      e.paths[0] = mpt_path_spec{MPT_PATH_CE, MPT_SHARE_ONE, std::max<uint64_t>(align, round_up(nbytes, align)), 0, 0};
+    } else {
+      e = model_choice(nbytes, dir, mode, align);
+    }
   }
   for (uint32_t p = 0; p < e.npaths; ++p) e.paths[p].chunk_bytes = std::max<uint64_t>(align, round_up(e.paths[p].chunk_bytes, align));
   if (whole_set) {
@@ -365,8 +373,10 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
                     uint32_t* out_n, double* out_us) {
   if (!c) return fail(MPT_EINVAL, "mpt_tune: NULL context");
   const bool pageable = (mode & MPT_MODE_PAGEABLE) != 0;
+  const bool duplex = (mode & MPT_MODE_DUPLEX) != 0;
   const bool graph_mode = (mode & 1u) == 0;
-  if (dir > MPT_D2H || (mode & ~MPT_MODE_PAGEABLE) > 1 || (pageable && dir == MPT_D2D))
+  if (dir > MPT_D2H || (mode & ~(MPT_MODE_PAGEABLE | MPT_MODE_DUPLEX)) > 1 || (pageable && dir == MPT_D2D) ||
+      (duplex && (dir == MPT_D2D || pageable)))
     return fail(MPT_EINVAL, "mpt_tune: bad direction or mode");
   if (nbytes == 0) return fail(MPT_EINVAL, "mpt_tune: empty message");
   if (reps == 0) reps = nbytes >= (256ull << 20) ? 3 : (nbytes >= (16ull << 20) ? 5 : 11);
@@ -402,36 +412,67 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
     CUDA_TRY(cudaHostAlloc(&c->tune_h, span, cudaHostAllocMapped | cudaHostAllocPortable));
     c->tune_host_bytes = span;
   }
+  if (duplex && c->tune_h2_bytes < span) {  // the opposite direction's host side
+    if (c->tune_h2) cudaFreeHost(c->tune_h2);
+    c->tune_h2 = nullptr;
+    c->tune_h2_bytes = 0;
+    CUDA_TRY(cudaHostAlloc(&c->tune_h2, span, cudaHostAllocPortable));
+    c->tune_h2_bytes = span;
+  }
   st = ensure_dev(c->flush, c->flush_bytes, 256ull << 20);
   if (st != MPT_OK) return st;
   void* host = pageable ? c->tune_pg : c->tune_h;
   void* src = dir == MPT_H2D ? host : c->tune_a;
   void* dst = dir == MPT_D2H ? host : c->tune_b;
+  // duplex: the mirrored plan runs device -> second host buffer beside a host-to-device
+  // candidate, second host buffer -> the device buffer a device-to-host candidate leaves unused
+  void* opp_src = dir == MPT_H2D ? c->tune_a : c->tune_h2;
+  void* opp_dst = dir == MPT_H2D ? c->tune_h2 : c->tune_b;
   cudaStream_t s = c->lane[MPT_MAX_PATHS - 1].s[0];
-  cudaEvent_t e0, e1;
+  cudaStream_t s_opp = c->lane[MPT_MAX_PATHS - 1].s[1];
+  cudaEvent_t e0, e1, e_opp;
   CUDA_TRY(cudaEventCreate(&e0));
   CUDA_TRY(cudaEventCreate(&e1));
+  CUDA_TRY(cudaEventCreateWithFlags(&e_opp, cudaEventDisableTiming));
   TuneEntry best;
   double best_us = 1e30;
   auto region = [&](void* base, uint32_t k) -> void* { return static_cast<uint8_t*>(base) + (uint64_t)k * stride; };
   const char* vv = std::getenv("MPT_TUNE_VERBOSE");
   const bool verbose = vv && *vv && *vv != '0';
   auto measure = [&](const Candidate& k) {
-    mpt_plan_t plan = nullptr;
+    mpt_plan_t plan = nullptr, mirror = nullptr;
     if (mpt_plan(nullptr, nbytes, dir, k.p, k.n, 16, MPT_LAYOUT_CONTIG, &plan) != MPT_OK) return;
-    std::vector<mpt_graph_s> g(graph_mode ? chain : 0);
+    // duplex: the same path set in the opposite direction runs at the same time (the paper's
+    // bidirectional test moves equal messages both ways), and the time is until both finish
+    if (duplex && mpt_plan(nullptr, nbytes, dir == MPT_H2D ? MPT_D2H : MPT_H2D, k.p, k.n, 16, MPT_LAYOUT_CONTIG,
+                           &mirror) != MPT_OK) {
+      mpt_plan_destroy(plan);
+      return;
+    }
+    std::vector<mpt_graph_s> g(graph_mode ? chain : 0), gm(graph_mode && duplex ? chain : 0);
     bool ok = true;
     for (uint32_t k2 = 0; ok && k2 < g.size(); ++k2)
       ok = build_private_graph(c, plan, region(dst, k2), region(src, k2), &g[k2]) == MPT_OK;
+    for (uint32_t k2 = 0; ok && k2 < gm.size(); ++k2)
+      ok = build_private_graph(c, mirror, region(opp_dst, k2), region(opp_src, k2), &gm[k2]) == MPT_OK;
     std::vector<float> ts;
     for (uint32_t r = 0; ok && r < reps + 1; ++r) {
       // write 256 MiB (twice the L2) first, on the timing stream: each run starts with a cold
       // L2 full of dirty lines, as after the kernel that produced the data
       cudaMemsetAsync(c->flush, r & 0xff, c->flush_bytes, s);
       cudaEventRecord(e0, s);
+      if (duplex) cudaStreamWaitEvent(s_opp, e0, 0);
       for (uint32_t k2 = 0; ok && k2 < chain; ++k2) {
         if (graph_mode) ok = g[k2].exec == nullptr || cudaGraphLaunch(g[k2].exec, s) == cudaSuccess;
         else ok = run_eager(c, plan, region(dst, k2), region(src, k2), s) == MPT_OK;
+        if (ok && duplex) {
+          if (graph_mode) ok = gm[k2].exec == nullptr || cudaGraphLaunch(gm[k2].exec, s_opp) == cudaSuccess;
+          else ok = run_eager(c, mirror, region(opp_dst, k2), region(opp_src, k2), s_opp) == MPT_OK;
+        }
+      }
+      if (duplex) {
+        cudaEventRecord(e_opp, s_opp);
+        cudaStreamWaitEvent(s, e_opp, 0);
       }
       cudaEventRecord(e1, s);
       if (cudaEventSynchronize(e1) != cudaSuccess) ok = false;
@@ -440,7 +481,9 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
       if (r > 0) ts.push_back(ms / (float)chain);  // the first run warms up
     }
     for (mpt_graph_s& gk : g) free_private_graph(&gk);
+    for (mpt_graph_s& gk : gm) free_private_graph(&gk);
     mpt_plan_destroy(plan);
+    if (mirror) mpt_plan_destroy(mirror);
     if (!ok || ts.empty()) {
       cudaGetLastError();
       return;
@@ -482,6 +525,7 @@ mpt_status mpt_tune(mpt_ctx_t c, uint32_t dir, uint64_t nbytes, uint32_t mode, u
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaEventDestroy(e_opp);
   if (best.npaths == 0) return fail(MPT_ECUDA, "mpt_tune: no candidate ran");
   mpt_status dev = mpt_ctx_status(c, nullptr);
   if (dev != MPT_OK) return dev;
@@ -532,7 +576,8 @@ mpt_status mpt_tune_load(mpt_ctx_t c, const char* path) {
     }
     if (n == 0) continue;
     const uint32_t lmode = (uint32_t)v[1];
-    if (n < 10 || (n - 5) % 5 != 0 || v[0] > 2 || (lmode & ~MPT_MODE_PAGEABLE) > 1 || v[2] > 63) {
+    if (n < 10 || (n - 5) % 5 != 0 || v[0] > 2 || (lmode & ~(MPT_MODE_PAGEABLE | MPT_MODE_DUPLEX)) > 1 ||
+        v[2] > 63) {
       std::fclose(f);
       return fail(MPT_EINVAL, "mpt_tune_load: %s line %u is not a tuner entry", path, lineno);
     }

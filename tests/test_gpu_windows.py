@@ -118,3 +118,49 @@ def test_host_to_device_and_device_to_host_at_once(ctx, pathset, mode):
             mpt.mpt_plan_destroy(p)
     st, site = mpt.mpt_ctx_status(ctx)
     assert st == mpt.MPT_OK, f"status {st} site {site}"
+
+
+def test_duplex_plans_tuned_under_opposite_traffic(ctx):
+    """Plans tuned while the other link direction is busy (MPT_MODE_DUPLEX), used for an H2D and
+    a D2H transfer at once: the plan flag picks the tuned entry, an untuned size falls back to
+    one copy-engine chunk, and both destinations equal the oracle's copies."""
+    import torch
+    n = 32 * MiB + 48
+    # an untuned bucket: one copy-engine chunk covering the message
+    try:
+        mpt.mpt_tune_get(ctx, mpt.MPT_H2D, 3 * MiB, mpt.MPT_MODE_GRAPH | mpt.MPT_MODE_DUPLEX)
+        untuned = False
+    except mpt.MptError as e:
+        untuned = e.status == mpt.MPT_EAGAIN
+    if untuned:
+        p = mpt.mpt_plan(ctx, 3 * MiB, mpt.MPT_H2D, None, 16, mpt.MPT_PLAN_DUPLEX)
+        assert [(q["kind"], q["share"]) for q in mpt.mpt_plan_paths(p)] == [(CE, 65536)]
+        assert len(mpt.mpt_plan_chunks(p)) == 1
+        mpt.mpt_plan_destroy(p)
+    tuned = {}
+    for direction in (mpt.MPT_H2D, mpt.MPT_D2H):
+        paths, us = mpt.mpt_tune(ctx, direction, n, mpt.MPT_MODE_GRAPH | mpt.MPT_MODE_DUPLEX, 3)
+        assert paths and us > 0
+        got, _ = mpt.mpt_tune_get(ctx, direction, n, mpt.MPT_MODE_GRAPH | mpt.MPT_MODE_DUPLEX)
+        assert [tuple(x.values())[:2] for x in got] == [tuple(x.values())[:2] for x in paths]
+        tuned[direction] = paths
+    h_src, d_dst = Buf(n, "host"), Buf(n, "dev")
+    d_src, h_dst = Buf(n, "dev"), Buf(n, "host")
+    up = mpt.mpt_plan(ctx, n, mpt.MPT_H2D, None, 16, mpt.MPT_PLAN_DUPLEX)
+    down = mpt.mpt_plan(ctx, n, mpt.MPT_D2H, None, 16, mpt.MPT_PLAN_DUPLEX)
+    assert [q["kind"] for q in mpt.mpt_plan_paths(up)] == [q["kind"] for q in tuned[mpt.MPT_H2D]]
+    hu = mpt.mpt_capture(ctx, up, d_dst.ptr, h_src.ptr)
+    hd = mpt.mpt_capture(ctx, down, h_dst.ptr, d_src.ptr)
+    try:
+        a, b = seeded("u32", 0x99001, n), seeded("u32", 0x99002, n)
+        h_src.fill(a)
+        d_src.fill(b)
+        _launch_together([hu, hd], [torch.cuda.Stream(), torch.cuda.Stream()])
+        assert np.array_equal(d_dst.numpy(), T.copy(a))
+        assert np.array_equal(h_dst.numpy(), T.copy(b))
+        assert d_dst.guards_intact() and h_dst.guards_intact()
+    finally:
+        for h in (hu, hd):
+            mpt.mpt_graph_release(h)
+        for q in (up, down):
+            mpt.mpt_plan_destroy(q)

@@ -104,3 +104,16 @@ def test_host_thread_staging_is_host_link_only():
     with pytest.raises(mpt.MptError) as e:
         lib_plan(4096, P.D2D, [(P.HS, 65536, 1024, 0, mpt.MPT_HS_HOST_THREADS)])
     assert e.value.status == mpt.MPT_EINVAL
+
+
+def test_duplex_flag_needs_a_host_side_and_a_context():
+    import paper_2604_22228_gb300 as mpt
+    with pytest.raises(mpt.MptError) as e:  # device-to-device has no link direction to share
+        mpt.mpt_plan(None, 1 << 20, mpt.MPT_D2D, None, 16, mpt.MPT_PLAN_DUPLEX)
+    assert e.value.status == mpt.MPT_EINVAL
+    with pytest.raises(mpt.MptError) as e:  # pageable memory is not the duplex case
+        mpt.mpt_plan(None, 1 << 20, mpt.MPT_H2D, None, 16, mpt.MPT_PLAN_DUPLEX | mpt.MPT_PLAN_PAGEABLE)
+    assert e.value.status == mpt.MPT_EINVAL
+    with pytest.raises(mpt.MptError) as e:  # the tuned choice needs a context
+        mpt.mpt_plan(None, 1 << 20, mpt.MPT_H2D, None, 16, mpt.MPT_PLAN_DUPLEX)
+    assert e.value.status == mpt.MPT_EINVAL
