@@ -423,8 +423,11 @@ MPT_API mpt_status mpt_tune_get(mpt_ctx_t ctx, uint32_t dir, uint64_t nbytes, ui
 /* Size the context's batch ring: `slots` batches in flight at once (default 4), up to
  * `max_xfers` transfers per batch (default 4096), `ctas` CTAs of the batch kernel
  * (default 3 x SMs) and `tile_bytes` per work item (default 256 KiB; >= 4096, multiple of
- * 16).  0 keeps a default.  Waits for the device; fails with EAGAIN while a batch is held.
- * The ring is built on first use with defaults when this is never called. */
+ * 16).  tile_bytes is the largest tile: a batch whose kernel-moved bytes give each CTA less
+ * than one tile is cut into the power of two at or above its bytes per CTA (at least
+ * 32 KiB), so that a short batch spreads over the grid.  0 keeps a default.  Waits for the
+ * device; fails with EAGAIN while a batch is held.  The ring is built on first use with
+ * defaults when this is never called. */
 MPT_API mpt_status mpt_batch_configure(mpt_ctx_t ctx, uint32_t slots, uint32_t max_xfers, uint32_t ctas,
                                        uint32_t tile_bytes);
 
@@ -481,7 +484,9 @@ MPT_API mpt_status mpt_batch_register(mpt_ctx_t ctx, const void* base, uint64_t 
  * Each xfer: D2D (device -> device), H2D (page-locked host -> device, read over the host
  * link by the kernel) or D2H (device -> page-locked host).  Destinations must not overlap
  * (Sec. 4.5: each transfer owns its region).  The descriptor table is copied into the
- * slot, so `xfers` may be reused on return.  *out is owned by the caller until
+ * slot, so `xfers` may be reused on return; the replay copies only the table's used bytes
+ * to the device (a few hundred for a short batch) and the kernel resets its own counters,
+ * so a one-transfer batch is one small copy and one kernel.  *out is owned by the caller until
  * mpt_batch_release, which frees the slot.  Errors: EINVAL (bad descriptor, overlapping
  * destinations, n outside 1..max_xfers), EAGAIN (every slot held), ECUDA. */
 MPT_API mpt_status mpt_batch_submit(mpt_ctx_t ctx, const mpt_xfer* xfers, size_t n, void* stream, mpt_batch_t* out);
@@ -580,7 +585,10 @@ MPT_API uint64_t mpt_now_ns(void);
  * and the batch kernel one CTA per SM, so a batch of short requests runs beside an earlier
  * batch with a long one instead of behind it (on GB300 at 50k requests/s: p50 49 us against
  * 152 us in order, p99 from submit 572 us against 1.19 ms); requests in flight are then
- * unordered and must not share destination bytes. */
+ * unordered and must not share destination bytes.  An idle worker spins on the arrival
+ * flag for MPT_SERVE_SPIN_US microseconds (default 2000; 0 = block at once) after its last
+ * work before it blocks, so a request after a short gap is not delayed by a thread wake-up
+ * (one core busy while the server is active). */
 MPT_API mpt_status mpt_serve_start(mpt_ctx_t ctx, const mpt_serve_config* cfg, mpt_server_t* out);
 
 /* Enqueue one request (thread-safe).  arrival_ns: the request's scheduled arrival on the

@@ -12,9 +12,12 @@
 //
 // Each context owns a ring of batch slots.  A slot holds the page-locked and device copies
 // of its table, its counters and flags, and one instantiated graph
-//   [table host->device copy] + [counter reset] -> [batch kernel]
-// whose parameters never change: the descriptor count lives in the table header, so any
-// batch up to the slot capacity replays the same graph.
+//   [table host->device copy] -> [batch kernel]
+// The descriptor count lives in the table header, so any batch up to the slot capacity
+// replays the same graph; only the copy's size follows the batch (the table is packed, so
+// a short batch copies a few hundred bytes).  The kernel leaves its counters at zero when
+// it ends, so no reset node runs between replays: a one-request batch costs one small copy
+// and one kernel.
 #include <algorithm>
 #include <iterator>
 #include <chrono>
@@ -49,6 +52,7 @@ template <bool kAny>
 __device__ __forceinline__ void batch_body(const BatchArgs& a) {
   __shared__ uint32_t s_item;
   const BatchHeader h = *a.hdr;
+  const uint32_t* order = reinterpret_cast<const uint32_t*>(a.desc + h.n);
   if (threadIdx.x == 0) {
     const uint64_t t = now_ns();
     atomicMax(a.start_inv, ~t);
@@ -91,10 +95,10 @@ __device__ __forceinline__ void batch_body(const BatchArgs& a) {
     uint32_t lo = link ? 0 : h.n_link, hi = (link ? h.n_link : h.n_tiled) - 1;
     while (lo < hi) {
       const uint32_t mid = (lo + hi + 1) >> 1;
-      if (a.desc[a.order[mid]].first_tile <= item) lo = mid;
+      if (a.desc[order[mid]].first_tile <= item) lo = mid;
       else hi = mid - 1;
     }
-    lo = a.order[lo];
+    lo = order[lo];
     const BatchDesc d = a.desc[lo];
     const uint64_t off = (uint64_t)(item - d.first_tile) * h.tile_bytes;
     if (off < d.bytes) {
@@ -114,7 +118,21 @@ __device__ __forceinline__ void batch_body(const BatchArgs& a) {
         a.times[lo] = now_ns();
         __threadfence_system();
         asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(a.host_flags + lo), "r"(h.epoch) : "memory");
+        a.done[lo] = 0;  // every tile of lo is counted: no CTA of this launch touches it again
       }
+    }
+  }
+  if (threadIdx.x == 0) {
+    __threadfence();
+    // the last CTA out: every CTA has stopped claiming, so the cursors and the start
+    // counters can go back to zero for the slot's next launch
+    if (atomicAdd(a.exited, 1u) == gridDim.x - 1) {
+      *a.start_out = atomicExch(a.start_inv, 0ull);
+      *a.cursor = 0;
+      *a.cursor_dev = 0;
+      *a.started = 0;
+      __threadfence();
+      *a.exited = 0;
     }
   }
 }
@@ -136,6 +154,7 @@ namespace {
 constexpr uint32_t kDefaultSlots = 4;
 constexpr uint32_t kDefaultMaxXfers = 4096;
 constexpr uint32_t kDefaultTile = 256 * 1024;
+constexpr uint64_t kMinAdaptiveTile = 32 * 1024;  // smallest tile a short batch is cut into
 constexpr uint32_t kDmaDirs = 3;  // lanes per direction: D2D, H2D, D2H
 
 uint64_t host_ns() {
@@ -165,14 +184,17 @@ mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t cta
   s.dma_lanes = c->batch_dma_lanes;
   s.dma_items = c->batch_dma_lanes ? c->batch_dma_items : 0;
   const uint32_t ndma = kDmaDirs * s.dma_lanes * s.dma_items;
-  const size_t map_off = sizeof(BatchHeader) + (size_t)max_xfers * sizeof(BatchDesc);
-  const size_t order_off = map_off + (size_t)ndma * sizeof(uint32_t);
-  s.table_bytes = order_off + (size_t)max_xfers * sizeof(uint32_t);
+  // table: header | lane map[ndma] | desc[n] | order[n] (BatchArgs): a batch copies its first
+  // desc_off + n * 44 bytes
+  const size_t map_off = sizeof(BatchHeader);
+  s.desc_off = (map_off + (size_t)ndma * sizeof(uint32_t) + 15) & ~(size_t)15;
+  s.table_bytes = s.desc_off + (size_t)max_xfers * (sizeof(BatchDesc) + sizeof(uint32_t));
   CUDA_TRY(cudaHostAlloc(&s.h_table, s.table_bytes, cudaHostAllocPortable));
   CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&s.h_flags), (size_t)max_xfers * sizeof(uint32_t),
                          cudaHostAllocMapped | cudaHostAllocPortable));
   std::memset(s.h_flags, 0, (size_t)max_xfers * sizeof(uint32_t));
-  // device block: table | ctrl (cursor, start) | done[max] | times[max]
+  // device block: table | ctrl (cursors, start, counters) | done[max] | times[max]; zeroed
+  // here once, kept zero between launches by the kernel
   const size_t ctrl_off = (s.table_bytes + 255) & ~(size_t)255;
   s.ctrl_bytes = 256 + (size_t)max_xfers * sizeof(uint32_t);
   const size_t times_off = (ctrl_off + s.ctrl_bytes + 255) & ~(size_t)255;
@@ -184,20 +206,20 @@ mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t cta
   s.d_times = reinterpret_cast<unsigned long long*>(base + times_off);
   CUDA_TRY(cudaMemset(s.d_mem, 0, scratch_off + 256));
   s.h_dma_map = reinterpret_cast<uint32_t*>(s.h_table + map_off);
-  s.h_order = reinterpret_cast<uint32_t*>(s.h_table + order_off);
   for (uint32_t k = 0; k < ndma; ++k) s.h_dma_map[k] = ~0u;
   if (ndma) CUDA_TRY(cudaHostAlloc(&s.h_scratch, 64, cudaHostAllocPortable));
   uint8_t* d_scratch = base + scratch_off;
   const uint32_t* d_map = reinterpret_cast<const uint32_t*>(s.d_table + map_off);
   CUDA_TRY(cudaEventCreateWithFlags(&s.done_ev, cudaEventDisableTiming));
   s.args.hdr = reinterpret_cast<const BatchHeader*>(s.d_table);
-  s.args.desc = reinterpret_cast<const BatchDesc*>(s.d_table + sizeof(BatchHeader));
-  s.args.order = reinterpret_cast<const uint32_t*>(s.d_table + order_off);
+  s.args.desc = reinterpret_cast<const BatchDesc*>(s.d_table + s.desc_off);
   s.args.cursor = reinterpret_cast<uint32_t*>(s.d_ctrl);
   s.args.cursor_dev = reinterpret_cast<uint32_t*>(s.d_ctrl + 24);
   s.args.start_inv = reinterpret_cast<unsigned long long*>(s.d_ctrl + 8);
+  s.args.start_out = reinterpret_cast<unsigned long long*>(s.d_ctrl + 32);
   s.args.done = reinterpret_cast<uint32_t*>(s.d_ctrl + 256);
   s.args.started = reinterpret_cast<uint32_t*>(s.d_ctrl + 16);
+  s.args.exited = reinterpret_cast<uint32_t*>(s.d_ctrl + 20);
   CUDA_TRY(cudaHostAlloc(reinterpret_cast<void**>(&s.h_stamps), 2 * sizeof(unsigned long long),
                          cudaHostAllocMapped | cudaHostAllocPortable));
   s.h_stamps[0] = s.h_stamps[1] = 0;
@@ -206,20 +228,16 @@ mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t cta
   uint32_t* hf_dev = nullptr;
   CUDA_TRY(cudaHostGetDevicePointer(reinterpret_cast<void**>(&hf_dev), s.h_flags, 0));
   s.args.host_flags = hf_dev;
-  // graphs: table copy and counter reset, then the kernel (aligned-only or any alignment)
+  // graphs: the table copy, then the kernel (aligned-only or any alignment); the copy's size
+  // follows the batch (mpt_batch_submit)
   for (int gi = 0; gi < 2; ++gi) {
     CUDA_TRY(cudaGraphCreate(&s.graph[gi], 0));
-    cudaGraphNode_t cp, ms, kn;
+    cudaGraphNode_t cp, kn;
     CUDA_TRY(cudaGraphAddMemcpyNode1D(&cp, s.graph[gi], nullptr, 0, s.d_table, s.h_table, s.table_bytes,
                                       cudaMemcpyHostToDevice));
-    cudaMemsetParams mp{};
-    mp.dst = s.d_ctrl;
-    mp.value = 0;
-    mp.elementSize = 1;
-    mp.width = s.ctrl_bytes;
-    mp.height = 1;
-    CUDA_TRY(cudaGraphAddMemsetNode(&ms, s.graph[gi], nullptr, 0, &mp));
-    cudaGraphNode_t deps[2] = {cp, ms};
+    s.table_cp[gi] = cp;
+    s.table_cp_bytes[gi] = s.table_bytes;
+    cudaGraphNode_t deps[1] = {cp};
     void* params[] = {&s.args};
     cudaKernelNodeParams kp{};
     kp.func = gi == 0 ? reinterpret_cast<void*>(&k_batch) : reinterpret_cast<void*>(&k_batch_any);
@@ -227,7 +245,7 @@ mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t cta
     kp.gridDim = dim3(gi == 0 ? ctas : std::min<uint32_t>(ctas, 2u * (uint32_t)c->sms));
     kp.blockDim = dim3(kVecThreads);
     kp.kernelParams = params;
-    CUDA_TRY(cudaGraphAddKernelNode(&kn, s.graph[gi], deps, 2, &kp));
+    CUDA_TRY(cudaGraphAddKernelNode(&kn, s.graph[gi], deps, 1, &kp));
     // DMA lanes beside the kernel: per direction, chains of memcpy -> completion kernel.
     // Instantiation-time operands are scratch buffers of the lane's memory kinds (a
     // retargeted memcpy node keeps the kinds it was built with).
@@ -244,7 +262,7 @@ mpt_status slot_init(mpt_ctx_t c, BatchSlot& s, uint32_t max_xfers, uint32_t cta
           if (prev) {
             CUDA_TRY(cudaGraphAddMemcpyNode1D(&cn, s.graph[gi], &prev, 1, to, from, 16, cudaMemcpyDefault));
           } else {
-            CUDA_TRY(cudaGraphAddMemcpyNode1D(&cn, s.graph[gi], deps, 2, to, from, 16, cudaMemcpyDefault));
+            CUDA_TRY(cudaGraphAddMemcpyNode1D(&cn, s.graph[gi], deps, 1, to, from, 16, cudaMemcpyDefault));
           }
           uint32_t it = item;
           void* fparams[] = {&s.args, const_cast<uint32_t**>(&d_map), &it};
@@ -519,9 +537,11 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
   BatchSlot& s = c->slots[si];
   // validate: direction, memory kinds, and non-overlapping destinations (Sec. 4.5: each
   // transfer owns its destination region)
-  std::vector<std::pair<uint64_t, uint64_t>> spans;
-  spans.reserve(n);
-  std::vector<uint32_t> dma_cand;  // entries large enough for a copy-engine lane
+  // scratch owned by the context (one thread per context): no allocation per batch
+  std::vector<std::pair<uint64_t, uint64_t>>& spans = c->batch_spans;
+  spans.clear();
+  std::vector<uint32_t>& dma_cand = c->batch_cand;  // entries large enough for a copy-engine lane
+  dma_cand.clear();
   for (size_t i = 0; i < n; ++i) {
     const mpt_xfer& x = xfers[i];
     int ks, kd;
@@ -551,11 +571,13 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
   s.epoch++;
   if (s.epoch == 0) s.epoch = 1;
   BatchHeader* h = reinterpret_cast<BatchHeader*>(s.h_table);
-  BatchDesc* d = reinterpret_cast<BatchDesc*>(s.h_table + sizeof(BatchHeader));
+  BatchDesc* d = reinterpret_cast<BatchDesc*>(s.h_table + s.desc_off);
+  uint32_t* order = reinterpret_cast<uint32_t*>(d + n);
   // DMA lanes: largest eligible entries first, each to the least-loaded lane of its
   // direction with a free item (longest-processing-time order); the rest stay with the kernel
   const uint32_t ndma = kDmaDirs * s.dma_lanes * s.dma_items;
-  std::vector<uint8_t> to_dma(n, 0);
+  std::vector<uint8_t>& to_dma = c->batch_to_dma;
+  to_dma.assign(n, 0);
   for (uint32_t k = 0; k < ndma; ++k) s.h_dma_map[k] = ~0u;
   if (!dma_cand.empty()) {
     std::sort(dma_cand.begin(), dma_cand.end(),
@@ -578,16 +600,35 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
   }
   // tiles numbered within two classes, link (a host side) and device, each descriptor's
   // tiles contiguous in its class; order lists the descriptors with tiles, link class first
-  uint64_t tiles[2] = {0, 0};  // [0] link, [1] device
-  const uint64_t tile = c->batch_tile;
   bool any_shift = false;
+  uint64_t kernel_bytes = 0;
+  for (size_t i = 0; i < n; ++i) {
+    if (to_dma[i]) continue;
+    const mpt_xfer& x = xfers[i];
+    any_shift |= (((uintptr_t)x.src ^ (uintptr_t)x.dst) & 15) != 0 && x.bytes >= 16;
+    kernel_bytes += x.bytes;
+  }
+  const int gi = any_shift ? 1 : 0;
+  const uint32_t ctas = c->batch_ctas ? c->batch_ctas : 3u * (uint32_t)c->sms;
+  const uint32_t grid = gi == 0 ? ctas : std::min<uint32_t>(ctas, 2u * (uint32_t)c->sms);  // as slot_init
+  // tile size: the configured one, unless the batch is too small to give every CTA a full
+  // tile; then the power of two at or above the kernel's bytes per CTA, at least 32 KiB (a
+  // CTA moves 32 KiB per round of loads), so that a short batch spreads over the grid
+  // instead of queueing its bytes behind a few CTAs
+  uint64_t tile = c->batch_tile;
+  {
+    const uint64_t per_cta = (kernel_bytes + grid - 1) / grid;
+    uint64_t t = kMinAdaptiveTile;
+    while (t < per_cta) t <<= 1;
+    tile = std::min<uint64_t>(tile, t);
+  }
+  uint64_t tiles[2] = {0, 0};  // [0] link, [1] device
   uint32_t n_link = 0, n_dev = 0;
   for (size_t i = 0; i < n; ++i) {
     const mpt_xfer& x = xfers[i];
     const uint32_t fl = (x.dir == MPT_D2H ? kDescHostDst : 0u) | (x.dir != MPT_D2D ? kDescHostSide : 0u) |
                         (to_dma[i] ? kDescDma : 0u);
     const uint64_t t = to_dma[i] ? 0 : std::max<uint64_t>(1, (x.bytes + tile - 1) / tile);
-    if (!to_dma[i]) any_shift |= (((uintptr_t)x.src ^ (uintptr_t)x.dst) & 15) != 0 && x.bytes >= 16;
     // one class for everything when the split is off
     const int cls = (c->batch_split && x.dir == MPT_D2D) ? 1 : 0;
     d[i] = BatchDesc{(uint64_t)(uintptr_t)x.src, (uint64_t)(uintptr_t)x.dst, x.bytes, (uint32_t)tiles[cls],
@@ -602,12 +643,9 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
     for (size_t i = 0; i < n; ++i) {
       if (!d[i].ntiles) continue;
       const bool dev = c->batch_split && xfers[i].dir == MPT_D2D;
-      s.h_order[dev ? di++ : li++] = (uint32_t)i;
+      order[dev ? di++ : li++] = (uint32_t)i;
     }
   }
-  const int gi = any_shift ? 1 : 0;
-  const uint32_t ctas = c->batch_ctas ? c->batch_ctas : 3u * (uint32_t)c->sms;
-  const uint32_t grid = gi == 0 ? ctas : std::min<uint32_t>(ctas, 2u * (uint32_t)c->sms);  // as slot_init
   uint32_t link_ctas = grid;  // split off, or no device tiles: every CTA on the one class
   if (c->batch_split && tiles[0] && tiles[1])
     link_ctas = c->batch_link_ctas ? std::min(c->batch_link_ctas, grid) : std::max(1u, grid / 3);
@@ -623,6 +661,19 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
       CUDA_TRY(cudaGraphNodeSetEnabled(s.exec[gi], s.dma_cp[gi][k], want));
       CUDA_TRY(cudaGraphNodeSetEnabled(s.exec[gi], s.dma_fin[gi][k], want));
       s.dma_on[gi][k] = want;
+    }
+  }
+  // copy the used part of the table, rounded up to a power of two (at least 256 bytes) so
+  // that batches of similar length reuse the node's size without an update
+  {
+    const size_t used = s.desc_off + n * (sizeof(BatchDesc) + sizeof(uint32_t));
+    size_t want = 256;
+    while (want < used) want <<= 1;
+    want = std::min(want, s.table_bytes);
+    if (want != s.table_cp_bytes[gi]) {
+      CUDA_TRY(cudaGraphExecMemcpyNodeSetParams1D(s.exec[gi], s.table_cp[gi], s.d_table, s.h_table, want,
+                                                  cudaMemcpyHostToDevice));
+      s.table_cp_bytes[gi] = want;
     }
   }
   const cudaStream_t cs = static_cast<cudaStream_t>(stream);
@@ -678,7 +729,7 @@ mpt_status mpt_batch_times(mpt_batch_t b, uint64_t* out_ns) {
   std::vector<unsigned long long> t(b->n + 1);
   unsigned long long start_inv = 0;
   CUDA_TRY(cudaMemcpy(t.data(), s.d_times, b->n * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
-  CUDA_TRY(cudaMemcpy(&start_inv, s.args.start_inv, sizeof start_inv, cudaMemcpyDeviceToHost));
+  CUDA_TRY(cudaMemcpy(&start_inv, s.args.start_out, sizeof start_inv, cudaMemcpyDeviceToHost));
   const unsigned long long start = ~start_inv;
   for (size_t i = 0; i < b->n; ++i) out_ns[i] = t[i] >= start ? t[i] - start : 0;
   return MPT_OK;

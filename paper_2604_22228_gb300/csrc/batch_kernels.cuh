@@ -36,17 +36,26 @@ struct BatchDesc {
   uint32_t pad;
 };
 
+// Device table of one batch, packed so that a batch of n descriptors is one copy of its
+// first bytes: header | DMA-lane map | desc[n] | order[n], where order lists the
+// descriptors with tiles, link class first (its address follows from n).
+//
+// The launch counters (cursors, per-descriptor tile counts, started and exited CTAs, the
+// start time) are zero when a launch begins and the kernel leaves them zero: the CTA that
+// counts a descriptor's last tile clears that descriptor's count, and the last CTA to exit,
+// once no CTA can claim any more, clears the rest.  No reset node runs between launches.
 struct BatchArgs {
   const BatchHeader* hdr;
-  const BatchDesc* desc;
-  const uint32_t* order;         // descriptor indices with tiles: the link class, then the device class
-  uint32_t* cursor;              // next link tile to claim (reset to 0 per launch)
-  uint32_t* cursor_dev;          // next device tile to claim (reset to 0 per launch)
-  unsigned long long* start_inv; // ~(kernel start time), max over CTAs
-  uint32_t* done;                // tiles finished per descriptor (reset per launch)
+  const BatchDesc* desc;         // desc[0..n); order[0..n) follows it
+  uint32_t* cursor;              // next link tile to claim
+  uint32_t* cursor_dev;          // next device tile to claim
+  unsigned long long* start_inv; // ~(kernel start time), max over CTAs, during a launch
+  unsigned long long* start_out; // the launch's ~(start time), kept after the launch
+  uint32_t* done;                // tiles finished per descriptor
   unsigned long long* times;     // completion time per descriptor (global timer, ns)
   uint32_t* host_flags;          // device alias of page-locked flags, one per descriptor
-  uint32_t* started;             // CTAs that have started (reset to 0 per launch)
+  uint32_t* started;             // CTAs that have started
+  uint32_t* exited;              // CTAs that have stopped claiming
   unsigned long long* host_stamps;  // device alias of page-locked [first, last] CTA start times
 };
 

@@ -5,6 +5,7 @@
 #include <memory>
 #include <unordered_map>
 #include <unordered_set>
+#include <utility>
 #include <vector>
 
 #include "host_pool.h"
@@ -62,7 +63,8 @@ struct Arena {
 struct BatchSlot {
   uint32_t max_xfers = 0;
   size_t table_bytes = 0, ctrl_bytes = 0;
-  uint8_t* h_table = nullptr;   // page-locked table, copied to d_table by the graph
+  size_t desc_off = 0;          // descriptors' offset in the table (after header and lane map)
+  uint8_t* h_table = nullptr;   // page-locked table, its used part copied to d_table by the graph
   uint32_t* h_flags = nullptr;  // page-locked, mapped: per-descriptor completion epochs
   unsigned long long* h_stamps = nullptr;  // page-locked, mapped: first and last CTA start
   void* d_mem = nullptr;
@@ -72,6 +74,8 @@ struct BatchSlot {
   BatchArgs args{};
   cudaGraph_t graph[2] = {nullptr, nullptr};      // [0] k_batch, [1] k_batch_any
   cudaGraphExec_t exec[2] = {nullptr, nullptr};
+  cudaGraphNode_t table_cp[2] = {nullptr, nullptr};  // the table copy node of each graph
+  size_t table_cp_bytes[2] = {0, 0};                 // and the size it copies now
   cudaEvent_t done_ev = nullptr;
   cudaEvent_t t0_ev = nullptr, t1_ev = nullptr;  // timing events around the replay (batch_timing)
   uint32_t epoch = 0;
@@ -84,7 +88,6 @@ struct BatchSlot {
   // others disabled (no cost when no entry is large).
   uint32_t dma_lanes = 0, dma_items = 0;
   uint32_t* h_dma_map = nullptr;  // in the page-locked table: item -> descriptor (~0 unused)
-  uint32_t* h_order = nullptr;    // in the page-locked table: descriptors with tiles, link class first
   std::vector<cudaGraphNode_t> dma_cp[2], dma_fin[2];
   std::vector<uint8_t> dma_on[2];
   void* h_scratch = nullptr;      // page-locked 64 bytes: instantiation-time operand of host lanes
@@ -170,6 +173,10 @@ struct mpt_ctx_s {
   std::vector<mpt::BatchSlot> slots;
   std::vector<mpt::Arena> arenas;
   uint32_t batch_slots = 0, batch_max_xfers = 0, batch_ctas = 0, batch_tile = 0;
+  // mpt_batch_submit's per-batch scratch, kept to avoid allocating per batch
+  std::vector<std::pair<uint64_t, uint64_t>> batch_spans;
+  std::vector<uint32_t> batch_cand;
+  std::vector<uint8_t> batch_to_dma;
   uint32_t batch_dma_lanes = 0, batch_dma_items = 0;  // per direction; items per lane
   uint64_t batch_dma_min = 0;                         // smallest entry a DMA lane takes
   bool batch_dma_set = false;                         // configured (else environment defaults)

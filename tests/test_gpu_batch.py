@@ -239,3 +239,57 @@ def test_batch_full_size_workload(ctx):
     for i, (a, s, d, sz) in enumerate(items):
         p = s % period
         assert np.array_equal(out[d:d + sz], T.copy(ext[p:p + sz])), (i, a, s, d, sz)
+
+
+# one transfer per batch around the tile boundaries: below the configured 256 KiB tile a
+# batch is cut into power-of-two tiles of at least 32 KiB spread over the grid (456 CTAs
+# aligned, 304 for the general kernel), above it into the configured tile
+TILE_EDGE_SIZES = [1, 15, 16, 17, 32 * 1024 - 1, 32 * 1024, 32 * 1024 + 1, 456 * 32 * 1024 - 16,
+                   456 * 32 * 1024 + 16, 304 * 64 * 1024 + 7, 456 * 256 * 1024 + 48, 8 * MiB + 3, 64 * MiB + 5]
+
+
+@pytest.mark.parametrize("direction", [mpt.MPT_D2D, mpt.MPT_H2D, mpt.MPT_D2H], ids=["d2d", "h2d", "d2h"])
+@pytest.mark.parametrize("offsets", [(0, 0), (3, 11)], ids=["aligned", "shifted"])
+def test_batch_tile_sizes_follow_the_batch(ctx, direction, offsets):
+    """A lone transfer of every size around the tile boundaries, its source and destination
+    aligned or not, equals the oracle's copy with the guard bytes untouched."""
+    from gpu_util import Buf, seeded
+    where = {mpt.MPT_D2D: ("dev", "dev"), mpt.MPT_H2D: ("host", "dev"), mpt.MPT_D2H: ("dev", "host")}[direction]
+    for k, n in enumerate(TILE_EDGE_SIZES):
+        src, dst = Buf(n, where[0], offsets[0]), Buf(n, where[1], offsets[1])
+        data = seeded("u8", 0xB0000 + 32 * k + direction, n)
+        src.fill(data)
+        b = mpt.mpt_batch_submit(ctx, [(src.ptr, dst.ptr, n, direction)])
+        mpt.mpt_batch_wait(b)
+        done, _ = mpt.mpt_batch_poll(b, 1)
+        mpt.mpt_batch_release(b)
+        assert done == 1, n
+        assert np.array_equal(dst.numpy(), T.copy(data)), n
+        assert dst.guards_intact(), n
+    st, site = mpt.mpt_ctx_status(ctx)
+    assert st == mpt.MPT_OK, (st, site)
+
+
+def test_batch_counters_reset_across_replays(ctx):
+    """The kernel leaves its cursors and tile counts at zero for the next replay of its slot
+    (no reset node runs between replays): batches of one to three transfers and batches of
+    hundreds alternate on the same slot, aligned and packed, and every one of them equals
+    the oracle with every flag raised and a completion time from its own launch."""
+    import torch
+    s = torch.cuda.current_stream()
+    for rep in range(12):
+        small = rep % 2 == 0
+        n = 1 + rep % 3 if small else 200 + 50 * (rep % 3)
+        w = Workload(n, 0xC000 + rep, MiB if small else 2 * MiB, align=16 if rep % 4 < 2 else 1)
+        b = mpt.mpt_batch_submit(ctx, w.xfers, s)
+        mpt.mpt_batch_wait(b)
+        done, flags = mpt.mpt_batch_poll(b, n)
+        times = mpt.mpt_batch_times(b, n)
+        mpt.mpt_batch_release(b)
+        assert done == n and all(flags), rep
+        # times count from this launch's start: a start left over from another launch would
+        # put them far off (or clamp them all to 0)
+        assert all(0 <= t < 10 ** 9 for t in times) and max(times) > 0, (rep, times[:4])
+        assert np.array_equal(w.result(), w.expected()), rep
+    st, site = mpt.mpt_ctx_status(ctx)
+    assert st == mpt.MPT_OK, (st, site)
