@@ -1459,6 +1459,7 @@ def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30, trace_di
         th = threading.Thread(target=feed)
         th.start()
         comp = [0] * n
+        admit = [0] * n
         verified, skipped, bad_digest, moved, got = 0, 0, 0, 0, 0
         bad_status = {}
         deadline = time.perf_counter() + seconds + 60
@@ -1466,6 +1467,7 @@ def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30, trace_di
             for tag, arr, adm, cns, nb, st in mpt.mpt_serve_poll(server):
                 got += 1
                 comp[tag] = cns
+                admit[tag] = adm
                 if st != mpt.MPT_OK:
                     bad_status[st] = bad_status.get(st, 0) + 1
                     continue
@@ -1502,7 +1504,8 @@ def run_serving_replay(mpt, torch, ctx, rates, seconds, budget=8 << 30, trace_di
         if trace_dir:
             np.savez_compressed(os.path.join(trace_dir, f"replay_requests_{int(rate)}.npz"), t0=t0,
                                 due=np.frombuffer(due, dtype=np.uint64), late=np.frombuffer(late, dtype=np.uint64),
-                                comp=np.array(comp, dtype=np.uint64), size=np.array([r[2] for r in rows], dtype=np.uint64),
+                                comp=np.array(comp, dtype=np.uint64), admit=np.array(admit, dtype=np.uint64),
+                                size=np.array([r[2] for r in rows], dtype=np.uint64),
                                 dir=np.array([r[3] for r in rows], dtype=np.uint8))
         out.append({"rate_per_s": rate, "seconds": seconds, "requests": n, "completed": got,
                     "client": "native replay (mpt_serve_replay)",
