@@ -711,13 +711,21 @@ def run_ours(args):
             e2e_step(k)
         torch.cuda.synchronize()
         dist_barrier(world)
-        e0.record(s_up)
-        for k in range(e2e_steps):
-            e2e_step(k, stage_marks)
-        s_up.wait_stream(s_mid)
-        s_up.wait_stream(s_down)
-        e1.record(s_up)
-        e1.synchronize()
+        # the loop only enqueues: a pause of this thread (the cyclic collector) while the
+        # launch queue is full would leave the device idle
+        import gc
+        gc.collect()
+        gc.disable()
+        try:
+            e0.record(s_up)
+            for k in range(e2e_steps):
+                e2e_step(k, stage_marks)
+            s_up.wait_stream(s_mid)
+            s_up.wait_stream(s_down)
+            e1.record(s_up)
+            e1.synchronize()
+        finally:
+            gc.enable()
         dist_barrier(world)
         e2e_s = e0.elapsed_time(e1) / 1e3
         e2e_val, _ = aggregate(world, total_bytes * e2e_steps, e2e_s)
@@ -727,11 +735,16 @@ def run_ours(args):
         # per stage: its duration and its start after the region's start, median over the steps
         stage = {}
         for j, name in ((0, "up"), (2, "sweep"), (4, "down")):
-            stage[f"{name}_ms"] = round(statistics.median(m[j].elapsed_time(m[j + 1]) for m in stage_marks), 3)
+            d = [m[j].elapsed_time(m[j + 1]) for m in stage_marks]
+            stage[f"{name}_ms"] = round(statistics.median(d), 3)
+            stage[f"{name}_ms_max"] = round(max(d), 3)
         periods = [stage_marks[k][0].elapsed_time(stage_marks[k + 1][0]) for k in range(len(stage_marks) - 1)]
         stage["step_period_ms"] = round(statistics.median(periods), 3)
         # a device-wide pause shows as one long period (the median above stays put)
         stage["step_period_max_ms"] = round(max(periods), 3)
+        stage["slowest_period"] = int(max(range(len(periods)), key=lambda k: periods[k]))
+        # a long period whose legs all kept their usual length means the device waited for
+        # the next step's launches
         e2e = {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": total, "d2h_bytes_per_step": total,
                "stages": stage, "host_numa_pages": {"src": _numa_of(hsrc.data_ptr()), "dst": _numa_of(hdst.data_ptr())},
                "steps": e2e_steps, "pipelined": "2 device arena sets; step k down while step k+1 comes up",
@@ -1785,13 +1798,19 @@ def run_batch_only(args):
     ctx = mpt.mpt_ctx_create(0)
     mpt.mpt_batch_configure(ctx, 2, 4096, args.batch_ctas, args.batch_tile)
     sizes, d2d, gaps = payload.batch_workload(args.batch_n)
-    which = {"d2d": [True] * len(sizes), "h2d": [False] * len(sizes), "mix": d2d}[args.batch_only]
+    which = {"d2d": [True] * len(sizes), "h2d": [False] * len(sizes), "d2h": [False] * len(sizes),
+             "mix": d2d}[args.batch_only]
     items, offs = payload.batch_layout(sizes, which, gaps, align=args.batch_align)
     src = {"dev": torch.zeros(offs["dev"] + 64, dtype=torch.uint8, device="cuda"),
            "host": torch.zeros(offs["host"] + 64, dtype=torch.uint8).pin_memory()}
-    dst = torch.empty(offs["dst"] + 64, dtype=torch.uint8, device="cuda")
-    xf = mpt.make_xfers([(src[a].data_ptr() + so, dst.data_ptr() + do, sz, mpt.MPT_D2D if a == "dev" else mpt.MPT_H2D)
-                         for a, so, do, sz in items])
+    if args.batch_only == "d2h":  # host-side sources become device sources, host destination
+        src["host"] = torch.zeros(offs["host"] + 64, dtype=torch.uint8, device="cuda")
+        dst = torch.empty(offs["dst"] + 64, dtype=torch.uint8).pin_memory()
+        kind = lambda a: mpt.MPT_D2H
+    else:
+        dst = torch.empty(offs["dst"] + 64, dtype=torch.uint8, device="cuda")
+        kind = lambda a: mpt.MPT_D2D if a == "dev" else mpt.MPT_H2D
+    xf = mpt.make_xfers([(src[a].data_ptr() + so, dst.data_ptr() + do, sz, kind(a)) for a, so, do, sz in items])
     s = torch.cuda.Stream()
     ks = []
     for r in range(args.warmup + args.steps):
@@ -2136,7 +2155,7 @@ def main(argv=None):
     ap.add_argument("--kernel-ctas", type=int, default=0)
     ap.add_argument("--bulk-config", type=int, default=None,
                     help="bulk kernel configuration for --kernel-only bulk (-1: every configuration in turn)")
-    ap.add_argument("--batch-only", choices=["mix", "d2d", "h2d"], default=None,
+    ap.add_argument("--batch-only", choices=["mix", "d2d", "h2d", "d2h"], default=None,
                     help="run one batch of the batched workload's shape alone (profiling)")
     ap.add_argument("--batch-n", type=int, default=4096)
     ap.add_argument("--batch-ctas", type=int, default=0)

@@ -477,10 +477,12 @@ MPT_API mpt_status mpt_batch_register(mpt_ctx_t ctx, const void* base, uint64_t 
 /* Move n transfers in one launch of the persistent batch kernel, as one replay of a slot's
  * graph on `stream` (windowed transfers, Sec. 5.3: many messages in flight, one launch).
  * The kernel's CTAs claim fixed-size tiles of the transfers through two cursors: tiles of
- * transfers with a host side (over the host link) and device-to-device tiles.  A third of
- * the CTAs start on the former, the rest on the latter, and a CTA whose class runs out moves
- * to the other, so a mixed batch keeps the link busy from the start (MPT_BATCH_SPLIT=0: one
- * cursor over every tile in table order; MPT_BATCH_LINK_CTAS=k: k CTAs start on link tiles).
+ * transfers with a host side (over the host link) and device-to-device tiles.  The first
+ * 32 CTAs (MPT_BATCH_LINK_CTAS=k: k) start on the former and move to device tiles when they
+ * run out; the others take device tiles only.  32 CTAs hold the link at its rate, and
+ * keeping no more of its traffic in flight keeps short what other batches' transfers,
+ * table copies and completion flags wait behind on the link (MPT_BATCH_SPLIT=0: one cursor
+ * over every tile in table order, every CTA on it).
  * Each xfer: D2D (device -> device), H2D (page-locked host -> device, read over the host
  * link by the kernel) or D2H (device -> page-locked host).  Destinations must not overlap
  * (Sec. 4.5: each transfer owns its region).  The descriptor table is copied into the

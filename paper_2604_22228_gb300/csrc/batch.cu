@@ -64,9 +64,14 @@ __device__ __forceinline__ void batch_body(const BatchArgs& a) {
   }
   __shared__ uint32_t s_link;
   const uint32_t dev_tiles = h.total_tiles - h.link_tiles;
-  // thread 0's claiming state: the class it claims from, and whether it has switched yet
-  bool on_link = blockIdx.x < h.link_ctas ? h.link_tiles > 0 : dev_tiles == 0;
-  bool switched = false;
+  // thread 0's claiming state: the class it claims from, and whether it has switched yet.
+  // CTAs [0, link_ctas) take link tiles first, then device tiles; the others take device
+  // tiles only.  That bounds the host-link reads and writes this launch keeps in flight,
+  // and with them the queue that every other user of the link (another batch's table copy,
+  // its completion flags, its host-side bytes) waits behind.
+  const bool may_link = blockIdx.x < h.link_ctas;
+  bool on_link = may_link && h.link_tiles > 0;
+  bool switched = !may_link;
   while (true) {
     if (threadIdx.x == 0) {
       uint32_t item = ~0u;
@@ -155,6 +160,11 @@ constexpr uint32_t kDefaultSlots = 4;
 constexpr uint32_t kDefaultMaxXfers = 4096;
 constexpr uint32_t kDefaultTile = 256 * 1024;
 constexpr uint64_t kMinAdaptiveTile = 32 * 1024;  // smallest tile a short batch is cut into
+// CTAs of a launch that may take link tiles (MPT_BATCH_LINK_CTAS overrides).  32 CTAs keep
+// 1 MiB of host-link traffic in flight, about 5 us of the link: enough to hold it at its
+// rate (host-to-device 204 GB/s, device-to-host 176 GB/s, as with every CTA), while a longer
+// queue only delays whatever else crosses the link
+constexpr uint32_t kDefaultLinkCtas = 32;
 constexpr uint32_t kDmaDirs = 3;  // lanes per direction: D2D, H2D, D2H
 
 uint64_t host_ns() {
@@ -646,9 +656,9 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
       order[dev ? di++ : li++] = (uint32_t)i;
     }
   }
-  uint32_t link_ctas = grid;  // split off, or no device tiles: every CTA on the one class
-  if (c->batch_split && tiles[0] && tiles[1])
-    link_ctas = c->batch_link_ctas ? std::min(c->batch_link_ctas, grid) : std::max(1u, grid / 3);
+  uint32_t link_ctas = grid;  // split off: one class, every CTA on it
+  if (c->batch_split && tiles[0])
+    link_ctas = std::min(grid, c->batch_link_ctas ? c->batch_link_ctas : kDefaultLinkCtas);
   *h = BatchHeader{(uint32_t)n, (uint32_t)(tiles[0] + tiles[1]), (uint32_t)tile, s.epoch,
                    (uint32_t)tiles[0], n_link, n_link + n_dev, link_ctas};
   for (uint32_t k = 0; k < ndma; ++k) {  // retarget used lane items, switch the rest off

@@ -182,7 +182,7 @@ struct mpt_ctx_s {
   bool batch_dma_set = false;                         // configured (else environment defaults)
   bool batch_timing = false;                          // bracket each batch replay with timing events
   bool batch_split = true;                            // link and device tiles claimed separately (MPT_BATCH_SPLIT)
-  uint32_t batch_link_ctas = 0;                       // CTAs starting on link tiles (MPT_BATCH_LINK_CTAS; 0 = a third)
+  uint32_t batch_link_ctas = 0;                       // CTAs that may take link tiles (MPT_BATCH_LINK_CTAS; 0 = default)
   std::vector<cudaEvent_t> each_ev;                   // completion events of mpt_copy_each (grown on demand)
   std::unordered_map<uint64_t, uint64_t> host_bufs;   // page-locked buffers mpt_host_alloc made: address -> bytes
 };
