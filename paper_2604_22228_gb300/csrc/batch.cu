@@ -121,7 +121,8 @@ __device__ __forceinline__ void batch_body(const BatchArgs& a) {
       const uint32_t prev = atomicAdd(a.done + lo, 1u);
       if (prev + 1 == d.ntiles) {
         a.times[lo] = now_ns();
-        __threadfence_system();
+        // the release store's system-scope fence orders the tiles counted through `done`
+        // (each published by its CTA's fence before the count) ahead of the flag
         asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(a.host_flags + lo), "r"(h.epoch) : "memory");
         a.done[lo] = 0;  // every tile of lo is counted: no CTA of this launch touches it again
       }
@@ -328,7 +329,8 @@ uint64_t env_or(const char* name, uint64_t dflt) {
 
 mpt_status batch_setup(mpt_ctx_t c) {
   if (!c->slots.empty()) return MPT_OK;
-  const uint32_t nslots = c->batch_slots ? c->batch_slots : kDefaultSlots;
+  const uint32_t nslots = c->batch_slots ? c->batch_slots
+                                         : (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(64, env_or("MPT_BATCH_SLOTS", kDefaultSlots)));
   const uint32_t maxx = c->batch_max_xfers ? c->batch_max_xfers : kDefaultMaxXfers;
   // three 512-thread CTAs per SM (the aligned kernel's register limit): high occupancy,
   // which the latency of host-link reads needs; all CTAs resident at once
