@@ -148,7 +148,8 @@ __global__ void k_batch_dma_done(BatchArgs a, const uint32_t* dma_map, uint32_t 
   const uint32_t idx = dma_map[item];
   if (idx == ~0u) return;
   a.times[idx] = now_ns();
-  __threadfence_system();
+  // the lane's copy finished before this kernel began (graph edge); the release store
+  // publishes the flag after it
   asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(a.host_flags + idx), "r"(a.hdr->epoch) : "memory");
 }
 
