@@ -293,3 +293,36 @@ def test_batch_counters_reset_across_replays(ctx):
         assert np.array_equal(w.result(), w.expected()), rep
     st, site = mpt.mpt_ctx_status(ctx)
     assert st == mpt.MPT_OK, (st, site)
+
+
+@pytest.mark.parametrize("split", [True, False], ids=["two_cursors", "one_cursor"])
+@pytest.mark.parametrize("link_ctas", [1, 7, 32, 10 ** 6], ids=["1", "7", "32", "all"])
+@pytest.mark.parametrize("align", [16, 1])
+def test_batch_link_ctas_and_cursors(ctx, split, link_ctas, align):
+    """However few CTAs may take host-link tiles (one, a handful, the default 32, every CTA),
+    with two cursors or one, a mixed batch (device-to-device and host-to-device transfers,
+    sizes from 256 B to 4 MiB) equals the oracle and raises every flag: CTAs outside the link
+    group stop when the device tiles run out, and the link group finishes the rest."""
+    import os
+    import torch
+    env = {"MPT_BATCH_LINK_CTAS": str(link_ctas), "MPT_BATCH_SPLIT": "1" if split else "0"}
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        mpt.mpt_batch_configure(ctx, 0, 0, 0, 0)  # rebuilt: the batch ring reads both here
+        w = Workload(300, 0xD000 + link_ctas % 97 + 7 * split + align, 4 * MiB, align=align)
+        b = mpt.mpt_batch_submit(ctx, w.xfers, torch.cuda.current_stream())
+        mpt.mpt_batch_wait(b)
+        done, flags = mpt.mpt_batch_poll(b, len(w.xfers))
+        mpt.mpt_batch_release(b)
+        assert done == len(w.xfers) and all(flags)
+        assert np.array_equal(w.result(), w.expected())
+    finally:
+        for k, v in old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+        mpt.mpt_batch_configure(ctx, 0, 0, 0, 0)
+    st, site = mpt.mpt_ctx_status(ctx)
+    assert st == mpt.MPT_OK, (st, site)
