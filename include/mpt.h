@@ -585,12 +585,13 @@ MPT_API uint64_t mpt_now_ns(void);
  * run overlap with them on the device.  Each request completes individually when the
  * batch kernel raises its flag.  By default each batch in flight gets a stream of its own
  * and the batch kernel one CTA per SM, so a batch of short requests runs beside an earlier
- * batch with a long one instead of behind it (on GB300 at 50k requests/s: p50 49 us against
- * 152 us in order, p99 from submit 572 us against 1.19 ms); requests in flight are then
- * unordered and must not share destination bytes.  An idle worker spins on the arrival
- * flag for MPT_SERVE_SPIN_US microseconds (default 2000; 0 = block at once) after its last
- * work before it blocks, so a request after a short gap is not delayed by a thread wake-up
- * (one core busy while the server is active). */
+ * batch with a long one instead of behind it (on GB300 at 50k requests/s, 2 s: p50 from
+ * submit 28 us against 130 us in order on one stream with three CTAs per SM, p99 277 us
+ * against 1.31 ms); requests in flight are then unordered and must not share destination
+ * bytes.  An idle worker spins on the arrival flag for MPT_SERVE_SPIN_US microseconds
+ * (default 2000; 0 = block at once) after its last work before it blocks, so a request
+ * after a short gap is not delayed by a thread wake-up (one core busy while the server is
+ * active). */
 MPT_API mpt_status mpt_serve_start(mpt_ctx_t ctx, const mpt_serve_config* cfg, mpt_server_t* out);
 
 /* Enqueue one request (thread-safe).  arrival_ns: the request's scheduled arrival on the
