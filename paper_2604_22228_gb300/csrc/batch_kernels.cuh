@@ -14,9 +14,10 @@ constexpr uint32_t kDescDma = 4;       // moved by a copy-engine lane, not by th
 
 // Tiles come in two classes, each numbered from 0 and claimed through its own cursor: link
 // tiles (one side in host memory: they move over the host link) and device tiles (both sides
-// in this GPU's memory).  CTAs [0, link_ctas) claim link tiles first and the others device
-// tiles first; a CTA whose class runs out moves to the other.  The link, which bounds a
-// mixed batch, then stays busy from the start while the device tiles run beside it.
+// in this GPU's memory).  CTAs [0, link_ctas) claim link tiles first and move to device
+// tiles when those run out; the others claim device tiles only.  The link, which bounds a
+// mixed batch, stays busy from the start while the device tiles run beside it, and no more
+// of its traffic is in flight than the link group keeps there.
 struct BatchHeader {
   uint32_t n;            // descriptors in this batch
   uint32_t total_tiles;  // sum of tiles over descriptors, both classes
@@ -25,7 +26,7 @@ struct BatchHeader {
   uint32_t link_tiles;   // tiles of the link class (the rest are device tiles)
   uint32_t n_link;       // descriptors with tiles in the link class: order[0, n_link)
   uint32_t n_tiled;      // descriptors with tiles: order[n_link, n_tiled) are the device class
-  uint32_t link_ctas;    // CTAs that start on link tiles
+  uint32_t link_ctas;    // CTAs that may take link tiles (the first ones of the grid)
 };
 
 struct BatchDesc {
