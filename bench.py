@@ -806,6 +806,18 @@ def run_ours(args):
             gc.unfreeze()
         serve_isolated = run_serve_isolated(mpt, torch, ctx)
         ok = ok and serve_isolated["parity_ok"]
+        # references for the replay's latencies: the lone-request costs just measured (4 KiB
+        # device-to-device; 1 MiB host-to-device less its bytes at the link's rate)
+        rows = {(r["dir"], r["bytes"]): r["server"]["p50_us"] for r in serve_isolated["rows"]}
+        fixed_dev = rows.get(("d2d", 4096))
+        fixed_link = rows.get(("h2d", MiB))
+        if fixed_dev and fixed_link:
+            import payload
+            fixed_link = round(fixed_link - MiB / 204e3, 2)
+            for r in serving_replay:
+                b = serving_bounds(payload.serving_schedule(r["rate_per_s"], r["seconds"]), fixed_dev, fixed_link)
+                r["bounds"] = b
+                r["p99_vs_fair_share"] = round(r["p99_us"] / b["fair_share_p99_us"], 3)
         ok = ok and all(r["errors"] == 0 for r in serving + serving_replay)
         ok = ok and all(r["destinations_disjoint_in_flight"] and r["completed"] == r["requests"] for r in serving_replay)
 
@@ -1329,6 +1341,55 @@ def ring_next_overwrite(place):
             if i < len(nxt) and nxt[i][1] < b:
                 out[k] = nxt[i][2]
     return out
+
+
+def _fair_share_finish(arrivals, work_s):
+    """Finish times of jobs on one server of unit rate shared equally among the jobs present
+    (processor sharing), by virtual time: a job arriving at virtual time V leaves when the
+    virtual time reaches V + its work, and virtual time advances at 1/(jobs present)."""
+    import heapq
+    fin = [0.0] * len(arrivals)
+    t, v, i, active = 0.0, 0.0, 0, []
+    while i < len(arrivals) or active:
+        t_arr = arrivals[i] if i < len(arrivals) else math.inf
+        t_fin = t + (active[0][0] - v) * len(active) if active else math.inf
+        if t_arr <= t_fin:
+            if active:
+                v += (t_arr - t) / len(active)
+            t = t_arr
+            heapq.heappush(active, (v + work_s[i], i))
+            i += 1
+        else:
+            v, k = heapq.heappop(active)
+            t = t_fin
+            fin[k] = t
+    return fin
+
+
+def serving_bounds(sched, fixed_dev_us, fixed_link_us, link_gbs=(204.0, 176.0), dev_gbs=3300.0):
+    """Latency references for a serving schedule (p50/p99, microseconds).  Every request pays
+    a fixed cost (a lone request's, device-to-device or over the host link) plus its bytes:
+    no_queue -- each request alone, at the link's or HBM's rate; fair_share -- each link
+    direction shared equally among the requests on it at each moment (the ideal
+    work-conserving server), device-to-device requests never waiting.  link_gbs: the batch
+    kernel's host-to-device and device-to-host rates; dev_gbs: its device-to-device payload
+    rate."""
+    alone = []
+    fair = [0.0] * len(sched)
+    for k, (_, nb, d) in enumerate(sched):
+        bw = dev_gbs if d == 0 else link_gbs[d - 1]
+        alone.append((fixed_dev_us if d == 0 else fixed_link_us) + nb / (bw * 1e3))
+        if d == 0:
+            fair[k] = alone[-1]
+    for d in (1, 2):
+        idx = [k for k, x in enumerate(sched) if x[2] == d]
+        fin = _fair_share_finish([sched[k][0] for k in idx], [sched[k][1] / (link_gbs[d - 1] * 1e9) for k in idx])
+        for k, f in zip(idx, fin):
+            fair[k] = fixed_link_us + (f - sched[k][0]) * 1e6
+    return {"no_queue_p50_us": round(_percentile(alone, 50), 1), "no_queue_p99_us": round(_percentile(alone, 99), 1),
+            "fair_share_p50_us": round(_percentile(fair, 50), 1), "fair_share_p99_us": round(_percentile(fair, 99), 1),
+            "fixed_us": {"device": fixed_dev_us, "link": fixed_link_us}, "link_gbs": list(link_gbs),
+            "dev_gbs": dev_gbs}
 
 
 def run_serve_isolated(mpt, torch, ctx, reps=200):

@@ -90,3 +90,30 @@ def test_summary_ratios():
 def test_headline_of_a_sparse_study():
     line = bench.headline({"metric": "m", "value": 1.0, "unit": "GB/s"})
     assert line == {"metric": "m", "value": 1.0, "unit": "GB/s", "summary": {}}
+
+
+def test_fair_share_finish_times_by_hand():
+    """The serving bound's processor-sharing server against cases worked by hand: a job alone
+    takes its work; two jobs arriving together share the rate (works 1 and 2 finish at 2 and
+    3); a job arriving while another is half done (works 2 at t=0 and 1 at t=1: from t=1 both
+    run at half rate, the second finishes at 3, the first's last 0 at 3 too); and a job that
+    arrives after the server emptied starts afresh."""
+    assert bench._fair_share_finish([5.0], [2.0]) == [7.0]
+    assert bench._fair_share_finish([0.0, 0.0], [1.0, 2.0]) == [2.0, 3.0]
+    f = bench._fair_share_finish([0.0, 1.0], [2.0, 1.0])
+    assert abs(f[0] - 3.0) < 1e-12 and abs(f[1] - 3.0) < 1e-12
+    f = bench._fair_share_finish([0.0, 1.0, 10.0], [0.5, 4.0, 1.0])
+    assert f == [0.5, 5.0, 11.0]
+
+
+def test_serving_bounds_orders_and_alone_case():
+    """No-queue and fair-share references: with one request they agree with fixed cost plus
+    bytes at the rate; fair sharing never beats running alone."""
+    one = [(0.0, 2 << 20, 1)]
+    b = bench.serving_bounds(one, 10.0, 20.0, link_gbs=(200.0, 100.0), dev_gbs=1000.0)
+    want = 20.0 + (2 << 20) / 200e3
+    assert abs(b["no_queue_p99_us"] - round(want, 1)) < 1e-9 and abs(b["fair_share_p99_us"] - round(want, 1)) < 1e-9
+    import payload
+    sched = payload.serving_schedule(50000, 0.2)
+    b = bench.serving_bounds(sched, 14.0, 16.0)
+    assert b["fair_share_p99_us"] >= b["no_queue_p99_us"] and b["fair_share_p50_us"] >= b["no_queue_p50_us"]
