@@ -743,6 +743,7 @@ def run_ours(args):
         # a device-wide pause shows as one long period (the median above stays put)
         stage["step_period_max_ms"] = round(max(periods), 3)
         stage["slowest_period"] = int(max(range(len(periods)), key=lambda k: periods[k]))
+        stage["periods_ms"] = [round(x, 2) for x in periods]
         # a long period whose legs all kept their usual length means the device waited for
         # the next step's launches
         e2e = {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": total, "d2h_bytes_per_step": total,
