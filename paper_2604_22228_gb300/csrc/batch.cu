@@ -632,7 +632,7 @@ mpt_status mpt_batch_submit(mpt_ctx_t c, const mpt_xfer* xfers, size_t n, void* 
   {
     const uint64_t per_cta = (kernel_bytes + grid - 1) / grid;
     uint64_t t = kMinAdaptiveTile;
-    while (t < per_cta) t <<= 1;
+    while (t < per_cta && t < tile) t <<= 1;  // bounded by the configured tile: no overflow
     tile = std::min<uint64_t>(tile, t);
   }
   uint64_t tiles[2] = {0, 0};  // [0] link, [1] device
