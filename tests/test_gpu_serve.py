@@ -243,3 +243,36 @@ def test_backlog_of_a_slow_client_drains_in_order(ctx):
     assert all(c[5] == mpt.MPT_OK for c in got)
     assert all(a[3] <= b[3] for a, b in zip(got, got[1:]))  # oldest completion first
     assert ar.digests("dst") == ar.digests("src")
+
+
+@pytest.mark.parametrize("spin_us", ["0", "50"], ids=["blocking", "short_spin"])
+def test_worker_that_blocks_between_requests(ctx, spin_us):
+    """With the idle worker blocking at once (MPT_SERVE_SPIN_US=0) or after a short spin,
+    requests that arrive after gaps longer than the spin (so the worker has gone to sleep)
+    still complete, each equal to its source per the oracle's definition of a transfer."""
+    import os
+    ar = Arenas(40, payload.SEED_SERVE + 7)
+    old = os.environ.get("MPT_SERVE_SPIN_US")
+    os.environ["MPT_SERVE_SPIN_US"] = spin_us
+    try:
+        server = mpt.mpt_serve_start(ctx)
+    finally:
+        if old is None:
+            os.environ.pop("MPT_SERVE_SPIN_US", None)
+        else:
+            os.environ["MPT_SERVE_SPIN_US"] = old
+    done = {}
+    for k, s_ar, s_off, d_ar, d_off, nb, d in ar.reqs:
+        time.sleep(0.0005 if k % 2 else 0.003)  # half the gaps outlast a 2 ms spin as well
+        mpt.mpt_serve_submit(server, ar.ptr(s_ar, s_off), ar.ptr(d_ar, d_off), nb, d, k, mpt.mpt_now_ns())
+        t0 = time.time()
+        while k not in done and time.time() - t0 < 10:
+            for c in mpt.mpt_serve_poll(server):
+                done[c[0]] = c
+    mpt.mpt_serve_stop(server)
+    assert len(done) == len(ar.reqs) and all(c[5] == mpt.MPT_OK for c in done.values())
+    assert ar.digests("dst") == ar.digests("src")
+    for k in range(0, len(ar.reqs), 7):
+        _, s_ar, s_off, d_ar, d_off, nb, _ = ar.reqs[k]
+        got = ar.t[d_ar][d_off:d_off + nb].cpu().numpy()
+        assert np.array_equal(got, ar.src_np[s_ar][s_off:s_off + nb])
