@@ -1018,15 +1018,15 @@ def run_copy64_split(mpt, torch, ctx, stream, replays=100, warm=10):
 
 def time_back_to_back(mpt, torch, stream, handles, max_k=10000):
     """Per-transfer time of K launches of one handle back to back, K = max(1, 2^26 / N) capped
-    at max_k (median of 3 runs when K = 1): the regime of a stream of messages of one size
-    over the same buffers (L2-warm below about 64 MiB)."""
+    at max_k (median of 3 runs): the regime of a stream of messages of one size over the same
+    buffers (L2-warm below about 64 MiB)."""
     import statistics
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = []
     for n, h in zip(SIZES, handles):
         k = max(1, min(max_k, (1 << 26) // n))
         ts = []
-        for _ in range(3 if k == 1 else 1):
+        for _ in range(3):
             mpt.mpt_launch(h, stream)
             e0.record(stream)
             for _ in range(k):
@@ -2179,7 +2179,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--tune-file", default=None)
-    ap.add_argument("--baseline-reps", type=int, default=9)
+    ap.add_argument("--baseline-reps", type=int, default=21)
     ap.add_argument("--kernel-launches", type=int, default=20)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
