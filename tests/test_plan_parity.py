@@ -117,3 +117,38 @@ def test_duplex_flag_needs_a_host_side_and_a_context():
     with pytest.raises(mpt.MptError) as e:  # the tuned choice needs a context
         mpt.mpt_plan(None, 1 << 20, mpt.MPT_H2D, None, 16, mpt.MPT_PLAN_DUPLEX)
     assert e.value.status == mpt.MPT_EINVAL
+
+
+def _shipped_entries():
+    import json
+    import os
+    import re
+    root = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2604_22228_gb300", "tuned")
+    out = []
+    for name in sorted(os.listdir(root)) if os.path.isdir(root) else []:
+        if not name.endswith(".jsonl"):
+            continue
+        with open(os.path.join(root, name)) as f:
+            for line in f:
+                if line.strip() and not line.startswith("#"):
+                    out.append((re.sub(r"\.jsonl$", "", name), json.loads(line)))
+    return out
+
+
+def test_shipped_tuned_tables_give_oracle_plans():
+    """Every entry of the shipped offline-tuned tables is a path set the oracle accepts for its
+    direction, and at both ends of the entry's size bucket (2^b and 2^(b+1) - 1 bytes) the
+    library's plan equals the oracle's plan, which passes the oracle's invariant checker."""
+    entries = _shipped_entries()
+    assert entries, "no shipped table"
+    for dev, e in entries:
+        specs = [(p[0], p[1], p[2]) for p in e["paths"]]
+        assert sum(s[1] for s in specs) == P.SHARE_ONE, (dev, e)
+        assert all(s[0] in P.ALLOWED_KINDS[e["dir"]] for s in specs), (dev, e)
+        assert e["us"] > 0, (dev, e)
+        for n in (1 << e["bucket"], (2 << e["bucket"]) - 1):
+            want = P.plan(n, e["dir"], specs)
+            P.check_invariants(n, specs, 16, want)
+            got, paths = lib_plan(n, e["dir"], specs)
+            assert got == want, (dev, e, n)
+            assert [(p["kind"], p["share"], p["chunk_bytes"]) for p in paths] == specs
