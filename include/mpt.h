@@ -395,8 +395,11 @@ MPT_API mpt_status mpt_model_optimize(const mpt_model* m, uint64_t nbytes, uint3
  * with a cold L2 full of dirty lines (a 256 MiB write first, as after the kernel that
  * produced the data; a message of at most 64 MiB is timed as the mean of 8 back-to-back
  * launches after it, each on its own buffer region -- the regime of a stream of messages,
- * where launch costs overlap),
- * and store the fastest for the message's log2 size bucket.  With mode | MPT_MODE_PAGEABLE
+ * where launch costs overlap).  The three fastest candidates and the fastest single-path
+ * candidate of each path kind are then timed again in interleaved rounds (one run of each
+ * per round, at least 5 rounds), so that drift between candidates timed far apart cannot
+ * decide the choice; the lowest median of those rounds is stored for the message's log2
+ * size bucket.  With mode | MPT_MODE_PAGEABLE
  * (H2D/D2H) the host buffer is ordinary pageable memory and the candidates are the paths
  * that accept it: the zero-copy kernel, host-thread staging (MPT_HS_HOST_THREADS) and their
  * splits; the entry serves mpt_plan(..., MPT_PLAN_PAGEABLE).  Blocking;
