@@ -716,10 +716,13 @@ def run_ours(args):
         import gc
         gc.collect()
         gc.disable()
+        host_enq = []  # host seconds after the region's start at which each step was enqueued
         try:
             e0.record(s_up)
+            t_h0 = time.perf_counter()
             for k in range(e2e_steps):
                 e2e_step(k, stage_marks)
+                host_enq.append(time.perf_counter() - t_h0)
             s_up.wait_stream(s_mid)
             s_up.wait_stream(s_down)
             e1.record(s_up)
@@ -744,6 +747,11 @@ def run_ours(args):
         stage["step_period_max_ms"] = round(max(periods), 3)
         stage["slowest_period"] = int(max(range(len(periods)), key=lambda k: periods[k]))
         stage["periods_ms"] = [round(x, 2) for x in periods]
+        # when the host had each step enqueued, and when the device began it (its up leg's
+        # start), both from the region's start: a step the device began long after the host
+        # enqueued it waited on the device or the link, not on the launching thread
+        stage["host_enqueued_ms"] = [round(1e3 * x, 2) for x in host_enq]
+        stage["device_started_ms"] = [round(e0.elapsed_time(m[0]), 2) for m in stage_marks]
         # a long period whose legs all kept their usual length means the device waited for
         # the next step's launches
         e2e = {"value": round(e2e_val, 3), "unit": "GB/s", "h2d_bytes_per_step": total, "d2h_bytes_per_step": total,
