@@ -152,3 +152,53 @@ def test_shipped_defaults_load(monkeypatch):
             mpt.mpt_tune_get(ctx, P.D2D, 1 << 30, mpt.MPT_MODE_GRAPH)
     finally:
         mpt.mpt_ctx_destroy(ctx)
+
+
+def _verbose_lines(err, tag):
+    """Parse MPT_TUNE_VERBOSE lines: (median us, [(kind, share, chunk, ctas, flags), ...])."""
+    import re
+    out = []
+    for line in err.splitlines():
+        if not line.startswith(tag + " dir="):
+            continue
+        us = float(re.search(r" us=([0-9.]+)", line).group(1))
+        paths = [tuple(int(x) for x in m.split()) for m in re.findall(r"\[([0-9 ]+)\]", line)]
+        out.append((us, paths))
+    return out
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("direction,n,kinds", [(P.D2D, 4 * MiB, {P.CE, P.SM}),
+                                               (P.H2D, 8 * MiB, {P.CE, P.ZC, P.HS})])
+def test_tune_confirms_leaders_against_single_paths(capfd, monkeypatch, direction, n, kinds):
+    """mpt_tune re-times its leaders together with the fastest single-path candidate of each
+    path kind in interleaved rounds, and keeps the lowest median of those rounds: the rounds
+    hold a single-path candidate of every kind that was measured, the three first-pass
+    leaders, and the stored choice is the confirmed minimum."""
+    monkeypatch.delenv("MPT_PATHS", raising=False)
+    monkeypatch.setenv("MPT_TUNE_VERBOSE", "1")
+    ctx = mpt.mpt_ctx_create(0)
+    try:
+        capfd.readouterr()
+        paths, us = mpt.mpt_tune(ctx, direction, n, mpt.MPT_MODE_GRAPH)
+        err = capfd.readouterr().err
+        assert mpt.mpt_ctx_status(ctx)[0] == mpt.MPT_OK
+    finally:
+        mpt.mpt_ctx_destroy(ctx)
+    first = _verbose_lines(err, "mpt_tune")
+    confirm = _verbose_lines(err, "mpt_tune confirm")
+    assert len(first) >= 10 and 3 <= len(confirm) <= 3 + len(kinds)
+    assert {p[0][0] for _, p in confirm if len(p) == 1} >= kinds
+    # the three first-pass leaders were confirmed; medians print rounded to 0.01 us, so ties
+    # at the third place are allowed either way
+    confirmed = [q for _, q in confirm]
+    ranked = sorted(first, key=lambda r: r[0])
+    cut = ranked[2][0]
+    for u, p in ranked:
+        if u < cut:
+            assert p in confirmed, p
+    assert sum(1 for u, p in ranked if u <= cut and p in confirmed) >= 3
+    best_us = min(u for u, _ in confirm)
+    chosen = [tuple(q[k] for k in ("kind", "share", "chunk_bytes", "ctas", "flags")) for q in paths]
+    assert chosen in [p for u, p in confirm if u == best_us]
+    assert abs(us - best_us) < 0.006
