@@ -552,67 +552,69 @@ def run_ours(args):
     per_size_tuned = [max(1e-6, full_ms - sweep_ms(step_handles[:i] + step_handles[i + 1:])) for i in range(nsz)]
 
     # ---- per-size baselines (not part of value) ----
-    def time_graphs(graphs, reps):
-        out = []
-        for i, g in enumerate(graphs):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ts = []
+    def time_isolated(sets, reps):
+        """Single isolated launches of every set at every size: for each size, `reps` rounds
+        of one launch per set, each after a 1 GiB transfer that evicts the message from L2
+        and bracketed by CUDA events; the median per set and size.  The sets take turns
+        within each round, so drift over the run (clocks, memory state) does not fall
+        between them."""
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        out = {name: [] for name in sets}
+        for i in range(nsz):
+            ts = {name: [] for name in sets}
             for _ in range(reps):
-                # a 1 GiB transfer in between evicts this message from L2
-                mpt.mpt_launch(tuned_graphs[-1], stream)
-                e0.record(stream)
-                mpt.mpt_launch(g, stream)
-                e1.record(stream)
-                e1.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            out.append(statistics.median(ts))
+                for name, launch in sets.items():
+                    mpt.mpt_launch(tuned_graphs[-1], stream)
+                    e0.record(stream)
+                    launch(i)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ts[name].append(e0.elapsed_time(e1))
+            for name in sets:
+                out[name].append(statistics.median(ts[name]))
         return out
 
-    def time_eager(plans, reps):
-        out = []
-        for n, o, p in zip(SIZES, offs, plans):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            ts = []
-            for _ in range(reps):
-                mpt.mpt_launch(tuned_graphs[-1], stream)
-                e0.record(stream)
-                mpt.mpt_launch_eager(ctx, p, base_d + o, base_s + o, stream)
-                e1.record(stream)
-                e1.synchronize()
-                ts.append(e0.elapsed_time(e1))
-            out.append(statistics.median(ts))
-        return out
+    def graph_launcher(handles):
+        return lambda i: mpt.mpt_launch(handles[i], stream)
+
+    def eager_launcher(plans):
+        return lambda i: mpt.mpt_launch_eager(ctx, plans[i], base_d + offs[i], base_s + offs[i], stream)
 
     reps = args.baseline_reps
     base = {}
     if not args.no_baselines:
-        base["tuned"] = time_graphs(step_handles, reps)
-        base["tuned_graph_only"] = time_graphs(tuned_graphs, reps)
+        eager_plans = [mpt.mpt_plan(ctx, n, mpt.MPT_D2D, None, 16, mpt.MPT_PLAN_EAGER) for n in SIZES]
+        sets = {"tuned": graph_launcher(step_handles), "tuned_graph_only": graph_launcher(tuned_graphs),
+                "tuned_eager": eager_launcher(eager_plans)}
+        held_plans, held_graphs = [], []
         for kind in ("ce", "sm", "split", "hs"):
             plans, graphs = capture_all(kind)
-            base[kind] = time_graphs(graphs, reps)
-            for g in graphs:
-                mpt.mpt_graph_release(g)
-            if kind == "split":
-                base["split_eager"] = time_eager(plans, reps)
-            if kind in ("ce", "sm"):  # a single path may also be issued directly
-                base[kind + "_eager"] = time_eager(plans, reps)
-            for p in plans:
-                mpt.mpt_plan_destroy(p)
-        eager_plans = [mpt.mpt_plan(ctx, n, mpt.MPT_D2D, None, 16, mpt.MPT_PLAN_EAGER) for n in SIZES]
-        base["tuned_eager"] = time_eager(eager_plans, reps)
+            held_plans += plans
+            held_graphs += graphs
+            sets[kind] = graph_launcher(graphs)
+            if kind in ("ce", "sm", "split"):  # a single path may also be issued directly
+                sets[kind + "_eager"] = eager_launcher(plans)
+        base.update(time_isolated(sets, reps))
+        for g in held_graphs:
+            mpt.mpt_graph_release(g)
+        for p in held_plans:
+            mpt.mpt_plan_destroy(p)
         # back to back, K launches per size (per-transfer time), each set as graph and direct issue
         b2b_sets = {"tuned": (tuned_plans, eager_plans)}
         for kind in ("ce", "sm"):
             b2b_sets[kind] = ([make_plan(n, kind) for n in SIZES], None)
+        b2b_handles = {}
         for name, (gplans, eplans) in b2b_sets.items():
             eplans = eplans or gplans
             for mode, plans in (("graph", gplans), ("eager", eplans)):
                 pm = mpt.MPT_PREPARE_GRAPH if mode == "graph" else mpt.MPT_PREPARE_EAGER
-                hs = [mpt.mpt_prepare(ctx, p, base_d + o, base_s + o, pm) for p, o in zip(plans, offs)]
-                base[f"b2b_{name}_{mode}"] = time_back_to_back(mpt, torch, stream, hs, args.b2b_max_launches)
-                for h in hs:
-                    mpt.mpt_graph_release(h)
+                b2b_handles[f"b2b_{name}_{mode}"] = [mpt.mpt_prepare(ctx, p, base_d + o, base_s + o, pm)
+                                                     for p, o in zip(plans, offs)]
+        base.update(time_back_to_back(mpt, torch, stream, b2b_handles, args.b2b_max_launches))
+        for hs in b2b_handles.values():
+            for h in hs:
+                mpt.mpt_graph_release(h)
+        for name, (gplans, _) in b2b_sets.items():
             if name != "tuned":
                 for p in gplans:
                     mpt.mpt_plan_destroy(p)
@@ -1024,25 +1026,29 @@ def run_copy64_split(mpt, torch, ctx, stream, replays=100, warm=10):
     return out
 
 
-def time_back_to_back(mpt, torch, stream, handles, max_k=10000):
+def time_back_to_back(mpt, torch, stream, sets, max_k=10000):
     """Per-transfer time of K launches of one handle back to back, K = max(1, 2^26 / N) capped
-    at max_k (median of 3 runs): the regime of a stream of messages of one size over the same
-    buffers (L2-warm below about 64 MiB)."""
+    at max_k, for every set of handles (name -> one handle per size): the regime of a stream
+    of messages of one size over the same buffers (L2-warm below about 64 MiB).  For each
+    size, three rounds in which the sets take turns; the median per set and size."""
     import statistics
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    out = []
-    for n, h in zip(SIZES, handles):
+    out = {name: [] for name in sets}
+    for i, n in enumerate(SIZES):
         k = max(1, min(max_k, (1 << 26) // n))
-        ts = []
+        ts = {name: [] for name in sets}
         for _ in range(3):
-            mpt.mpt_launch(h, stream)
-            e0.record(stream)
-            for _ in range(k):
+            for name, handles in sets.items():
+                h = handles[i]
                 mpt.mpt_launch(h, stream)
-            e1.record(stream)
-            e1.synchronize()
-            ts.append(e0.elapsed_time(e1) / k)
-        out.append(statistics.median(ts))
+                e0.record(stream)
+                for _ in range(k):
+                    mpt.mpt_launch(h, stream)
+                e1.record(stream)
+                e1.synchronize()
+                ts[name].append(e0.elapsed_time(e1) / k)
+        for name in sets:
+            out[name].append(statistics.median(ts[name]))
     return out
 
 
